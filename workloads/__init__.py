@@ -1,0 +1,258 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only builds inputs: lattice sizes, edge kinds, solid masks,
+parameter sets and initial fields.  It contains none of the lattice update's
+arithmetic, and both the FP64 oracle and the CUDA library consume what it
+returns.  Every random draw comes from ``numpy.random.default_rng(seed)``.
+
+Conventions (shared by both implementations):
+  * arrays are [ny, nx]; node (i, j) sits at (x, y) = (i, j);
+  * edges = (left, right, bottom, top) with 0 periodic, 1 wetting wall,
+    2 neutral wall, 3 velocity lid (top only); half-way walls sit half a
+    spacing outside the first and last rows/columns;
+  * mask: 0 fluid, 1 wetting solid, 2 neutral solid; a cylinder node is solid
+    iff its distance to the centre is <= R;
+  * the initial order parameter of a drop of radius R is the smooth profile
+    0.5 + 0.5 tanh(2 (R - r) / D) of Eqs. 46, 50 and 56, with r the Euclidean
+    distance (the printed formulas drop the square root); a compound drop is
+    c1 = profile(R_core), c2 = profile(R_shell) - c1;
+  * "mobility m" in a workload description means M_1 = m, i.e. M0 = m * lambda_1
+    (the paper quotes M_1 = M_2 = 0.1 directly in Sec. III.D).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PERIODIC, WETTING, NEUTRAL, LID = 0, 1, 2, 3
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    edges: tuple
+    mask: np.ndarray
+    params: dict
+    c1: np.ndarray
+    c2: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    p: np.ndarray | None = None
+    steps: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny
+
+
+def lambda1(s12, s13, s23):
+    return s12 + s13 - s23
+
+
+def theta12_from(s12, s13, s23, th13_deg, th23_deg):
+    """theta_12 from the Eq. 39 constraint, given theta_13 and theta_23 (degrees)."""
+    c = (s13 * math.cos(math.radians(th13_deg)) - s23 * math.cos(math.radians(th23_deg))) / s12
+    if abs(c) > 1.0:
+        raise ValueError("no theta_12 satisfies Eq. 39 for these angles")
+    return math.degrees(math.acos(c))
+
+
+def params(*, sigma=(1e-3, 1e-3, 1e-3), theta=(90.0, 90.0, 90.0), rho=(1.0, 1.0, 1.0),
+           nu=(0.1, 0.1, 0.1), mobility=0.1, D=4.0, tau=(0.8, 0.8), g=(0.0, 0.0),
+           lid_u=0.0, M0=None) -> dict:
+    s12, s13, s23 = sigma
+    if M0 is None:
+        M0 = mobility * lambda1(s12, s13, s23)
+    return dict(sigma12=s12, sigma13=s13, sigma23=s23,
+                theta12_deg=theta[0], theta13_deg=theta[1], theta23_deg=theta[2],
+                rho1=rho[0], rho2=rho[1], rho3=rho[2], nu1=nu[0], nu2=nu[1], nu3=nu[2],
+                M0=M0, D=D, tau1=tau[0], tau2=tau[1], gx=g[0], gy=g[1], lid_u=lid_u)
+
+
+def grid(nx, ny):
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    return x, y
+
+
+def profile(x, y, xc, yc, R, D, period_x=None, period_y=None):
+    """0.5 + 0.5 tanh(2 (R - r) / D), r the (minimum-image if periodic) distance."""
+    dx = x - xc
+    dy = y - yc
+    if period_x:
+        dx = (dx + period_x / 2) % period_x - period_x / 2
+    if period_y:
+        dy = (dy + period_y / 2) % period_y - period_y / 2
+    r = np.sqrt(dx * dx + dy * dy)
+    return 0.5 + 0.5 * np.tanh(2.0 * (R - r) / D)
+
+
+def _zeros(nx, ny):
+    return np.zeros((ny, nx))
+
+
+# ---- the paper-shaped workloads -------------------------------------------
+
+def binary_drops_on_wall(nx=128, ny=64, R=16.0, sep=40.0, theta=(60.0, 90.0, 120.0),
+                         steps=2000) -> Workload:
+    """Two semicircular drops (fluid 1 and fluid 2) on a wetting bottom wall in
+    fluid 3, neutral top wall, periodic in x (Sec. III.A set-up at 128x64)."""
+    x, y = grid(nx, ny)
+    xc1 = nx / 2 - sep / 2
+    xc2 = nx / 2 + sep / 2
+    c1 = profile(x, y, xc1, -0.5, R, 4.0, period_x=nx)
+    c2 = profile(x, y, xc2, -0.5, R, 4.0, period_x=nx)
+    P = params(sigma=(1e-3, 1e-3, 1e-3), theta=theta, rho=(1, 1, 1), nu=(0.1, 0.1, 0.1),
+               mobility=0.1, D=4.0)
+    return Workload("binary_drops_128x64", nx, ny, (PERIODIC, PERIODIC, WETTING, NEUTRAL),
+                    np.zeros((ny, nx), np.uint8), P, c1, c2, _zeros(nx, ny), _zeros(nx, ny),
+                    steps=steps)
+
+
+def compound_drop_shear(nx=512, ny=256, R_core=30.0, R_shell=50.0, U0=0.01, steps=20000,
+                        sigma=(2e-3, 1e-3, 1e-3), theta13=90.0, theta23=135.0) -> Workload:
+    """Compound drop (core fluid 1, shell fluid 2) on a wetting wall in fluid 3,
+    sheared by a velocity lid (Sec. III.C set-up at 512x256).  theta_12 is
+    derived from Eq. 39 (the paper's convention for given theta_13, theta_23)."""
+    x, y = grid(nx, ny)
+    xc = nx / 2
+    c1 = profile(x, y, xc, -0.5, R_core, 4.0, period_x=nx)
+    c2 = profile(x, y, xc, -0.5, R_shell, 4.0, period_x=nx) - c1
+    th12 = theta12_from(*sigma, theta13, theta23)
+    P = params(sigma=sigma, theta=(th12, theta13, theta23), rho=(1.0, 2.0, 1.0),
+               nu=(0.05, 0.1, 0.05), mobility=0.1, D=4.0, lid_u=U0)
+    ux = _zeros(nx, ny)
+    ux[ny - 1, :] = U0
+    return Workload(f"compound_drop_shear_{nx}x{ny}", nx, ny,
+                    (PERIODIC, PERIODIC, WETTING, LID), np.zeros((ny, nx), np.uint8), P,
+                    c1, c2, ux, _zeros(nx, ny), steps=steps)
+
+
+def compound_drop_on_cylinder(nx=1024, ny=2048, R_cyl=120.0, R_core=60.0, R_shell=100.0,
+                              We=10.0, theta=90.0, steps=50000, cyl_center=None,
+                              drop_center=None) -> Workload:
+    """Compound drop falling onto a wetting circular cylinder, fully periodic
+    (Sec. III.D set-up).  sigma_ij = 0.01, rho = (10, 10, 1), nu_i = 0.02,
+    M_1 = M_2 = 0.1, theta_12 = 90, theta_13 = theta_23 = theta; the impact
+    speed U follows from We = rho_bar xi U^2 / sigma_bar (Eq. 55) with
+    xi = 2 R_shell; u0 = (0, -U) (c1 + c2)."""
+    x, y = grid(nx, ny)
+    cx, cy = cyl_center or (nx / 2, nx / 2)
+    dx_, dy_ = drop_center or (nx / 2, nx / 2 + R_cyl + R_shell + 48.0)
+    mask = (((x - cx) ** 2 + (y - cy) ** 2) <= R_cyl ** 2).astype(np.uint8)
+    c1 = profile(x, y, dx_, dy_, R_core, 4.0, period_x=nx, period_y=ny)
+    c2 = profile(x, y, dx_, dy_, R_shell, 4.0, period_x=nx, period_y=ny) - c1
+    c1[mask == 1] = 0.0
+    c2[mask == 1] = 0.0
+    sig = 0.01
+    rho_bar = 10.0
+    xi = 2.0 * R_shell
+    U = math.sqrt(We * sig / (rho_bar * xi))
+    P = params(sigma=(sig, sig, sig), theta=(90.0, theta, theta), rho=(10.0, 10.0, 1.0),
+               nu=(0.02, 0.02, 0.02), mobility=0.1, D=4.0)
+    uy = -U * (c1 + c2)
+    return Workload(f"compound_drop_on_cylinder_{nx}x{ny}", nx, ny,
+                    (PERIODIC, PERIODIC, PERIODIC, PERIODIC), mask, P, c1, c2,
+                    _zeros(nx, ny), uy, steps=steps,
+                    meta=dict(We=We, U=U, Re=xi * U / 0.02))
+
+
+def tiled_drops(nx=2048, ny=2048, seed=1710, steps=1000) -> Workload:
+    """Large lattice with the binary-drop physics tiled up: drops of fluid 1 and
+    fluid 2 (R = 16) every 40 nodes along a wetting bottom wall, a neutral top
+    wall, periodic in x, plus seeded free compound drops in the bulk."""
+    rng = np.random.default_rng(seed)
+    x, y = grid(nx, ny)
+    c1 = np.zeros((ny, nx))
+    c2 = np.zeros((ny, nx))
+    for i, xc in enumerate(np.arange(20.0, nx, 40.0)):
+        prof = profile(x, y, xc, -0.5, 16.0, 4.0, period_x=nx)
+        if i % 2 == 0:
+            c1 = np.maximum(c1, prof)
+        else:
+            c2 = np.maximum(c2, prof)
+    n_free = max(1, (nx * ny) // 60000)
+    for _ in range(n_free):
+        xc = rng.uniform(0, nx)
+        yc = rng.uniform(80, ny - 60)
+        rs = rng.uniform(10, 24)
+        prof_s = profile(x, y, xc, yc, rs, 4.0, period_x=nx)
+        prof_c = profile(x, y, xc, yc, 0.55 * rs, 4.0, period_x=nx)
+        keep = c1 + c2 < 0.01
+        c1 = np.where(keep, np.maximum(c1, prof_c), c1)
+        c2 = np.where(keep, np.maximum(c2, prof_s - prof_c), c2)
+    P = params(sigma=(1e-3, 1e-3, 1e-3), theta=(60.0, 90.0, 120.0), mobility=0.1, D=4.0)
+    return Workload(f"tiled_drops_{nx}x{ny}", nx, ny, (PERIODIC, PERIODIC, WETTING, NEUTRAL),
+                    np.zeros((ny, nx), np.uint8), P, np.clip(c1, 0, 1), np.clip(c2, 0, 1),
+                    _zeros(nx, ny), _zeros(nx, ny), steps=steps)
+
+
+# ---- random small lattices for parity tests -------------------------------
+
+def random_lattice(nx, ny, seed, edges=None, solids=("disc",), u_amp=0.01, rho=(1.0, 3.0, 1.0),
+                   lid_u=0.0) -> Workload:
+    """Random drops, a random solid mask (discs, pillars, L-shaped concave
+    corners), small random velocity.  Used to reach every branch of the wall
+    rules in parity tests."""
+    rng = np.random.default_rng(seed)
+    if edges is None:
+        edges = (PERIODIC, PERIODIC, WETTING, NEUTRAL)
+    x, y = grid(nx, ny)
+    mask = np.zeros((ny, nx), np.uint8)
+    for kind in solids:
+        kind_val = int(rng.integers(1, 3))
+        if kind == "disc":
+            cx, cy, R = rng.uniform(0.3 * nx, 0.7 * nx), rng.uniform(0.3 * ny, 0.7 * ny), rng.uniform(3, max(4, min(nx, ny) / 6))
+            mask[((x - cx) ** 2 + (y - cy) ** 2) <= R * R] = kind_val
+        elif kind == "pillar":
+            px, py = int(rng.integers(3, nx - 3)), int(rng.integers(3, ny - 3))
+            mask[py, px] = kind_val
+        elif kind == "corner":
+            px, py = int(rng.integers(4, nx - 8)), int(rng.integers(4, ny - 8))
+            mask[py:py + 4, px:px + 2] = kind_val
+            mask[py:py + 2, px:px + 5] = kind_val
+    # keep the lid row and the row below it fluid
+    if edges[3] == LID:
+        mask[ny - 3:, :] = 0
+    c1 = np.zeros((ny, nx))
+    c2 = np.zeros((ny, nx))
+    for i in range(int(rng.integers(2, 5))):
+        xc, yc = rng.uniform(0, nx), rng.uniform(0, ny)
+        R = rng.uniform(3, max(4, min(nx, ny) / 4))
+        prof = profile(x, y, xc, yc, R, 4.0, period_x=nx if edges[0] == PERIODIC else None,
+                       period_y=ny if edges[2] == PERIODIC else None)
+        if i % 2 == 0:
+            c1 = np.maximum(c1, prof)
+        else:
+            c2 = np.maximum(c2, prof)
+    s = c1 + c2
+    over = s > 1
+    c1[over] /= s[over]
+    c2[over] /= s[over]
+    c1[mask > 0] = 0
+    c2[mask > 0] = 0
+    ux = u_amp * rng.standard_normal((ny, nx))
+    uy = u_amp * rng.standard_normal((ny, nx))
+    ux[mask > 0] = 0
+    uy[mask > 0] = 0
+    sigma = tuple(rng.uniform(0.8e-3, 1.5e-3, 3))
+    # keep lambda_i > 0.5 lambda_T by drawing near-equal tensions
+    th13, th23 = rng.uniform(40, 140, 2)
+    try:
+        th12 = theta12_from(*sigma, th13, th23)
+    except ValueError:
+        th13, th23 = 90.0, 90.0
+        th12 = theta12_from(*sigma, th13, th23)
+    P = params(sigma=sigma, theta=(th12, th13, th23), rho=rho,
+               nu=tuple(rng.uniform(0.05, 0.15, 3)), mobility=float(rng.uniform(0.05, 0.15)),
+               D=float(rng.choice([3.0, 4.0, 5.0])), tau=tuple(rng.uniform(0.7, 1.0, 2)),
+               g=(0.0, -1e-6), lid_u=lid_u)
+    if edges[3] == LID:
+        ux[ny - 1, :] = lid_u
+        uy[ny - 1, :] = 0
+    return Workload(f"random_{nx}x{ny}_s{seed}", nx, ny, tuple(edges), mask, P, c1, c2, ux, uy,
+                    steps=0)
