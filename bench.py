@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Throughput of the ternary phase-field lattice Boltzmann update on GB300.
+
+One bench step = one time step of the whole hot path (fused interior kernel +
+near-wall kernel) over the 2048x2048 tiled-drops lattice (binary drops on a
+wetting bottom wall, neutral top wall, periodic in x, free compound drops in
+the bulk).  The state (FP64: 1.8 GB double-buffered) is far larger than the
+129 MB L2, so no explicit flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead, on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one lattice per rank, no
+collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % of HBM roofline, batched/served vs plain; p50/p99 solve latency"
+# algorithmic bytes per node update: 27 distributions + 4 c_i u values, read
+# and written once (solid and near-wall nodes included in the node count)
+SCALARS_PER_NODE = 2 * (27 + 4)
+# algorithmic flops per node update (FMA = 2), the tally of the update's
+# arithmetic: moments, stencils, chemical potentials, forces, 9-direction
+# equilibria, sources and BGK relaxation of the three distributions
+FLOPS_PER_NODE = 700
+# FP64 vector peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+SAMPLE_ROWS = 256
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variants", default="fp32", help="comma list of extra precisions to time")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.seek(0)
+        sms, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as D
+        backend = os.environ.get("TLB_BENCH_BACKEND", "nccl")
+        D.init_process_group(backend)
+        return D, D.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def sample_workload(w, rows=SAMPLE_ROWS):
+    """Bottom `rows` rows of a workload (same edges, physics and drops)."""
+    import copy
+    s = copy.copy(w)
+    s.ny = rows
+    for k in ("mask", "c1", "c2", "ux", "uy"):
+        setattr(s, k, np.ascontiguousarray(getattr(w, k)[:rows]))
+    s.name = f"{w.name}[rows 0..{rows - 1}]"
+    return s
+
+
+def oracle_run(w, steps, warmup=0):
+    """Time the FP64 oracle on workload w (host cores); returns (MLUPS, seconds, threads)."""
+    import oracle
+    O = oracle.OracleLattice(w.nx, w.ny, w.edges, w.mask, w.params)
+    O.set_fields(w.c1, w.c2, w.ux, w.uy)
+    if warmup:
+        O.step(warmup)
+    t0 = time.perf_counter()
+    O.step(steps)
+    dt = time.perf_counter() - t0
+    return w.nx * w.ny * steps / dt / 1e6, dt, oracle.threads()
+
+
+def cpu_baseline(w, budget_s=15.0):
+    s = sample_workload(w)
+    _, t1, _ = oracle_run(s, 1)
+    steps = max(1, min(200, int(budget_s / max(t1, 1e-3))))
+    mlups, dt, thr = oracle_run(s, steps)
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
+            "sample": f"{s.nx}x{s.ny} bottom strip of the {w.nx}x{w.ny} lattice, {steps} steps, "
+                      f"{dt:.1f} s, FP64 C oracle with OpenMP over nodes"}
+
+
+def run_reference(args):
+    D, rank, ws, _ = dist()
+    if rank != 0:
+        return
+    import workloads as W
+    w = sample_workload(W.tiled_drops(args.nx, args.ny))
+    import oracle
+    O = oracle.OracleLattice(w.nx, w.ny, w.edges, w.mask, w.params)
+    O.set_fields(w.c1, w.c2, w.ux, w.uy)
+    O.step(args.warmup)
+    t0 = time.perf_counter()
+    O.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = w.nx * w.ny * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "precision": "fp64",
+                       "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": oracle.threads(),
+                             "kind": "oracle", "sample": f"{w.name}, {args.steps} steps per run"},
+            "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(L, steps, torch, stream):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    L.step(steps)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end)
+
+
+def run_ours(args):
+    import torch
+    D, rank, ws, local = dist()
+    torch.cuda.set_device(local)
+    import paper_1710_09534_gb300 as T
+    import workloads as W
+    stream = torch.cuda.current_stream()
+    w = W.tiled_drops(args.nx, args.ny)
+    L = T.lattice_from_workload(w, args.precision)
+    n_nodes = w.nx * w.ny
+    L.step(args.warmup)
+    L.sync()
+    # timed region: K steps, barrier + synchronize on both sides
+    if D:
+        D.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local) if rank == 0 else None
+    L.profile(True)
+    ms = time_steps(L, args.steps, torch, stream)
+    k1_ms, k2_ms, k1_n, k2_n = L.profile_read()
+    L.profile(False)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    if D:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        D.all_reduce(t, op=D.ReduceOp.MAX)
+        ms = float(t.item())
+        D.barrier()
+    mlups = n_nodes * args.steps * ws / (ms / 1e3) / 1e6
+    es = 8 if args.precision == "fp64" else 4
+    hbm_gbs, peak_kind = peaks()
+    bytes_node = SCALARS_PER_NODE * es
+    k1_avg = k1_ms / max(k1_n, 1)
+    # the fused interior kernel dominates; its algorithmic units are the
+    # interior nodes it updates per launch
+    interior_nodes = n_nodes - L.wall_nodes()
+    ach_gbs = interior_nodes * bytes_node / (k1_avg / 1e3) / 1e9
+    ach_tf = interior_nodes * FLOPS_PER_NODE / (k1_avg / 1e3) / 1e12
+    hbm_frac = ach_gbs / hbm_gbs
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(ach_tf / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                "kernel": "k_step_interior<double>", "hbm_achieved_gbs": round(ach_gbs, 1),
+                "hbm_peak_gbs": hbm_gbs, "hbm_frac": round(hbm_frac, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(ach_gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel": "k_step_interior<float>"}
+    result = {
+        "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "precision": args.precision,
+                   "l2": f"state {2 * 27 * n_nodes * es / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "wall_nodes": int(L.wall_nodes())},
+        "hbm_roofline_pct": round(100 * mlups / ws * 1e6 * bytes_node / (hbm_gbs * 1e9), 2),
+        "roofline": roof,
+        "kernel_ms": {"interior_avg": round(k1_avg, 4), "wall_avg": round(k2_ms / max(k2_n, 1), 4)},
+        "gpu_launches": int(k1_n + k2_n),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_e2e:
+        result["e2e"] = e2e(L, w, args, torch, T)
+    if rank == 0:
+        variants = {}
+        for prec in [v for v in args.variants.split(",") if v and v != args.precision]:
+            V = T.lattice_from_workload(w, prec)
+            V.step(args.warmup)
+            V.sync()
+            vms = time_steps(V, args.steps, torch, stream)
+            v_mlups = n_nodes * args.steps / (vms / 1e3) / 1e6
+            ves = 8 if prec == "fp64" else 4
+            variants[prec] = {"value": round(v_mlups, 2), "unit": "MLUPS",
+                              "hbm_roofline_pct": round(100 * v_mlups * 1e6 * SCALARS_PER_NODE * ves / (hbm_gbs * 1e9), 2)}
+            del V
+        result["variants"] = variants
+        if not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(result), flush=True)
+    if D:
+        D.barrier()
+        D.destroy_process_group()
+
+
+def e2e(L, w, args, torch, T):
+    """Whole jobs through the public API: pinned host inputs -> set_fields ->
+    K steps -> read all fields into pinned host memory."""
+    n = w.nx * w.ny
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).pin_memory()
+    ins = [pin(a) for a in (w.c1, w.c2, w.ux, w.uy)]
+    out = torch.empty((10, w.ny, w.nx), dtype=torch.float64).pin_memory()
+    jobs = 2
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(jobs):
+        L.set_fields(*(t.numpy() for t in ins))
+        L.step(args.steps)
+        L.fields(out=out.numpy())
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(n * args.steps * jobs / dt / 1e6, 2), "unit": "MLUPS",
+            "h2d_bytes_per_step": int(4 * n * 8 / args.steps), "d2h_bytes_per_step": int(10 * n * 8 / args.steps),
+            "job": f"set_fields (4 FP64 planes H2D) + {args.steps} steps + read_fields (10 FP64 planes D2H)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * tlbm.h -- C ABI of the GB300 lattice library for the phase-field lattice
+ * Boltzmann ternary-fluid model with ternary wetting boundaries of
+ * Liang, Li, Shi and Chai, "Lattice Boltzmann modeling of wall-bounded ternary
+ * fluid flows" (arXiv:1710.09534), Sec. II.
+ *
+ * One call of tlb_step advances one D2Q9 lattice by n time steps on the
+ * caller's CUDA stream: two order-parameter distributions f^1, f^2 and one
+ * hydrodynamic distribution g (Eqs. 1a, 1b) with BGK collision, equilibria
+ * (Eqs. 2a, 2b, 4), sources (Eqs. 11a, 11b, 12, 19), moments (Eqs. 13-15),
+ * chemical potentials (Eqs. 8, 9) from the isotropic stencils (Eqs. 20a, 20b),
+ * the ternary wetting ghost values (Eq. 42), symmetric ghosts (Eq. 43),
+ * half-way bounce-back (Eq. 44) and the non-equilibrium-extrapolation velocity
+ * lid (Eqs. 51-53).
+ *
+ * Conventions shared by every call
+ *   - Node arrays are row-major [ny][nx] (x fastest); node (i, j) sits at
+ *     (x, y) = (i, j).  Host arrays are copied, never retained.
+ *   - Edges are given as int32 edges[4] = {left, right, bottom, top}, each one
+ *     of TLB_EDGE_*.  A periodic edge must be paired with a periodic opposite
+ *     edge.  Half-way walls sit half a spacing outside the lattice.  The lid is
+ *     allowed on the top edge only; it turns row ny-1 into the boundary row
+ *     x_u of Eq. 51, whose neighbour x_f is the node directly below.  At a
+ *     corner outside in both x and y, the x edge decides the kind of site.
+ *   - Readings of the paper that both this library and its FP64 oracle follow:
+ *     eta_i = M_i / (cs^2 (tau_i - 1/2)) per component with M_i = M0/lambda_i;
+ *     lambda_T = 3 l1 l2 l3 / (l1 l2 + l1 l3 + l2 l3); the Eq. 42 offset on
+ *     every solid link (axis or diagonal), used only for lap c_i inside mu_i;
+ *     a neutral wall is cos = 0; body force G = rho (gx, gy).
+ *   - Every call returns TLB_OK or a negative TLB_E* code and sets a
+ *     thread-local message readable with tlb_last_error().  No call aborts
+ *     or throws.  Device work is asynchronous on the stream given at creation
+ *     unless a call says that it synchronizes.
+ *   - Memory ownership: the caller allocates the device workspace
+ *     (tlb_workspace_bytes) and keeps it and the stream alive until
+ *     tlb_destroy.  The library itself never allocates device memory.
+ */
+#ifndef TLBM_H
+#define TLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tlb_lattice tlb_lattice;
+
+/* Storage precision of the distributions.  TLB_FP64 computes in FP64;
+ * TLB_FP32 stores and computes in FP32 (diagnostic sums in FP64). */
+enum { TLB_FP64 = 0, TLB_FP32 = 1 };
+
+enum { TLB_EDGE_PERIODIC = 0, TLB_EDGE_WETTING = 1, TLB_EDGE_NEUTRAL = 2, TLB_EDGE_LID = 3 };
+
+/* Solid mask values for tlb_set_geometry. */
+enum { TLB_NODE_FLUID = 0, TLB_NODE_WETTING_SOLID = 1, TLB_NODE_NEUTRAL_SOLID = 2 };
+
+enum {
+    TLB_OK = 0,
+    TLB_EINVAL = -1,    /* invalid argument or parameter set */
+    TLB_ENOMEM = -2,    /* workspace too small */
+    TLB_ECUDA = -3,     /* a CUDA runtime call failed (message has the CUDA error) */
+    TLB_EUNSTABLE = -4, /* non-finite values found in the state */
+    TLB_ETIMEOUT = -5,  /* tlb_sync deadline passed with work still pending */
+    TLB_ESTATE = -6     /* call out of order (e.g. step before set_fields) */
+};
+
+/* Field selection bits for tlb_read_fields; planes are written in bit order. */
+enum {
+    TLB_F_C1 = 1u << 0, TLB_F_C2 = 1u << 1, TLB_F_C3 = 1u << 2, TLB_F_RHO = 1u << 3,
+    TLB_F_UX = 1u << 4, TLB_F_UY = 1u << 5, TLB_F_P = 1u << 6, TLB_F_MU1 = 1u << 7,
+    TLB_F_MU2 = 1u << 8, TLB_F_MU3 = 1u << 9, TLB_F_ALL = (1u << 10) - 1u
+};
+
+/* Model parameters (Sec. II).  sigma_ij: surface tensions (Eq. 7);
+ * theta_ij: static contact angles measured through fluid i (Eq. 38), which
+ * must satisfy Eq. 39; rho_i, nu_i: phase densities and viscosities (Eqs. 14,
+ * 15); M0: M_i = M0 / lambda_i (Eq. 12); D: interface thickness (Eq. 8);
+ * tau1, tau2: relaxation times of Eq. 1a; gx, gy: body force per unit mass;
+ * lid_u: U0 of Eq. 53 for a TLB_EDGE_LID top edge. */
+typedef struct {
+    double sigma12, sigma13, sigma23;
+    double theta12_deg, theta13_deg, theta23_deg;
+    double rho1, rho2, rho3;
+    double nu1, nu2, nu3;
+    double M0;
+    double D;
+    double tau1, tau2;
+    double gx, gy;
+    double lid_u;
+} tlb_params;
+
+/* FP64 diagnostics of the current state (Sec. III.A measures; reduced on
+ * the device in a fixed order).  mass[i] = sum over fluid nodes of c_{i+1}
+ * (the lid row counts with the values of the row below it); nonfinite =
+ * number of fluid nodes whose c1, c2 or g-moments are not finite. */
+typedef struct {
+    double mass[3];
+    int64_t nonfinite;
+} tlb_diag;
+
+/* Bytes of device workspace one lattice needs (the state of Eqs. 1a/1b
+ * double-buffered, the c_i u planes of Eq. 19, node classes and the near-wall
+ * list).  Returns a negative TLB_E* code for invalid sizes or precision. */
+int64_t tlb_workspace_bytes(int nx, int ny, int precision);
+
+/* Create a lattice of nx*ny nodes (nx, ny >= 3 and <= 32768).  dev_workspace:
+ * caller-owned device memory of at least tlb_workspace_bytes, 256-byte aligned.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  *out receives
+ * the handle.  The lattice starts all-fluid; parameters and fields must be set
+ * before stepping. */
+int tlb_create_lattice(int nx, int ny, int precision, const int32_t edges[4],
+                       void *dev_workspace, int64_t ws_bytes, void *cuda_stream,
+                       tlb_lattice **out);
+
+/* Solid geometry: host_mask[ny*nx] of TLB_NODE_* values (NULL = all fluid).
+ * A solid node is never updated; its fluid neighbours use the wetting ghost
+ * rule (Eq. 42, wetting solids) or the symmetric rule (neutral solids) and
+ * bounce back on links into it (Eq. 44).  With a lid, rows ny-2 and ny-1 must
+ * be fluid.  Builds the node classes and the compacted near-wall list on the
+ * host and uploads them (synchronizes the stream).  Must be followed by
+ * tlb_set_fields before the next step. */
+int tlb_set_geometry(tlb_lattice *lat, const uint8_t *host_mask);
+
+/* Model parameters.  TLB_EINVAL if: any sigma_ij <= 0, lambda_1 or lambda_2
+ * <= 0, lambda_3 < 0 (Eq. 7); D <= 0; rho_i <= 0; nu_i <= 0; tau_i <= 1/2;
+ * M0 <= 0; the Eq. 39 residual |s12 cos t12 - s13 cos t13 + s23 cos t23| >
+ * 1e-6 max(sigma); a non-finite value.  lambda_i <= lambda_T / 2 (outside the
+ * well-posed range stated after Eq. 7) is accepted; the message then says so. */
+int tlb_set_params(tlb_lattice *lat, const tlb_params *params);
+
+/* Initial state from host node arrays (length nx*ny each; p may be NULL for
+ * p = 0): f^i = f^{i,eq}(c_i, mu_i(c), u) (Eq. 2a with mu from Eq. 8),
+ * g = g^eq(p, rho(c), u) (Eq. 2b), stored c_i u = c_i u (so the first Eq. 19
+ * derivative is zero for a still start).  Solid nodes get zero.  The lid row
+ * takes c and mu from the row below.  Synchronizes the stream. */
+int tlb_set_fields(tlb_lattice *lat, const double *c1, const double *c2, const double *ux,
+                   const double *uy, const double *p);
+
+/* The same from device FP64 arrays (length nx*ny each, p may be NULL);
+ * asynchronous; the arrays must stay valid until the stream reaches it. */
+int tlb_set_fields_device(tlb_lattice *lat, const double *c1, const double *c2,
+                          const double *ux, const double *uy, const double *p);
+
+/* Advance n >= 0 time steps, asynchronously on the stream: per step one fused
+ * interior kernel and one near-wall kernel.  TLB_ESTATE before set_fields. */
+int tlb_step(tlb_lattice *lat, int64_t n);
+
+/* Wait for the stream with a deadline (timeout_ms < 0: no deadline).
+ * TLB_ETIMEOUT if work is still pending at the deadline (nothing is
+ * cancelled), TLB_ECUDA if the stream reported an error. */
+int tlb_sync(tlb_lattice *lat, int64_t timeout_ms);
+
+/* Macroscopic fields of the current state as FP64 planes of nx*ny, in the
+ * order of the set bits of field_mask (TLB_F_*): c1, c2, c3, rho, ux, uy, p,
+ * mu1, mu2, mu3.  Solid nodes read 0; the lid row reads the row below it with
+ * u = (U0, 0).  host_out receives popcount(field_mask)*nx*ny doubles.
+ * Synchronizes the stream. */
+int tlb_read_fields(tlb_lattice *lat, uint32_t field_mask, double *host_out);
+
+/* The same into device memory (dev_out: popcount(field_mask)*nx*ny doubles);
+ * asynchronous. */
+int tlb_read_fields_device(tlb_lattice *lat, uint32_t field_mask, double *dev_out);
+
+/* FP64 mass totals and non-finite count (see tlb_diag); synchronizes.
+ * Returns TLB_EUNSTABLE (with *out filled) if nonfinite > 0. */
+int tlb_diagnostics(tlb_lattice *lat, tlb_diag *out);
+
+/* Raw state as FP64 host planes [31][ny][nx]: f^1_k (k = 0..8), f^2_k,
+ * g_k, then c1 ux, c1 uy, c2 ux, c2 uy of the previous step (Eq. 19).
+ * Synchronizes. */
+int tlb_read_state(tlb_lattice *lat, double *host_out);
+
+/* Checkpoint: bytes needed, export into a host buffer and import from one
+ * (the exact storage-precision state, so a resumed run is bit-identical).
+ * Both synchronize.  Import requires a lattice of the same size, precision,
+ * edges and geometry (TLB_EINVAL on a size mismatch). */
+int64_t tlb_state_bytes(tlb_lattice *lat);
+int tlb_export_state(tlb_lattice *lat, void *host_buf, int64_t bytes);
+int tlb_import_state(tlb_lattice *lat, const void *host_buf, int64_t bytes);
+
+/* theta_12 from Eq. 39 given the tensions, theta_13 and theta_23 (degrees):
+ * the paper's convention when the two fluid-3 angles are prescribed
+ * (Sec. III.A).  TLB_EINVAL if no angle satisfies it. */
+int tlb_theta12_from(double sigma12, double sigma13, double sigma23, double theta13_deg,
+                     double theta23_deg, double *theta12_deg);
+
+/* Per-kernel timing with CUDA events on the lattice's stream.  enable = 1
+ * starts recording events around the fused interior launch and the
+ * near-wall launch of every step (and clears the totals); enable = 0 stops.
+ * tlb_profile_read synchronizes and returns the summed device milliseconds
+ * ms[0] (interior kernel), ms[1] (near-wall kernel) and the launch counts. */
+int tlb_profile(tlb_lattice *lat, int enable);
+int tlb_profile_read(tlb_lattice *lat, double ms[2], int64_t launches[2]);
+
+/* Number of nodes in the near-wall list (handled by the near-wall kernel). */
+int64_t tlb_wall_nodes(tlb_lattice *lat);
+
+/* Release the host handle (the workspace stays the caller's). */
+void tlb_destroy(tlb_lattice *lat);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *tlb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TLBM_H */

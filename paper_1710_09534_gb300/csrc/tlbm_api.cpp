@@ -1,0 +1,618 @@
+// C ABI of the lattice library (declared in include/tlbm.h): argument
+// validation, derived parameters (Eqs. 7, 9, 12, 18a, 38), geometry
+// classification and the compacted near-wall list, workspace carving, and the
+// per-step launches on the caller's stream.
+#include "tlbm.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "tlbm_ops.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int ok()
+{
+    g_err.clear();
+    return TLB_OK;
+}
+
+#define TLB_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(TLB_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));           \
+    } while (0)
+
+constexpr int64_t kAlign = 256;
+constexpr int kMassParts = 608;  // 4 x 152 SMs
+
+int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    int pitch = 0;
+    int64_t plane = 0;  // elements
+    int64_t fA = 0, fB = 0, cu = 0, cls = 0, list = 0, part = 0, diag = 0, total = 0;
+};
+
+bool precision_ok(int precision) { return precision == TLB_FP64 || precision == TLB_FP32; }
+
+size_t elem_size(int precision) { return precision == TLB_FP64 ? 8 : 4; }
+
+Layout layout_for(int nx, int ny, int precision)
+{
+    Layout L;
+    L.pitch = (int)align_up(nx, 32);
+    L.plane = (int64_t)L.pitch * ny;
+    const int64_t es = (int64_t)elem_size(precision);
+    int64_t off = 0;
+    auto take = [&](int64_t bytes) {
+        const int64_t at = off;
+        off = align_up(off + bytes, kAlign);
+        return at;
+    };
+    L.fA = take(27 * L.plane * es);
+    L.fB = take(27 * L.plane * es);
+    L.cu = take(4 * L.plane * es);
+    L.cls = take(L.plane);
+    L.list = take((int64_t)nx * ny * 4);
+    L.part = take((int64_t)kMassParts * 4 * 8);
+    L.diag = take(4 * 8);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct tlb_lattice {
+    int nx = 0, ny = 0, precision = 0, device = 0;
+    int32_t edge[4] = {0, 0, 0, 0};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    char* ws = nullptr;
+    Layout lay;
+    const tlb::Ops* ops = nullptr;
+    tlb::Geo geo{};
+    tlb::Prm<double> prm{};
+    int cur = 0;  // which of the two distribution buffers holds the state
+    bool have_params = false, have_fields = false;
+    std::vector<uint8_t> mask;    // host copy of the solid mask
+    std::vector<uint8_t> cls;     // host copy of the node classes (pitched)
+    int64_t nlist = 0;
+    // optional per-kernel timing: event triples around the two launches of a step
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    double prof_ms[2] = {0, 0};
+    int64_t prof_n[2] = {0, 0};
+
+    void* bufA() { return ws + (cur == 0 ? lay.fA : lay.fB); }
+    void* bufB() { return ws + (cur == 0 ? lay.fB : lay.fA); }
+    void* cu() { return ws + lay.cu; }
+    const uint8_t* dcls() { return (const uint8_t*)(ws + lay.cls); }
+    const uint32_t* dlist() { return (const uint32_t*)(ws + lay.list); }
+    int64_t n() const { return (int64_t)nx * ny; }
+};
+
+namespace {
+
+// Site classification with the same semantics as the device site_of().
+int host_site(const tlb_lattice* L, int x, int y, int64_t* idx)
+{
+    if (x < 0 || x >= L->nx) {
+        const int e = L->edge[x < 0 ? 0 : 1];
+        if (e != TLB_EDGE_PERIODIC) return e == TLB_EDGE_WETTING ? tlb::ST_WET : tlb::ST_NEUTRAL;
+        x = x < 0 ? x + L->nx : x - L->nx;
+    }
+    if (y < 0 || y >= L->ny) {
+        const int e = L->edge[y < 0 ? 2 : 3];
+        if (e == TLB_EDGE_LID) return tlb::ST_VOID;
+        if (e != TLB_EDGE_PERIODIC) return e == TLB_EDGE_WETTING ? tlb::ST_WET : tlb::ST_NEUTRAL;
+        y = y < 0 ? y + L->ny : y - L->ny;
+    }
+    const int64_t i = (int64_t)y * L->nx + x;
+    if (idx) *idx = i;
+    if (L->mask[i] == TLB_NODE_WETTING_SOLID) return tlb::ST_WET;
+    if (L->mask[i] == TLB_NODE_NEUTRAL_SOLID) return tlb::ST_NEUTRAL;
+    if (L->edge[3] == TLB_EDGE_LID && y == L->ny - 1) return tlb::ST_LID;
+    return tlb::ST_FLUID;
+}
+
+// Node classes and the near-wall list from the host mask; uploads both.
+int build_geometry(tlb_lattice* L)
+{
+    const int nx = L->nx, ny = L->ny, pitch = L->lay.pitch;
+    L->cls.assign((size_t)L->lay.plane, (uint8_t)tlb::ST_NEUTRAL);
+    std::vector<uint32_t> list;
+    list.reserve((size_t)nx * 4);
+    for (int y = 0; y < ny; y++) {
+        for (int x = 0; x < nx; x++) {
+            const int kind = host_site(L, x, y, nullptr);
+            uint8_t c = (uint8_t)kind;
+            if (kind == tlb::ST_FLUID) {
+                bool interior = true;
+                for (int dy = -2; dy <= 2 && interior; dy++)
+                    for (int dx = -2; dx <= 2 && interior; dx++)
+                        if (host_site(L, x + dx, y + dy, nullptr) != tlb::ST_FLUID) interior = false;
+                if (interior) c |= tlb::CLS_INTERIOR;
+            }
+            L->cls[(size_t)y * pitch + x] = c;
+            if ((kind == tlb::ST_FLUID || kind == tlb::ST_LID) && !(c & tlb::CLS_INTERIOR))
+                list.push_back(((uint32_t)y << 16) | (uint32_t)x);
+        }
+    }
+    L->nlist = (int64_t)list.size();
+    TLB_CUDA(cudaMemcpyAsync(L->ws + L->lay.cls, L->cls.data(), L->cls.size(), cudaMemcpyHostToDevice,
+                             L->stream));
+    if (!list.empty())
+        TLB_CUDA(cudaMemcpyAsync(L->ws + L->lay.list, list.data(), list.size() * 4, cudaMemcpyHostToDevice,
+                                 L->stream));
+    TLB_CUDA(cudaStreamSynchronize(L->stream));
+    return TLB_OK;
+}
+
+constexpr int kProfSlots = 512;
+
+// Fold the recorded event triples into the per-kernel totals (synchronizes).
+int prof_fold(tlb_lattice* L)
+{
+    if (L->ev_used == 0) return TLB_OK;
+    TLB_CUDA(cudaEventSynchronize(L->ev[3 * (L->ev_used - 1) + 2]));
+    for (int i = 0; i < L->ev_used; i++) {
+        float a = 0, b = 0;
+        TLB_CUDA(cudaEventElapsedTime(&a, L->ev[3 * i], L->ev[3 * i + 1]));
+        TLB_CUDA(cudaEventElapsedTime(&b, L->ev[3 * i + 1], L->ev[3 * i + 2]));
+        L->prof_ms[0] += a;
+        L->prof_ms[1] += b;
+        L->prof_n[0] += 1;
+        L->prof_n[1] += L->nlist > 0 ? 1 : 0;
+    }
+    L->ev_used = 0;
+    return TLB_OK;
+}
+
+int check_handle(tlb_lattice* L)
+{
+    if (!L) return fail(TLB_EINVAL, "null lattice handle");
+    TLB_CUDA(cudaSetDevice(L->device));
+    return TLB_OK;
+}
+
+bool finite_all(const tlb_params* p)
+{
+    const double* v = (const double*)p;
+    for (size_t i = 0; i < sizeof(tlb_params) / sizeof(double); i++)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+int popcount10(uint32_t m)
+{
+    int c = 0;
+    for (int q = 0; q < 10; q++) c += (m >> q) & 1u;
+    return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t tlb_workspace_bytes(int nx, int ny, int precision)
+{
+    if (nx < 3 || ny < 3 || nx > 32768 || ny > 32768) return fail(TLB_EINVAL, "lattice size %dx%d out of range", nx, ny);
+    if (!precision_ok(precision)) return fail(TLB_EINVAL, "unknown precision %d", precision);
+    ok();
+    return layout_for(nx, ny, precision).total;
+}
+
+int tlb_create_lattice(int nx, int ny, int precision, const int32_t edges[4], void* dev_workspace,
+                       int64_t ws_bytes, void* cuda_stream, tlb_lattice** out)
+{
+    if (!out) return fail(TLB_EINVAL, "out is null");
+    *out = nullptr;
+    if (nx < 3 || ny < 3 || nx > 32768 || ny > 32768) return fail(TLB_EINVAL, "lattice size %dx%d out of range", nx, ny);
+    if (!precision_ok(precision)) return fail(TLB_EINVAL, "unknown precision %d", precision);
+    if (!edges) return fail(TLB_EINVAL, "edges is null");
+    for (int e = 0; e < 4; e++)
+        if (edges[e] < TLB_EDGE_PERIODIC || edges[e] > TLB_EDGE_LID) return fail(TLB_EINVAL, "edge %d: bad kind %d", e, edges[e]);
+    if ((edges[0] == TLB_EDGE_PERIODIC) != (edges[1] == TLB_EDGE_PERIODIC))
+        return fail(TLB_EINVAL, "left/right edges: periodic must be paired");
+    if ((edges[2] == TLB_EDGE_PERIODIC) != (edges[3] == TLB_EDGE_PERIODIC))
+        return fail(TLB_EINVAL, "bottom/top edges: periodic must be paired");
+    if (edges[0] == TLB_EDGE_LID || edges[1] == TLB_EDGE_LID || edges[2] == TLB_EDGE_LID)
+        return fail(TLB_EINVAL, "a velocity lid is supported on the top edge only");
+    if (edges[3] == TLB_EDGE_LID && ny < 6) return fail(TLB_EINVAL, "a lid needs ny >= 6");
+    const Layout lay = layout_for(nx, ny, precision);
+    if (!dev_workspace) return fail(TLB_EINVAL, "workspace is null");
+    if (((uintptr_t)dev_workspace) % kAlign) return fail(TLB_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < lay.total)
+        return fail(TLB_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_bytes, (long long)lay.total);
+    auto* L = new tlb_lattice;
+    L->nx = nx;
+    L->ny = ny;
+    L->precision = precision;
+    for (int e = 0; e < 4; e++) L->edge[e] = edges[e];
+    L->stream = (cudaStream_t)cuda_stream;
+    L->ws = (char*)dev_workspace;
+    L->lay = lay;
+    L->ops = precision == TLB_FP64 ? &tlb::ops_f64() : &tlb::ops_f32();
+    L->geo.nx = nx;
+    L->geo.ny = ny;
+    L->geo.pitch = lay.pitch;
+    L->geo.plane = lay.plane;
+    for (int e = 0; e < 4; e++) L->geo.edge[e] = edges[e];
+    L->mask.assign((size_t)nx * ny, 0);
+    cudaError_t e = cudaGetDevice(&L->device);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete L;
+        return fail(TLB_ECUDA, "device set-up failed: %s", cudaGetErrorString(e));
+    }
+    int rc = build_geometry(L);
+    if (rc == TLB_OK) {
+        cudaError_t z = cudaMemsetAsync(L->ws + lay.fA, 0, (size_t)(lay.cls - lay.fA), L->stream);
+        if (z == cudaSuccess) z = cudaStreamSynchronize(L->stream);
+        if (z != cudaSuccess) rc = fail(TLB_ECUDA, "workspace clear failed: %s", cudaGetErrorString(z));
+    }
+    if (rc != TLB_OK) {
+        cudaEventDestroy(L->done);
+        delete L;
+        return rc;
+    }
+    *out = L;
+    return ok();
+}
+
+int tlb_set_geometry(tlb_lattice* L, const uint8_t* host_mask)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    std::vector<uint8_t> m((size_t)L->n(), 0);
+    if (host_mask) {
+        for (int64_t i = 0; i < L->n(); i++) {
+            if (host_mask[i] > TLB_NODE_NEUTRAL_SOLID) return fail(TLB_EINVAL, "mask value %d at node %lld", host_mask[i], (long long)i);
+            m[i] = host_mask[i];
+        }
+    }
+    if (L->edge[3] == TLB_EDGE_LID) {
+        for (int y = L->ny - 2; y < L->ny; y++)
+            for (int x = 0; x < L->nx; x++)
+                if (m[(size_t)y * L->nx + x]) return fail(TLB_EINVAL, "with a lid, rows ny-2 and ny-1 must be fluid");
+    }
+    L->mask.swap(m);
+    rc = build_geometry(L);
+    if (rc) return rc;
+    L->have_fields = false;
+    return ok();
+}
+
+int tlb_set_params(tlb_lattice* L, const tlb_params* p)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!p) return fail(TLB_EINVAL, "params is null");
+    if (!finite_all(p)) return fail(TLB_EINVAL, "non-finite parameter");
+    if (p->sigma12 <= 0 || p->sigma13 <= 0 || p->sigma23 <= 0) return fail(TLB_EINVAL, "surface tensions must be > 0");
+    const double l1 = p->sigma12 + p->sigma13 - p->sigma23;
+    const double l2 = p->sigma12 + p->sigma23 - p->sigma13;
+    const double l3 = p->sigma13 + p->sigma23 - p->sigma12;
+    if (l1 <= 0 || l2 <= 0 || l3 < 0) return fail(TLB_EINVAL, "Eq. 7 gives lambda = (%g, %g, %g): need l1, l2 > 0, l3 >= 0", l1, l2, l3);
+    if (p->D <= 0) return fail(TLB_EINVAL, "D must be > 0");
+    if (p->rho1 <= 0 || p->rho2 <= 0 || p->rho3 <= 0) return fail(TLB_EINVAL, "densities must be > 0");
+    if (p->nu1 <= 0 || p->nu2 <= 0 || p->nu3 <= 0) return fail(TLB_EINVAL, "viscosities must be > 0");
+    if (p->tau1 <= 0.5 || p->tau2 <= 0.5) return fail(TLB_EINVAL, "tau_i must be > 1/2");
+    if (p->M0 <= 0) return fail(TLB_EINVAL, "M0 must be > 0");
+    const double deg = 3.14159265358979323846 / 180.0;
+    const double c12 = std::cos(p->theta12_deg * deg), c13 = std::cos(p->theta13_deg * deg),
+                 c23 = std::cos(p->theta23_deg * deg);
+    const double smax = std::fmax(p->sigma12, std::fmax(p->sigma13, p->sigma23));
+    const double resid = p->sigma12 * c12 - p->sigma13 * c13 + p->sigma23 * c23;
+    if (std::fabs(resid) > 1e-6 * smax)
+        return fail(TLB_EINVAL, "contact angles violate Eq. 39 (residual %g)", resid);
+    const double den = l1 * l2 + l1 * l3 + l2 * l3;
+    const double lT = den != 0 ? 3.0 * l1 * l2 * l3 / den : 0.0;
+    tlb::Prm<double>& P = L->prm;
+    P.lam[0] = l1;
+    P.lam[1] = l2;
+    P.lam[2] = l3;
+    P.lamT = lT;
+    P.k12D = 12.0 / p->D;
+    P.k34D = 0.75 * p->D;
+    P.k4D = 4.0 / p->D;
+    const double tau[2] = {p->tau1, p->tau2};
+    const double M[2] = {p->M0 / l1, p->M0 / l2};
+    for (int i = 0; i < 2; i++) {
+        P.eta[i] = M[i] / ((1.0 / 3.0) * (tau[i] - 0.5));
+        P.inv_tau[i] = 1.0 / tau[i];
+        P.src_f[i] = 3.0 * (1.0 - 0.5 / tau[i]);
+    }
+    P.rho[0] = p->rho1;
+    P.rho[1] = p->rho2;
+    P.rho[2] = p->rho3;
+    P.nu[0] = p->nu1;
+    P.nu[1] = p->nu2;
+    P.nu[2] = p->nu3;
+    P.aM[0] = (p->rho1 - p->rho3) * M[0];
+    P.aM[1] = (p->rho2 - p->rho3) * M[1];
+    P.l3_l1 = l3 / l1;
+    P.l3_l2 = l3 / l2;
+    P.cos12 = c12;
+    P.cos13 = c13;
+    P.cos23 = c23;
+    P.gx = p->gx;
+    P.gy = p->gy;
+    P.lid_u = p->lid_u;
+    L->have_params = true;
+    L->have_fields = false;
+    g_err.clear();
+    if (l1 <= 0.5 * lT || l2 <= 0.5 * lT || l3 <= 0.5 * lT)
+        g_err = "warning: some lambda_i <= lambda_T / 2 (outside the well-posed range of the bulk free energy)";
+    return TLB_OK;
+}
+
+static int set_fields_impl(tlb_lattice* L, const double* c1, const double* c2, const double* ux,
+                           const double* uy, const double* p)
+{
+    TLB_CUDA(L->ops->init(L->bufA(), L->cu(), L->dcls(), c1, c2, ux, uy, p, L->geo, L->prm, L->stream));
+    L->have_fields = true;
+    return TLB_OK;
+}
+
+int tlb_set_fields(tlb_lattice* L, const double* c1, const double* c2, const double* ux, const double* uy,
+                   const double* p)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!L->have_params) return fail(TLB_ESTATE, "set_params first");
+    if (!c1 || !c2 || !ux || !uy) return fail(TLB_EINVAL, "c1, c2, ux, uy are required");
+    // stage the inputs in the spare distribution buffer, build the state,
+    // then clear the spare buffer (solid nodes and lid slots must read zero)
+    const size_t N = (size_t)L->n();
+    double* stage = (double*)L->bufB();
+    const double* src[5] = {c1, c2, ux, uy, p};
+    for (int q = 0; q < 5; q++)
+        if (src[q]) TLB_CUDA(cudaMemcpyAsync(stage + q * N, src[q], N * 8, cudaMemcpyHostToDevice, L->stream));
+    rc = set_fields_impl(L, stage, stage + N, stage + 2 * N, stage + 3 * N, p ? stage + 4 * N : nullptr);
+    if (rc) return rc;
+    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(27 * L->lay.plane * L->ops->elem), L->stream));
+    TLB_CUDA(cudaStreamSynchronize(L->stream));
+    return ok();
+}
+
+int tlb_set_fields_device(tlb_lattice* L, const double* c1, const double* c2, const double* ux,
+                          const double* uy, const double* p)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!L->have_params) return fail(TLB_ESTATE, "set_params first");
+    if (!c1 || !c2 || !ux || !uy) return fail(TLB_EINVAL, "c1, c2, ux, uy are required");
+    rc = set_fields_impl(L, c1, c2, ux, uy, p);
+    if (rc) return rc;
+    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(27 * L->lay.plane * L->ops->elem), L->stream));
+    return ok();
+}
+
+int tlb_step(tlb_lattice* L, int64_t n)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (n < 0) return fail(TLB_EINVAL, "negative step count");
+    if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "set_params and set_fields before step");
+    for (int64_t s = 0; s < n; s++) {
+        if (L->prof) {
+            if (L->ev_used == kProfSlots && (rc = prof_fold(L))) return rc;
+            TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used], L->stream));
+        }
+        TLB_CUDA(L->ops->interior(L->bufA(), L->bufB(), L->cu(), L->dcls(), L->geo, L->prm, L->stream));
+        if (L->prof) TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used + 1], L->stream));
+        TLB_CUDA(L->ops->wall(L->bufA(), L->bufB(), L->cu(), L->dcls(), L->dlist(), (int)L->nlist, L->geo,
+                              L->prm, L->stream));
+        if (L->prof) {
+            TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used + 2], L->stream));
+            L->ev_used++;
+        }
+        L->cur ^= 1;
+    }
+    return ok();
+}
+
+int tlb_sync(tlb_lattice* L, int64_t timeout_ms)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    TLB_CUDA(cudaEventRecord(L->done, L->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(L->done);
+        if (e == cudaSuccess) return ok();
+        if (e != cudaErrorNotReady) return fail(TLB_ECUDA, "stream error: %s", cudaGetErrorString(e));
+        if (timeout_ms >= 0) {
+            const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (ms >= timeout_ms) return fail(TLB_ETIMEOUT, "work still pending after %lld ms", (long long)timeout_ms);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+int tlb_read_fields_device(tlb_lattice* L, uint32_t mask, double* dev_out)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "no state yet");
+    if (!dev_out || (mask & ~(uint32_t)TLB_F_ALL) || !mask) return fail(TLB_EINVAL, "bad output or field mask");
+    TLB_CUDA(L->ops->read(L->bufA(), L->dcls(), dev_out, mask, L->geo, L->prm, L->stream));
+    return ok();
+}
+
+int tlb_read_fields(tlb_lattice* L, uint32_t mask, double* host_out)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "no state yet");
+    if (!host_out || (mask & ~(uint32_t)TLB_F_ALL) || !mask) return fail(TLB_EINVAL, "bad output or field mask");
+    const size_t N = (size_t)L->n();
+    double* stage = (double*)L->bufB();
+    TLB_CUDA(L->ops->read(L->bufA(), L->dcls(), stage, mask, L->geo, L->prm, L->stream));
+    TLB_CUDA(cudaMemcpyAsync(host_out, stage, (size_t)popcount10(mask) * N * 8, cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(27 * L->lay.plane * L->ops->elem), L->stream));
+    TLB_CUDA(cudaStreamSynchronize(L->stream));
+    return ok();
+}
+
+int tlb_diagnostics(tlb_lattice* L, tlb_diag* out)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!out) return fail(TLB_EINVAL, "out is null");
+    if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "no state yet");
+    double* part = (double*)(L->ws + L->lay.part);
+    double* dout = (double*)(L->ws + L->lay.diag);
+    TLB_CUDA(L->ops->mass(L->bufA(), L->dcls(), part, kMassParts, dout, L->geo, L->stream));
+    double h[4];
+    TLB_CUDA(cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaStreamSynchronize(L->stream));
+    out->mass[0] = h[0];
+    out->mass[1] = h[1];
+    out->mass[2] = h[2];
+    out->nonfinite = (int64_t)h[3];
+    if (out->nonfinite > 0) return fail(TLB_EUNSTABLE, "%lld fluid nodes hold non-finite values", (long long)out->nonfinite);
+    return ok();
+}
+
+int tlb_read_state(tlb_lattice* L, double* host_out)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!host_out) return fail(TLB_EINVAL, "out is null");
+    const size_t es = L->ops->elem, PL = (size_t)L->lay.plane;
+    std::vector<char> raw(31 * PL * es);
+    TLB_CUDA(cudaMemcpyAsync(raw.data(), L->bufA(), 27 * PL * es, cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaMemcpyAsync(raw.data() + 27 * PL * es, L->cu(), 4 * PL * es, cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaStreamSynchronize(L->stream));
+    const size_t N = (size_t)L->n();
+    for (int q = 0; q < 31; q++)
+        for (int y = 0; y < L->ny; y++)
+            for (int x = 0; x < L->nx; x++) {
+                const size_t src = q * PL + (size_t)y * L->lay.pitch + x;
+                double v;
+                if (es == 8) memcpy(&v, raw.data() + src * 8, 8);
+                else {
+                    float f;
+                    memcpy(&f, raw.data() + src * 4, 4);
+                    v = f;
+                }
+                host_out[q * N + (size_t)y * L->nx + x] = v;
+            }
+    return ok();
+}
+
+int64_t tlb_state_bytes(tlb_lattice* L)
+{
+    if (!L) return fail(TLB_EINVAL, "null lattice handle");
+    return 31 * L->lay.plane * (int64_t)L->ops->elem;
+}
+
+int tlb_export_state(tlb_lattice* L, void* host_buf, int64_t bytes)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    const int64_t need = tlb_state_bytes(L);
+    if (!host_buf || bytes < need) return fail(TLB_EINVAL, "buffer needs %lld bytes", (long long)need);
+    const size_t a = 27 * (size_t)L->lay.plane * L->ops->elem;
+    TLB_CUDA(cudaMemcpyAsync(host_buf, L->bufA(), a, cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaMemcpyAsync((char*)host_buf + a, L->cu(), (size_t)need - a, cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaStreamSynchronize(L->stream));
+    return ok();
+}
+
+int tlb_import_state(tlb_lattice* L, const void* host_buf, int64_t bytes)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    const int64_t need = tlb_state_bytes(L);
+    if (!host_buf || bytes != need) return fail(TLB_EINVAL, "state must be exactly %lld bytes", (long long)need);
+    if (!L->have_params) return fail(TLB_ESTATE, "set_params first");
+    const size_t a = 27 * (size_t)L->lay.plane * L->ops->elem;
+    TLB_CUDA(cudaMemcpyAsync(L->bufA(), host_buf, a, cudaMemcpyHostToDevice, L->stream));
+    TLB_CUDA(cudaMemcpyAsync(L->cu(), (const char*)host_buf + a, (size_t)need - a, cudaMemcpyHostToDevice, L->stream));
+    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, a, L->stream));
+    TLB_CUDA(cudaStreamSynchronize(L->stream));
+    L->have_fields = true;
+    return ok();
+}
+
+int tlb_theta12_from(double s12, double s13, double s23, double th13, double th23, double* th12)
+{
+    if (!th12 || s12 <= 0) return fail(TLB_EINVAL, "bad arguments");
+    const double deg = 3.14159265358979323846 / 180.0;
+    const double c = (s13 * std::cos(th13 * deg) - s23 * std::cos(th23 * deg)) / s12;
+    if (!(std::fabs(c) <= 1.0)) return fail(TLB_EINVAL, "no theta_12 satisfies Eq. 39 (cos = %g)", c);
+    *th12 = std::acos(c) / deg;
+    return ok();
+}
+
+int64_t tlb_wall_nodes(tlb_lattice* L)
+{
+    if (!L) return fail(TLB_EINVAL, "null lattice handle");
+    return L->nlist;
+}
+
+int tlb_profile(tlb_lattice* L, int enable)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (enable && L->ev.empty()) {
+        L->ev.resize(3 * kProfSlots);
+        for (auto& e : L->ev) TLB_CUDA(cudaEventCreate(&e));
+    }
+    if (!enable && (rc = prof_fold(L))) return rc;
+    L->prof = enable != 0;
+    L->prof_ms[0] = L->prof_ms[1] = 0;
+    L->prof_n[0] = L->prof_n[1] = 0;
+    L->ev_used = 0;
+    return ok();
+}
+
+int tlb_profile_read(tlb_lattice* L, double ms[2], int64_t launches[2])
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!ms || !launches) return fail(TLB_EINVAL, "null output");
+    if ((rc = prof_fold(L))) return rc;
+    for (int i = 0; i < 2; i++) {
+        ms[i] = L->prof_ms[i];
+        launches[i] = L->prof_n[i];
+    }
+    return ok();
+}
+
+void tlb_destroy(tlb_lattice* L)
+{
+    if (!L) return;
+    for (auto e : L->ev) cudaEventDestroy(e);
+    if (L->done) cudaEventDestroy(L->done);
+    delete L;
+}
+
+const char* tlb_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,569 @@
+// Kernels of one time step and of set-up / read-out, templated on the storage
+// type S and the arithmetic type R (double/double or float/float).
+//
+//   k_step_interior  fused stencil + collide + push for every node whose
+//                    5x5 neighbourhood is plain fluid (no wall, no lid):
+//                    c_1, c_2 on the tile plus a radius-2 halo from the local
+//                    sums of the pre-collision f (push streaming keeps them
+//                    local), mu_1, mu_2 on the tile plus radius 1 in shared
+//                    memory, then the per-node update.
+//   k_step_wall      the same update for the compacted list of the other
+//                    fluid nodes, with the ghost rules of Eqs. 42-43,
+//                    bounce-back (Eq. 44) and the lid (Eqs. 51-53).
+//   k_init, k_read_fields, k_mass_partials/k_mass_final, k_state_to_f64
+#pragma once
+#include <type_traits>
+#include "tlbm_device.cuh"
+
+namespace tlb {
+
+template <int K, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    if constexpr (K < N) {
+        f(std::integral_constant<int, K>{});
+        static_for<K + 1, N>(f);
+    }
+}
+
+template <typename S>
+__device__ __forceinline__ double to_d(S v) { return (double)v; }
+
+// Periodic wrap of a destination that may leave the lattice by one node on a
+// periodic axis (interior nodes never reach a non-periodic edge).
+__device__ __forceinline__ long long wrap_off(const Geo& g, int x, int y)
+{
+    x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+    y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+    return (long long)y * g.pitch + x;
+}
+
+// ---------------------------------------------------------------------------
+// K1: fused interior update.  Block = TX*TY threads, one node each.
+// ---------------------------------------------------------------------------
+template <typename S, typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+                const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
+{
+    constexpr int HX = TX + 4, HY = TY + 4;  // c tile, halo 2
+    constexpr int MX = TX + 2, MY = TY + 2;  // mu tile, halo 1
+    constexpr int NT = TX * TY;
+    __shared__ R sc1[HY * HX], sc2[HY * HX], sm1[MY * MX], sm2[MY * MX];
+
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const long long PL = g.plane;
+    const int tid = threadIdx.x;
+
+    // phase 1: c_i = sum_k f^i_k (Eq. 13a) on the tile + halo 2
+    for (int i = tid; i < HX * HY; i += NT) {
+        const int hx = i % HX, hy = i / HX;
+        int x = x0 - 2 + hx, y = y0 - 2 + hy;
+        R a = R(0), b = R(0);
+        // only x in [-2, nx+1], y in [-2, ny+1] are ever read; the rest of a
+        // tile that overhangs a small lattice is left at zero
+        bool inside = x < g.nx + 2 && y < g.ny + 2;
+        if (x < 0 || x >= g.nx) {
+            if (g.edge[0] == EDGE_PERIODIC) x = x < 0 ? x + g.nx : x - g.nx; else inside = false;
+        }
+        if (y < 0 || y >= g.ny) {
+            if (g.edge[2] == EDGE_PERIODIC) y = y < 0 ? y + g.ny : y - g.ny; else inside = false;
+        }
+        if (inside) {
+            const S* p = fA + (long long)y * g.pitch + x;
+#pragma unroll
+            for (int k = 0; k < 9; k++) a += R(ldg(p + k * PL));
+#pragma unroll
+            for (int k = 0; k < 9; k++) b += R(ldg(p + (9 + k) * PL));
+        }
+        sc1[i] = a;
+        sc2[i] = b;
+    }
+    __syncthreads();
+
+    // phase 2: mu_1, mu_2 (Eq. 8 with Eq. 20b) on the tile + halo 1
+    for (int i = tid; i < MX * MY; i += NT) {
+        const int mx = i % MX, my = i / MX;
+        const int c = (my + 1) * HX + (mx + 1);
+        R v1[9], v2[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            v1[k] = sc1[c + ey(k) * HX + ex(k)];
+            v2[k] = sc2[c + ey(k) * HX + ex(k)];
+        }
+        R mu1, mu2;
+        chem_pot(P, v1[0], v2[0], lap9(v1), lap9(v2), mu1, mu2);
+        sm1[i] = mu1;
+        sm2[i] = mu2;
+    }
+    __syncthreads();
+
+    // phase 3: per-node update
+    const int tx = tid % TX, ty = tid / TX;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= g.nx || y >= g.ny) return;
+    const long long o = (long long)y * g.pitch + x;
+    if (!(cls[o] & CLS_INTERIOR)) return;
+
+    Macro<R> m;
+    {
+        const int c = (ty + 2) * HX + (tx + 2);
+        const int cm = (ty + 1) * MX + (tx + 1);
+        R v1[9], v2[9], w1[9], w2[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            v1[k] = sc1[c + ey(k) * HX + ex(k)];
+            v2[k] = sc2[c + ey(k) * HX + ex(k)];
+            w1[k] = sm1[cm + ey(k) * MX + ex(k)];
+            w2[k] = sm2[cm + ey(k) * MX + ex(k)];
+        }
+        m.c1 = v1[0];
+        m.c2 = v2[0];
+        m.mu1 = w1[0];
+        m.mu2 = w2[0];
+        grad9(v1, m.g1x, m.g1y);
+        grad9(v2, m.g2x, m.g2y);
+        m.lm1 = lap9(w1);
+        m.lm2 = lap9(w2);
+        m.rho = m.c1 * P.rho[0] + m.c2 * P.rho[1] + (R(1) - m.c1 - m.c2) * P.rho[2];
+    }
+    R gv[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) gv[k] = R(ldg(fA + (18 + k) * PL + o));
+    Hydro<R> h;
+    hydro_from_g(P, m, gv, h);
+
+    // Eq. 19: d/dt (c_i u) from the stored previous product
+    const R c1ux = m.c1 * h.ux, c1uy = m.c1 * h.uy, c2ux = m.c2 * h.ux, c2uy = m.c2 * h.uy;
+    const R d1x = c1ux - R(cu[0 * PL + o]), d1y = c1uy - R(cu[1 * PL + o]);
+    const R d2x = c2ux - R(cu[2 * PL + o]), d2y = c2uy - R(cu[3 * PL + o]);
+    cu[0 * PL + o] = S(c1ux);
+    cu[1 * PL + o] = S(c1uy);
+    cu[2 * PL + o] = S(c2ux);
+    cu[3 * PL + o] = S(c2uy);
+
+    static_for<0, 9>([&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        const R f1k = R(ldg(fA + K * PL + o));
+        const R f2k = R(ldg(fA + (9 + K) * PL + o));
+        R o1, o2, og;
+        collide_k<K>(P, m, h, d1x, d1y, d2x, d2y, f1k, f2k, gv[K], o1, o2, og);
+        const long long d = (K == 0) ? o : wrap_off(g, x + ex(K), y + ey(K));
+        fB[K * PL + d] = S(o1);
+        fB[(9 + K) * PL + d] = S(o2);
+        fB[(18 + K) * PL + d] = S(og);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Generic per-node macros with the wall rules (5x5 window of c, 3x3 of mu).
+// CF(off, c1, c2) fetches the order parameters of an inside node.
+// ---------------------------------------------------------------------------
+template <typename R, typename CF>
+__device__ __forceinline__ void window_macros(const Geo& g, const uint8_t* __restrict__ cls, const Prm<R>& P,
+                                              int x, int y, CF cf, Macro<R>& m)
+{
+    R wc1[5][5], wc2[5][5];
+    int wk[5][5];
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            long long off = 0;
+            const int s = site_of(g, cls, x + i - 2, y + j - 2, off);
+            wk[j][i] = s;
+            R a = R(0), b = R(0);
+            if (s == ST_FLUID) cf(off, a, b);
+            wc1[j][i] = a;
+            wc2[j][i] = b;
+        }
+    }
+    // lid row: c is that of the node below (Eqs. 51-53 reading)
+#pragma unroll
+    for (int j = 1; j < 5; j++) {
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            if (wk[j][i] == ST_LID) {
+                wc1[j][i] = wc1[j - 1][i];
+                wc2[j][i] = wc2[j - 1][i];
+            }
+        }
+    }
+    // mu on the 3x3 around the node (Eq. 8), wetting ghosts of Eq. 42
+    R wm1[3][3], wm2[3][3];
+#pragma unroll
+    for (int j = 1; j < 4; j++) {
+#pragma unroll
+        for (int i = 1; i < 4; i++) {
+            R mu1 = R(0), mu2 = R(0);
+            if (wk[j][i] == ST_FLUID) {
+                const R cc1 = wc1[j][i], cc2 = wc2[j][i];
+                R o1, o2;
+                wet_offset(P, cc1, cc2, o1, o2);
+                R v1[9], v2[9];
+                v1[0] = cc1;
+                v2[0] = cc2;
+#pragma unroll
+                for (int k = 1; k < 9; k++) {
+                    const int s = wk[j + ey(k)][i + ex(k)];
+                    if (fluidlike(s)) {
+                        v1[k] = wc1[j + ey(k)][i + ex(k)];
+                        v2[k] = wc2[j + ey(k)][i + ex(k)];
+                    } else if (s == ST_WET) {
+                        v1[k] = cc1 + o1;
+                        v2[k] = cc2 + o2;
+                    } else {
+                        v1[k] = cc1;
+                        v2[k] = cc2;
+                    }
+                }
+                chem_pot(P, cc1, cc2, lap9(v1), lap9(v2), mu1, mu2);
+            }
+            wm1[j - 1][i - 1] = mu1;
+            wm2[j - 1][i - 1] = mu2;
+        }
+    }
+#pragma unroll
+    for (int j = 1; j < 3; j++) {
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            if (wk[j + 1][i + 1] == ST_LID) {
+                wm1[j][i] = wm1[j - 1][i];
+                wm2[j][i] = wm2[j - 1][i];
+            }
+        }
+    }
+    // gradients at the centre with symmetric ghosts (Eq. 43)
+    R v1[9], v2[9], w1[9], w2[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const int s = k == 0 ? ST_FLUID : wk[2 + ey(k)][2 + ex(k)];
+        const bool use = fluidlike(s);
+        v1[k] = use ? wc1[2 + ey(k)][2 + ex(k)] : wc1[2][2];
+        v2[k] = use ? wc2[2 + ey(k)][2 + ex(k)] : wc2[2][2];
+        w1[k] = use ? wm1[1 + ey(k)][1 + ex(k)] : wm1[1][1];
+        w2[k] = use ? wm2[1 + ey(k)][1 + ex(k)] : wm2[1][1];
+    }
+    m.c1 = wc1[2][2];
+    m.c2 = wc2[2][2];
+    m.mu1 = wm1[1][1];
+    m.mu2 = wm2[1][1];
+    grad9(v1, m.g1x, m.g1y);
+    grad9(v2, m.g2x, m.g2y);
+    m.lm1 = lap9(w1);
+    m.lm2 = lap9(w2);
+    m.rho = m.c1 * P.rho[0] + m.c2 * P.rho[1] + (R(1) - m.c1 - m.c2) * P.rho[2];
+}
+
+template <typename S, typename R>
+struct DistFetch {
+    const S* f;
+    long long PL;
+    __device__ __forceinline__ void operator()(long long off, R& a, R& b) const
+    {
+        R s1 = R(0), s2 = R(0);
+#pragma unroll
+        for (int k = 0; k < 9; k++) s1 += R(ldg(f + k * PL + off));
+#pragma unroll
+        for (int k = 0; k < 9; k++) s2 += R(ldg(f + (9 + k) * PL + off));
+        a = s1;
+        b = s2;
+    }
+};
+
+template <typename R>
+struct FieldFetch {
+    const double* c1;
+    const double* c2;
+    int nx, pitch;
+    __device__ __forceinline__ void operator()(long long off, R& a, R& b) const
+    {
+        const long long y = off / pitch, x = off - y * pitch;
+        a = R(c1[y * nx + x]);
+        b = R(c2[y * nx + x]);
+    }
+};
+
+// Push of one post-collision triple along direction K from node (x, y) with
+// the wall rules: into a fluid node, back into slot K-bar on a solid link
+// (Eq. 44), or out through the lid.
+template <int K, typename S, typename R>
+__device__ __forceinline__ void push_wall(const Geo& g, const uint8_t* __restrict__ cls, S* __restrict__ fB,
+                                          int x, int y, long long o, R o1, R o2, R og)
+{
+    const long long PL = g.plane;
+    if (K == 0) {
+        fB[o] = S(o1);
+        fB[9 * PL + o] = S(o2);
+        fB[18 * PL + o] = S(og);
+        return;
+    }
+    long long d = 0;
+    const int s = site_of(g, cls, x + ex(K), y + ey(K), d);
+    if (fluidlike(s)) {
+        fB[K * PL + d] = S(o1);
+        fB[(9 + K) * PL + d] = S(o2);
+        fB[(18 + K) * PL + d] = S(og);
+    } else if (s == ST_WET || s == ST_NEUTRAL) {
+        constexpr int KB = opp(K);
+        fB[KB * PL + o] = S(o1);
+        fB[(9 + KB) * PL + o] = S(o2);
+        fB[(18 + KB) * PL + o] = S(og);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2: near-wall and lid nodes from the compacted list.
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+__global__ void __launch_bounds__(128)
+k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+            const uint8_t* __restrict__ cls, const uint32_t* __restrict__ list, int nlist, Geo g, Prm<R> P)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nlist) return;
+    const uint32_t packed = list[t];
+    const int x = (int)(packed & 0xffffu), y = (int)(packed >> 16);
+    const long long PL = g.plane;
+    const long long o = (long long)y * g.pitch + x;
+    const int kind = cls[o] & CLS_KIND_MASK;
+    DistFetch<S, R> fetch{fA, PL};
+
+    if (kind == ST_FLUID) {
+        Macro<R> m;
+        window_macros(g, cls, P, x, y, fetch, m);
+        R gv[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) gv[k] = R(ldg(fA + (18 + k) * PL + o));
+        Hydro<R> h;
+        hydro_from_g(P, m, gv, h);
+        const R c1ux = m.c1 * h.ux, c1uy = m.c1 * h.uy, c2ux = m.c2 * h.ux, c2uy = m.c2 * h.uy;
+        const R d1x = c1ux - R(cu[0 * PL + o]), d1y = c1uy - R(cu[1 * PL + o]);
+        const R d2x = c2ux - R(cu[2 * PL + o]), d2y = c2uy - R(cu[3 * PL + o]);
+        cu[0 * PL + o] = S(c1ux);
+        cu[1 * PL + o] = S(c1uy);
+        cu[2 * PL + o] = S(c2ux);
+        cu[3 * PL + o] = S(c2uy);
+        static_for<0, 9>([&](auto kc) {
+            constexpr int K = decltype(kc)::value;
+            const R f1k = R(ldg(fA + K * PL + o));
+            const R f2k = R(ldg(fA + (9 + K) * PL + o));
+            R o1, o2, og;
+            collide_k<K>(P, m, h, d1x, d1y, d2x, d2y, f1k, f2k, gv[K], o1, o2, og);
+            push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
+        });
+    } else if (kind == ST_LID) {
+        // x_f is the node below; x_u takes its macros and gradients, u = (U0, 0)
+        const long long of = o - g.pitch;
+        Macro<R> m;
+        window_macros(g, cls, P, x, y - 1, fetch, m);
+        R gf[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) gf[k] = R(ldg(fA + (18 + k) * PL + of));
+        Hydro<R> hf;
+        hydro_from_g(P, m, gf, hf);
+        Hydro<R> h = hf;
+        h.ux = P.lid_u;
+        h.uy = R(0);
+        h.usq = P.lid_u * P.lid_u;
+        const R a = P.aM[0] * m.lm1 + P.aM[1] * m.lm2;
+        h.Fax = h.ux * a;
+        h.Fay = R(0);
+        const R c1ux = m.c1 * h.ux, c2ux = m.c2 * h.ux;
+        const R d1x = c1ux - R(cu[0 * PL + o]), d1y = R(0) - R(cu[1 * PL + o]);
+        const R d2x = c2ux - R(cu[2 * PL + o]), d2y = R(0) - R(cu[3 * PL + o]);
+        cu[0 * PL + o] = S(c1ux);
+        cu[1 * PL + o] = S(0);
+        cu[2 * PL + o] = S(c2ux);
+        cu[3 * PL + o] = S(0);
+        static_for<0, 9>([&](auto kc) {
+            constexpr int K = decltype(kc)::value;
+            R e1u, e2u, egu, e1f, e2f, egf;
+            equilibria(K, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, hf.p, h.ux, h.uy, e1u, e2u, egu);
+            equilibria(K, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, hf.p, hf.ux, hf.uy, e1f, e2f, egf);
+            // Eq. 51: f(x_u) = f^eq(x_u) + [f(x_f) - f^eq(x_f)]
+            const R f1k = e1u + (R(ldg(fA + K * PL + of)) - e1f);
+            const R f2k = e2u + (R(ldg(fA + (9 + K) * PL + of)) - e2f);
+            const R gk = egu + (gf[K] - egf);
+            R o1, o2, og;
+            collide_k<K>(P, m, h, d1x, d1y, d2x, d2y, f1k, f2k, gk, o1, o2, og);
+            push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
+            // slots fed from beyond the lid receive nothing: keep them zero
+            if constexpr (ey(K) == -1) {
+                long long dummy = 0;
+                if (site_of(g, cls, x - ex(K), y + 1, dummy) == ST_VOID) {
+                    fB[K * PL + o] = S(0);
+                    fB[(9 + K) * PL + o] = S(0);
+                    fB[(18 + K) * PL + o] = S(0);
+                }
+            }
+        });
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Set-up: f = f^eq(c, mu(c), u), g = g^eq(p, rho(c), u), cu = c u.
+// Inputs are dense [ny][nx] FP64 device arrays.
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+__global__ void k_init(S* __restrict__ fA, S* __restrict__ cu, const uint8_t* __restrict__ cls,
+                       const double* __restrict__ c1, const double* __restrict__ c2,
+                       const double* __restrict__ ux, const double* __restrict__ uy,
+                       const double* __restrict__ p, Geo g, Prm<R> P)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const long long PL = g.plane;
+    const long long o = (long long)y * g.pitch + x;
+    const long long n = (long long)y * g.nx + x;
+    const int kind = cls[o] & CLS_KIND_MASK;
+    if (!fluidlike(kind)) {
+        for (int q = 0; q < 27; q++) fA[q * PL + o] = S(0);
+        for (int q = 0; q < 4; q++) cu[q * PL + o] = S(0);
+        return;
+    }
+    FieldFetch<R> fetch{c1, c2, g.nx, g.pitch};
+    Macro<R> m;
+    window_macros(g, cls, P, x, kind == ST_LID ? y - 1 : y, fetch, m);
+    const R u = R(ux[n]), v = R(uy[n]);
+    const R pp = p ? R(p[n]) : R(0);
+    for (int k = 0; k < 9; k++) {
+        R e1, e2, eg;
+        equilibria(k, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, pp, u, v, e1, e2, eg);
+        fA[k * PL + o] = S(e1);
+        fA[(9 + k) * PL + o] = S(e2);
+        fA[(18 + k) * PL + o] = S(eg);
+    }
+    cu[0 * PL + o] = S(m.c1 * u);
+    cu[1 * PL + o] = S(m.c1 * v);
+    cu[2 * PL + o] = S(m.c2 * u);
+    cu[3 * PL + o] = S(m.c2 * v);
+}
+
+// ---------------------------------------------------------------------------
+// Read-out of macroscopic fields as FP64 planes (order c1 c2 c3 rho ux uy p
+// mu1 mu2 mu3, only the planes selected by `mask`).
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+__global__ void k_read_fields(const S* __restrict__ fA, const uint8_t* __restrict__ cls, double* __restrict__ out,
+                              uint32_t mask, Geo g, Prm<R> P)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const long long PL = g.plane;
+    const long long o = (long long)y * g.pitch + x;
+    const long long n = (long long)y * g.nx + x;
+    const long long N = (long long)g.nx * g.ny;
+    const int kind = cls[o] & CLS_KIND_MASK;
+    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (fluidlike(kind)) {
+        DistFetch<S, R> fetch{fA, PL};
+        const long long of = kind == ST_LID ? o - g.pitch : o;
+        Macro<R> m;
+        window_macros(g, cls, P, x, kind == ST_LID ? y - 1 : y, fetch, m);
+        R gv[9];
+        for (int k = 0; k < 9; k++) gv[k] = R(fA[(18 + k) * PL + of]);
+        Hydro<R> h;
+        hydro_from_g(P, m, gv, h);
+        if (kind == ST_LID) {
+            h.ux = P.lid_u;
+            h.uy = R(0);
+        }
+        const R mu3 = -(P.l3_l1 * m.mu1 + P.l3_l2 * m.mu2);
+        v[0] = m.c1;
+        v[1] = m.c2;
+        v[2] = R(1) - m.c1 - m.c2;
+        v[3] = m.rho;
+        v[4] = h.ux;
+        v[5] = h.uy;
+        v[6] = h.p;
+        v[7] = m.mu1;
+        v[8] = m.mu2;
+        v[9] = mu3;
+    }
+    int plane = 0;
+    for (int q = 0; q < 10; q++) {
+        if (mask & (1u << q)) {
+            out[plane * N + n] = v[q];
+            plane++;
+        }
+    }
+}
+
+// Raw state to dense FP64 planes [31][ny][nx].
+template <typename S>
+__global__ void k_state_to_f64(const S* __restrict__ fA, const S* __restrict__ cu, double* __restrict__ out, Geo g)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const long long PL = g.plane;
+    const long long o = (long long)y * g.pitch + x;
+    const long long n = (long long)y * g.nx + x;
+    const long long N = (long long)g.nx * g.ny;
+    for (int q = 0; q < 27; q++) out[q * N + n] = to_d(fA[q * PL + o]);
+    for (int q = 0; q < 4; q++) out[(27 + q) * N + n] = to_d(cu[q * PL + o]);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 mass totals: per-block partial sums in a fixed order, then one block
+// sums the partials in a fixed order (deterministic).  part[b*4 + 0..3] =
+// sum c1, sum c2, sum c3, non-finite count.
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+__global__ void __launch_bounds__(256)
+k_mass_partials(const S* __restrict__ fA, const uint8_t* __restrict__ cls, double* __restrict__ part, Geo g)
+{
+    __shared__ double red[4][256];
+    const long long PL = g.plane;
+    const long long N = (long long)g.nx * g.ny;
+    double s1 = 0, s2 = 0, s3 = 0, bad = 0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / g.nx), x = (int)(n - (long long)y * g.nx);
+        long long o = (long long)y * g.pitch + x;
+        const int kind = cls[o] & CLS_KIND_MASK;
+        if (!fluidlike(kind)) continue;
+        if (kind == ST_LID) o -= g.pitch;
+        R a = R(0), b = R(0), gs = R(0);
+        for (int k = 0; k < 9; k++) a += R(fA[k * PL + o]);
+        for (int k = 0; k < 9; k++) b += R(fA[(9 + k) * PL + o]);
+        for (int k = 0; k < 9; k++) gs += R(fA[(18 + k) * PL + o]);
+        const double c1 = a, c2 = b;
+        s1 += c1;
+        s2 += c2;
+        s3 += 1.0 - c1 - c2;
+        if (!isfinite(c1) || !isfinite(c2) || !isfinite((double)gs)) bad += 1.0;
+    }
+    red[0][threadIdx.x] = s1;
+    red[1][threadIdx.x] = s2;
+    red[2][threadIdx.x] = s3;
+    red[3][threadIdx.x] = bad;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 4; q++) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+static __global__ void __launch_bounds__(256) k_mass_final(const double* __restrict__ part, int nparts, double* __restrict__ out)
+{
+    __shared__ double red[4][256];
+    double s[4] = {0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x)
+        for (int q = 0; q < 4; q++) s[q] += part[b * 4 + q];
+    for (int q = 0; q < 4; q++) red[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 4; q++) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+}  // namespace tlb

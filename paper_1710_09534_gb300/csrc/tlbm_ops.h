@@ -1,0 +1,34 @@
+// Host-side launch table of one storage precision (internal to the library).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "tlbm_device.cuh"
+
+namespace tlb {
+
+struct Ops {
+    size_t elem;  // bytes per stored scalar
+    // one time step A -> B = interior tiles (fused kernel) + near-wall list
+    cudaError_t (*interior)(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
+                            const Prm<double>& P, cudaStream_t s);
+    cudaError_t (*wall)(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
+                        int nlist, const Geo& g, const Prm<double>& P, cudaStream_t s);
+    cudaError_t (*init)(void* fA, void* cu, const uint8_t* cls, const double* c1, const double* c2,
+                        const double* ux, const double* uy, const double* p, const Geo& g,
+                        const Prm<double>& P, cudaStream_t s);
+    cudaError_t (*read)(const void* fA, const uint8_t* cls, double* out, uint32_t mask, const Geo& g,
+                        const Prm<double>& P, cudaStream_t s);
+    // FP64 mass totals into out[4] via nparts block partials in part[4*nparts]
+    cudaError_t (*mass)(const void* fA, const uint8_t* cls, double* part, int nparts, double* out,
+                        const Geo& g, cudaStream_t s);
+};
+
+const Ops& ops_f64();
+const Ops& ops_f32();
+
+// Tile of the fused interior kernel for each precision.
+constexpr int kTileX64 = 32, kTileY64 = 8;
+constexpr int kTileX32 = 32, kTileY32 = 8;
+
+}  // namespace tlb

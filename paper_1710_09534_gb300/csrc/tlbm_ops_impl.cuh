@@ -1,0 +1,88 @@
+// Launchers of one precision; included by tlbm_f64.cu and tlbm_f32.cu.
+#pragma once
+#include "tlbm_kernels.cuh"
+#include "tlbm_ops.h"
+
+namespace tlb {
+
+template <typename R>
+inline Prm<R> cast_prm(const Prm<double>& d)
+{
+    Prm<R> r;
+    for (int i = 0; i < 3; i++) {
+        r.lam[i] = R(d.lam[i]);
+        r.rho[i] = R(d.rho[i]);
+        r.nu[i] = R(d.nu[i]);
+    }
+    for (int i = 0; i < 2; i++) {
+        r.eta[i] = R(d.eta[i]);
+        r.inv_tau[i] = R(d.inv_tau[i]);
+        r.src_f[i] = R(d.src_f[i]);
+        r.aM[i] = R(d.aM[i]);
+    }
+    r.lamT = R(d.lamT);
+    r.k12D = R(d.k12D);
+    r.k34D = R(d.k34D);
+    r.k4D = R(d.k4D);
+    r.l3_l1 = R(d.l3_l1);
+    r.l3_l2 = R(d.l3_l2);
+    r.cos12 = R(d.cos12);
+    r.cos13 = R(d.cos13);
+    r.cos23 = R(d.cos23);
+    r.gx = R(d.gx);
+    r.gy = R(d.gy);
+    r.lid_u = R(d.lid_u);
+    return r;
+}
+
+template <typename S, typename R, int TX, int TY>
+struct OpsImpl {
+    static cudaError_t interior(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
+                                const Prm<double>& Pd, cudaStream_t s)
+    {
+        const Prm<R> P = cast_prm<R>(Pd);
+        dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
+        k_step_interior<S, R, TX, TY><<<grid, TX * TY, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, g, P);
+        return cudaGetLastError();
+    }
+    static cudaError_t wall(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
+                            int nlist, const Geo& g, const Prm<double>& Pd, cudaStream_t s)
+    {
+        const Prm<R> P = cast_prm<R>(Pd);
+        if (nlist > 0)
+            k_step_wall<S, R><<<(nlist + 127) / 128, 128, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, list,
+                                                                   nlist, g, P);
+        return cudaGetLastError();
+    }
+    static cudaError_t init(void* fA, void* cu, const uint8_t* cls, const double* c1, const double* c2,
+                            const double* ux, const double* uy, const double* p, const Geo& g,
+                            const Prm<double>& Pd, cudaStream_t s)
+    {
+        const Prm<R> P = cast_prm<R>(Pd);
+        dim3 grid((g.nx + 127) / 128, g.ny);
+        k_init<S, R><<<grid, 128, 0, s>>>((S*)fA, (S*)cu, cls, c1, c2, ux, uy, p, g, P);
+        return cudaGetLastError();
+    }
+    static cudaError_t read(const void* fA, const uint8_t* cls, double* out, uint32_t mask, const Geo& g,
+                            const Prm<double>& Pd, cudaStream_t s)
+    {
+        const Prm<R> P = cast_prm<R>(Pd);
+        dim3 grid((g.nx + 127) / 128, g.ny);
+        k_read_fields<S, R><<<grid, 128, 0, s>>>((const S*)fA, cls, out, mask, g, P);
+        return cudaGetLastError();
+    }
+    static cudaError_t mass(const void* fA, const uint8_t* cls, double* part, int nparts, double* out,
+                            const Geo& g, cudaStream_t s)
+    {
+        k_mass_partials<S, R><<<nparts, 256, 0, s>>>((const S*)fA, cls, part, g);
+        k_mass_final<<<1, 256, 0, s>>>(part, nparts, out);
+        return cudaGetLastError();
+    }
+    static const Ops& table()
+    {
+        static const Ops t{sizeof(S), &interior, &wall, &init, &read, &mass};
+        return t;
+    }
+};
+
+}  // namespace tlb
