@@ -196,6 +196,26 @@ int tlb_profile_read(tlb_lattice *lat, double ms[2], int64_t launches[2]);
 /* Number of nodes in the near-wall list (handled by the near-wall kernel). */
 int64_t tlb_wall_nodes(tlb_lattice *lat);
 
+/* Allocation-free variant of the tlb_diagnostics reduction.  The paper has
+ * no counterpart: this exists for callers that cannot allocate device memory
+ * where they need the totals (code living in a fixed arena it does not own,
+ * or a loop that must not stall on an allocation).  It reads the lattice's
+ * current state, writes 4 doubles {sum c1, sum c2, sum c3, non-finite count}
+ * to dev_out (caller-owned device memory) asynchronously on the lattice's
+ * stream, and keeps its partial sums in a static 32 KiB device array that
+ * every GPU loading the library holds until process exit.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   - Limit: lattices of at most 16,777,216 nodes (4096 x 4096); larger ones
+ *     get TLB_EINVAL with a message (use tlb_diagnostics for those).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (different streams, or devices sharing nothing but this array) race
+ *     and may return wrong totals; order them on one stream.  Each call
+ *     overwrites every partial it reads, so nothing needs clearing.
+ * TLB_ESTATE before set_fields; TLB_EINVAL for a null dev_out. */
+int tlb_diagnostics_noalloc(tlb_lattice *lat, double *dev_out);
+
 /* Release the host handle (the workspace stays the caller's). */
 void tlb_destroy(tlb_lattice *lat);
 

@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tlb_import_state": (i32, [vp, vp, i64]),
         "tlb_theta12_from": (i32, [ctypes.c_double] * 5 + [dp]),
         "tlb_wall_nodes": (i64, [vp]),
+        "tlb_diagnostics_noalloc": (i32, [vp, vp]),
         "tlb_profile": (i32, [vp, i32]),
         "tlb_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "tlb_destroy": (None, [vp]),
@@ -215,6 +216,11 @@ class Lattice:
         if rc < 0 and rc != EUNSTABLE:
             raise TlbError(rc, last_error())
         return dict(mass=np.array(d.mass[:]), nonfinite=int(d.nonfinite), rc=rc)
+
+    def diagnostics_noalloc(self, dev_out):
+        """Allocation-free reduction into a device float64 tensor of >= 4
+        elements: [sum c1, sum c2, sum c3, non-finite count] (asynchronous)."""
+        _check(self.lib.tlb_diagnostics_noalloc(self._h, ctypes.c_void_p(dev_out.data_ptr())))
 
     def state(self) -> np.ndarray:
         out = np.empty((31, self.ny, self.nx))

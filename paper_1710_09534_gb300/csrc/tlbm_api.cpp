@@ -13,6 +13,7 @@
 #include <thread>
 #include <vector>
 
+#include "tlbm_internal.h"
 #include "tlbm_ops.h"
 
 namespace {
@@ -616,3 +617,26 @@ void tlb_destroy(tlb_lattice* L)
 const char* tlb_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+namespace tlb {
+
+int lattice_view(tlb_lattice* L, LatticeView* v)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!v) return fail(TLB_EINVAL, "null view");
+    if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "no state yet");
+    v->dist = L->bufA();
+    v->cls = L->dcls();
+    v->geo = L->geo;
+    v->precision = L->precision;
+    v->device = L->device;
+    v->stream = L->stream;
+    return TLB_OK;
+}
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+int clear_error() { return ok(); }
+
+}  // namespace tlb
