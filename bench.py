@@ -258,7 +258,7 @@ def run_ours(args):
         result["e2e"] = e2e(L, w, args, torch, T)
     if rank == 0:
         variants = {}
-        for prec in [v for v in args.variants.split(",") if v and v != args.precision]:
+        for prec in [v for v in args.variants.split(",") if v and v not in ("none", args.precision)]:
             V = T.lattice_from_workload(w, prec)
             V.step(args.warmup)
             V.sync()

@@ -336,15 +336,25 @@ int tlb_set_params(tlb_lattice* L, const tlb_params* p)
     P.lam[1] = l2;
     P.lam[2] = l3;
     P.lamT = lT;
+    P.two_lamT = 2.0 * lT;
     P.k12D = 12.0 / p->D;
     P.k34D = 0.75 * p->D;
     P.k4D = 4.0 / p->D;
     const double tau[2] = {p->tau1, p->tau2};
     const double M[2] = {p->M0 / l1, p->M0 / l2};
+    const double w[2] = {1.0 / 9.0, 1.0 / 36.0};
     for (int i = 0; i < 2; i++) {
+        P.k34Dlam[i] = 0.75 * p->D * P.lam[i];
         P.eta[i] = M[i] / ((1.0 / 3.0) * (tau[i] - 0.5));
         P.inv_tau[i] = 1.0 / tau[i];
+        P.omt[i] = 1.0 - 1.0 / tau[i];
         P.src_f[i] = 3.0 * (1.0 - 0.5 / tau[i]);
+        P.e0[i] = (4.0 / 9.0 - 1.0) * P.eta[i] / tau[i];
+        for (int c = 0; c < 2; c++) {
+            P.aw[i][c] = P.eta[i] * w[c] / tau[i];
+            P.bw[i][c] = 3.0 * w[c] / tau[i];
+            P.sw[i][c] = P.src_f[i] * w[c];
+        }
     }
     P.rho[0] = p->rho1;
     P.rho[1] = p->rho2;
@@ -352,6 +362,10 @@ int tlb_set_params(tlb_lattice* L, const tlb_params* p)
     P.nu[0] = p->nu1;
     P.nu[1] = p->nu2;
     P.nu[2] = p->nu3;
+    P.drho[0] = p->rho1 - p->rho3;
+    P.drho[1] = p->rho2 - p->rho3;
+    P.dnu[0] = p->nu1 - p->nu3;
+    P.dnu[1] = p->nu2 - p->nu3;
     P.aM[0] = (p->rho1 - p->rho3) * M[0];
     P.aM[1] = (p->rho2 - p->rho3) * M[1];
     P.l3_l1 = l3 / l1;

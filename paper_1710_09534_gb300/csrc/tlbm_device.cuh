@@ -1,9 +1,9 @@
 // Device-side building blocks of the ternary phase-field lattice Boltzmann
 // update (Liang et al., arXiv:1710.09534, Sec. II): D2Q9 constants, node
 // classification, the isotropic stencils of Eqs. 20a/20b, the chemical
-// potential of Eq. 8, the wetting ghost offset of Eq. 42, and the BGK
-// collide-and-push of Eqs. 1a, 1b, 2a, 2b, 4, 11a, 11b with half-way
-// bounce-back (Eq. 44).
+// potential of Eq. 8, the wetting ghost offset of Eq. 42, the moments of
+// Eqs. 13b/13c with the forces of Eq. 12, and the BGK collision of Eqs. 1a,
+// 1b, 2a, 2b, 4, 11a, 11b rearranged for few FP64 instructions.
 //
 // Layout in HBM (structure of arrays, x fastest, rows padded to `pitch`):
 //   dist[p][y][x], p = 0..8 f^1_k, 9..17 f^2_k, 18..26 g_k   (two buffers)
@@ -20,6 +20,10 @@ __host__ __device__ constexpr int ex(int k) { return (k == 1 || k == 5 || k == 8
 __host__ __device__ constexpr int ey(int k) { return (k == 2 || k == 5 || k == 6) ? 1 : ((k == 4 || k == 7 || k == 8) ? -1 : 0); }
 __host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : (k <= 4 ? ((k + 1) % 4) + 1 : ((k - 3) % 4) + 5); }
 __host__ __device__ constexpr double wk(int k) { return k == 0 ? 4.0 / 9.0 : (k <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+// Direction k as sign * (one of +x, +y, (1,1), (1,-1)): component index 0..3
+__host__ __device__ constexpr int comp(int k) { return (k == 1 || k == 3) ? 0 : ((k == 2 || k == 4) ? 1 : ((k == 5 || k == 7) ? 2 : 3)); }
+__host__ __device__ constexpr int sgn(int k) { return (k == 1 || k == 2 || k == 5 || k == 8) ? 1 : -1; }
+__host__ __device__ constexpr int wclass(int k) { return k <= 4 ? 0 : 1; }  // 0 axis, 1 diagonal
 
 // Site kinds (same semantics as the FP64 oracle's classification).
 enum : int { ST_FLUID = 0, ST_LID = 1, ST_WET = 2, ST_NEUTRAL = 3, ST_VOID = 4 };
@@ -32,17 +36,26 @@ struct Geo {
     long long plane;  // elements per plane = ny * pitch
 };
 
-// Derived constants, computed on the host from tlb_params.
+// Derived constants, computed on the host from tlb_params (index i: fluid
+// 1, 2; index c: direction class 0 = axis (w = 1/9), 1 = diagonal (w = 1/36)).
 template <typename R>
 struct Prm {
     R lam[3], lamT;
+    R two_lamT;       // 2 lambda_T
     R k12D;           // 12 / D
     R k34D;           // 3/4 D
+    R k34Dlam[2];     // 3/4 D lambda_i
     R k4D;            // 4 / D (Eq. 42 with dx = 1)
     R eta[2];         // eta_i = M_i / (cs^2 (tau_i - 1/2))
     R inv_tau[2];     // 1 / tau_i
+    R omt[2];         // 1 - 1 / tau_i
     R src_f[2];       // (1 - 1/(2 tau_i)) * 3 (Eq. 11a with 1/cs^2)
+    R e0[2];          // (w_0 - 1) eta_i / tau_i  (k = 0 equilibrium, relaxed)
+    R aw[2][2];       // eta_i w_c / tau_i
+    R bw[2][2];       // 3 w_c / tau_i
+    R sw[2][2];       // src_f_i w_c
     R rho[3], nu[3];
+    R drho[2], dnu[2];  // rho_i - rho_3, nu_i - nu_3
     R aM[2];          // (rho_i - rho_3) M_i (Eq. 12)
     R l3_l1, l3_l2;   // lambda_3 / lambda_i (mu_3 from sum mu_i / lambda_i = 0)
     R cos12, cos13, cos23;
@@ -72,21 +85,37 @@ __device__ __forceinline__ int site_of(const Geo& g, const uint8_t* __restrict__
 
 __device__ __forceinline__ bool fluidlike(int s) { return s == ST_FLUID || s == ST_LID; }
 
+// ---- reciprocal -------------------------------------------------------------
+// FP64: single-precision seed refined by two Newton-Raphson steps
+// r <- r + r (1 - a r), each doubling the correct bits (24 -> 48 -> 96), i.e.
+// within one ulp of 1/a for the positive, normal a used here (rho, tau_g).
+__device__ __forceinline__ double rcp(double a)
+{
+    double r = (double)(1.0f / (float)a);
+    double e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-a, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ float rcp(float a) { return 1.0f / a; }
+
 // ---- stencils (Eqs. 20a, 20b): v[k] = chi(x + e_k) -----------------------
 template <typename R>
 __device__ __forceinline__ void grad9(const R v[9], R& gx, R& gy)
 {
     // w_k e_k / cs^2: 1/3 on axis links, 1/12 on diagonals
-    gx = R(1.0 / 3.0) * (v[1] - v[3]) + R(1.0 / 12.0) * ((v[5] - v[7]) + (v[8] - v[6]));
-    gy = R(1.0 / 3.0) * (v[2] - v[4]) + R(1.0 / 12.0) * ((v[5] - v[7]) + (v[6] - v[8]));
+    const R d57 = v[5] - v[7], d86 = v[8] - v[6];
+    gx = fma(R(1.0 / 3.0), v[1] - v[3], R(1.0 / 12.0) * (d57 + d86));
+    gy = fma(R(1.0 / 3.0), v[2] - v[4], R(1.0 / 12.0) * (d57 - d86));
 }
 
 template <typename R>
 __device__ __forceinline__ R lap9(const R v[9])
 {
     // 2 w_k / cs^2: 2/3 on axis links, 1/6 on diagonals; centre weight -10/3
-    return R(2.0 / 3.0) * ((v[1] + v[3]) + (v[2] + v[4])) +
-           R(1.0 / 6.0) * ((v[5] + v[7]) + (v[6] + v[8])) - R(10.0 / 3.0) * v[0];
+    const R ax = (v[1] + v[3]) + (v[2] + v[4]);
+    const R dg = (v[5] + v[7]) + (v[6] + v[8]);
+    return fma(R(2.0 / 3.0), ax, fma(R(1.0 / 6.0), dg, R(-10.0 / 3.0) * v[0]));
 }
 
 // ---- Eq. 8 for i = 1, 2 ---------------------------------------------------
@@ -94,11 +123,11 @@ template <typename R>
 __device__ __forceinline__ void chem_pot(const Prm<R>& P, R c1, R c2, R lap1, R lap2, R& mu1, R& mu2)
 {
     const R c3 = R(1) - c1 - c2;
-    const R t = R(2) * P.lamT * (c1 * c2 * c3);
-    const R b1 = P.lam[0] * (c1 * (R(1) - c1) * (R(1) - R(2) * c1)) - t;
-    const R b2 = P.lam[1] * (c2 * (R(1) - c2) * (R(1) - R(2) * c2)) - t;
-    mu1 = P.k12D * b1 - P.k34D * P.lam[0] * lap1;
-    mu2 = P.k12D * b2 - P.k34D * P.lam[1] * lap2;
+    const R t = P.two_lamT * (c1 * c2) * c3;
+    const R b1 = fma(P.lam[0], c1 * (R(1) - c1) * fma(R(-2), c1, R(1)), -t);
+    const R b2 = fma(P.lam[1], c2 * (R(1) - c2) * fma(R(-2), c2, R(1)), -t);
+    mu1 = fma(P.k12D, b1, -P.k34Dlam[0] * lap1);
+    mu2 = fma(P.k12D, b2, -P.k34Dlam[1] * lap2);
 }
 
 // ---- Eq. 42: c_ghost - c_f on a link into a wetting solid ----------------
@@ -110,7 +139,7 @@ __device__ __forceinline__ void wet_offset(const Prm<R>& P, R c1, R c2, R& o1, R
     o2 = P.k4D * (-P.cos12 * c1 * c2 + P.cos23 * c2 * c3);
 }
 
-// Macroscopic state of one node, everything the collision needs.
+// Macroscopic state of one node from the stencil phase.
 template <typename R>
 struct Macro {
     R c1, c2, mu1, mu2, rho;
@@ -118,83 +147,152 @@ struct Macro {
     R lm1, lm2;             // lap mu1, lap mu2 (Eq. 20b)
 };
 
-// Velocity and pressure (Eqs. 13b, 13c) plus the forces of Eq. 12, given the
-// node's g and macros.  Also returns the tau_g-dependent constants.
+// Velocity, pressure and forces (Eqs. 12, 13b, 13c).
 template <typename R>
 struct Hydro {
     R ux, uy, p, usq;
     R Ftx, Fty;      // F_s + G
-    R Fax, Fay;      // F_a
+    R a;             // sum_i (rho_i - rho_3) M_i lap mu_i, so that F_a = u a
     R grx, gry;      // grad rho
     R inv_taug;
 };
 
 template <typename R>
-__device__ __forceinline__ void surface_force(const Prm<R>& P, const Macro<R>& m, R& Fsx, R& Fsy)
+__device__ __forceinline__ R density(const Prm<R>& P, R c1, R c2)
 {
-    const R mu3 = -(P.l3_l1 * m.mu1 + P.l3_l2 * m.mu2);
-    Fsx = (m.mu1 - mu3) * m.g1x + (m.mu2 - mu3) * m.g2x;
-    Fsy = (m.mu1 - mu3) * m.g1y + (m.mu2 - mu3) * m.g2y;
+    return fma(c2, P.drho[1], fma(c1, P.drho[0], P.rho[2]));
 }
 
 template <typename R>
 __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m, const R g[9], Hydro<R>& h)
 {
-    R Fsx, Fsy;
-    surface_force(P, m, Fsx, Fsy);
-    const R Gx = m.rho * P.gx, Gy = m.rho * P.gy;
-    h.Ftx = Fsx + Gx;
-    h.Fty = Fsy + Gy;
-    h.grx = (P.rho[0] - P.rho[2]) * m.g1x + (P.rho[1] - P.rho[2]) * m.g2x;
-    h.gry = (P.rho[0] - P.rho[2]) * m.g1y + (P.rho[1] - P.rho[2]) * m.g2y;
-    const R mx = (g[1] - g[3]) + (g[5] - g[7]) + (g[8] - g[6]);
-    const R my = (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
-    const R inv_rho = R(1) / m.rho;
-    h.ux = (mx + R(0.5) * h.Ftx) * inv_rho;
-    h.uy = (my + R(0.5) * h.Fty) * inv_rho;
-    h.usq = h.ux * h.ux + h.uy * h.uy;
+    const R mu3 = -fma(P.l3_l1, m.mu1, P.l3_l2 * m.mu2);
+    const R q1 = m.mu1 - mu3, q2 = m.mu2 - mu3;
+    // F_s = sum_i mu_i grad c_i with grad c3 = -grad c1 - grad c2; G = rho g
+    h.Ftx = fma(q1, m.g1x, fma(q2, m.g2x, m.rho * P.gx));
+    h.Fty = fma(q1, m.g1y, fma(q2, m.g2y, m.rho * P.gy));
+    h.grx = fma(P.drho[0], m.g1x, P.drho[1] * m.g2x);
+    h.gry = fma(P.drho[0], m.g1y, P.drho[1] * m.g2y);
+    const R g57 = g[5] - g[7], g86 = g[8] - g[6];
+    const R mx = (g[1] - g[3]) + (g57 + g86);
+    const R my = (g[2] - g[4]) + (g57 - g86);
+    const R inv_rho = rcp(m.rho);
+    h.ux = fma(R(0.5), h.Ftx, mx) * inv_rho;
+    h.uy = fma(R(0.5), h.Fty, my) * inv_rho;
+    h.usq = fma(h.ux, h.ux, h.uy * h.uy);
     const R sumg = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
     // p = cs^2/(1 - w0) [sum_{k!=0} g_k + u.grad rho / 2 + rho s_0(u)], s_0 = -w0 u.u / (2 cs^2)
-    h.p = R(0.6) * (sumg + R(0.5) * (h.ux * h.grx + h.uy * h.gry) - R(2.0 / 3.0) * m.rho * h.usq);
-    const R a = P.aM[0] * m.lm1 + P.aM[1] * m.lm2;
-    h.Fax = h.ux * a;
-    h.Fay = h.uy * a;
-    const R c3 = R(1) - m.c1 - m.c2;
-    const R nu = m.c1 * P.nu[0] + m.c2 * P.nu[1] + c3 * P.nu[2];
-    h.inv_taug = R(1) / (R(3) * nu + R(0.5));
+    const R ug = fma(h.ux, h.grx, h.uy * h.gry);
+    h.p = R(0.6) * fma(R(-2.0 / 3.0) * m.rho, h.usq, fma(R(0.5), ug, sumg));
+    h.a = fma(P.aM[0], m.lm1, P.aM[1] * m.lm2);
+    const R nu = fma(m.c2, P.dnu[1], fma(m.c1, P.dnu[0], P.nu[2]));
+    h.inv_taug = rcp(fma(R(3), nu, R(0.5)));
 }
 
-// Post-collision populations of direction k (Eqs. 1a, 1b, 2a, 2b, 4, 11a,
-// 11b, 45) from the pre-collision values f1k, f2k, gk.
-template <int K, typename R>
-__device__ __forceinline__ void collide_k(const Prm<R>& P, const Macro<R>& m, const Hydro<R>& h,
-                                          R d1x, R d1y, R d2x, R d2y, R f1k, R f2k, R gk,
-                                          R& o1, R& o2, R& og)
-{
-    constexpr R w = R(wk(K));
-    constexpr R exk = R(ex(K)), eyk = R(ey(K));
-    const R eu = exk * h.ux + eyk * h.uy;
-    const R sk = w * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * h.usq);
-    R f1eq, f2eq, geq;
-    if (K == 0) {
-        f1eq = m.c1 + (w - R(1)) * P.eta[0] * m.mu1;
-        f2eq = m.c2 + (w - R(1)) * P.eta[1] * m.mu2;
-        geq = R(3) * h.p * (w - R(1)) + m.rho * sk;
-    } else {
-        f1eq = w * (P.eta[0] * m.mu1 + R(3) * m.c1 * eu);
-        f2eq = w * (P.eta[1] * m.mu2 + R(3) * m.c2 * eu);
-        geq = R(3) * h.p * w + m.rho * sk;
+// Per-node precomputation of the BGK update (Eqs. 1a, 1b, 2a, 2b, 4, 11a,
+// 11b, 45), arranged so that each direction costs a few fused operations:
+//   f'_k = (1 - 1/tau) f_k + f^eq_k / tau + F_k
+//   g'_k = (1 - 1/tau_g) g_k + g^eq_k / tau_g + G_k
+//   g^eq_k / tau_g = w (3p + rho q_k) / tau_g,  q_k = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u
+//   G_k = w (1 - 1/(2 tau_g)) [q_k (e - u).H + (e - u).T] + 3 w e.F_a,
+//   H = grad rho + 3 (F_s + G), T = 3 (F_s + G)   (s_k = w q_k)
+template <typename R>
+struct Collider {
+    R eu[4];            // e.u for +x, +y, (1,1), (1,-1)
+    R A1[2], A2[2];     // f^eq / tau constant parts per class, with the source folded in below
+    R B1[2], B2[2];     // 3 w c_i / tau_i per class
+    R F1[4], F2[4];     // F^i for the 4 components (sign applied per direction)
+    R E1, E2;           // f^{i,eq}_0 / tau_i
+    R omt1, omt2, omtg;
+    R t0;               // -1.5 u.u
+    R H[4], T[4], uH, uT;
+    R Z[4];             // 3 w e.F_a per component (class weight included)
+    R Pw[2], Rw[2], Kw[2];  // 3 p w / tau_g, rho w / tau_g, w (1 - 1/(2 tau_g))
+    R P0;               // g^eq_0 / tau_g + G_0
+
+    __device__ __forceinline__ void build(const Prm<R>& P, const Macro<R>& m, const Hydro<R>& h,
+                                          R d1x, R d1y, R d2x, R d2y)
+    {
+        eu[0] = h.ux;
+        eu[1] = h.uy;
+        eu[2] = h.ux + h.uy;
+        eu[3] = h.ux - h.uy;
+        // order parameters
+        omt1 = P.omt[0];
+        omt2 = P.omt[1];
+        E1 = fma(P.e0[0], m.mu1, P.inv_tau[0] * m.c1);
+        E2 = fma(P.e0[1], m.mu2, P.inv_tau[1] * m.c2);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            A1[c] = P.aw[0][c] * m.mu1;
+            A2[c] = P.aw[1][c] * m.mu2;
+            B1[c] = P.bw[0][c] * m.c1;
+            B2[c] = P.bw[1][c] * m.c2;
+        }
+        F1[0] = P.sw[0][0] * d1x;
+        F1[1] = P.sw[0][0] * d1y;
+        F1[2] = P.sw[0][1] * (d1x + d1y);
+        F1[3] = P.sw[0][1] * (d1x - d1y);
+        F2[0] = P.sw[1][0] * d2x;
+        F2[1] = P.sw[1][0] * d2y;
+        F2[2] = P.sw[1][1] * (d2x + d2y);
+        F2[3] = P.sw[1][1] * (d2x - d2y);
+        // hydrodynamics
+        const R itg = h.inv_taug;
+        omtg = R(1) - itg;
+        const R kG = fma(R(-0.5), itg, R(1));
+        t0 = R(-1.5) * h.usq;
+        const R Tx = R(3) * h.Ftx, Ty = R(3) * h.Fty;
+        const R Hx = h.grx + Tx, Hy = h.gry + Ty;
+        H[0] = Hx;
+        H[1] = Hy;
+        H[2] = Hx + Hy;
+        H[3] = Hx - Hy;
+        T[0] = Tx;
+        T[1] = Ty;
+        T[2] = Tx + Ty;
+        T[3] = Tx - Ty;
+        uH = fma(h.ux, Hx, h.uy * Hy);
+        uT = fma(h.ux, Tx, h.uy * Ty);
+        const R za = R(3.0 / 9.0) * h.a, zd = R(3.0 / 36.0) * h.a;  // 3 w_c a, F_a = u a
+        Z[0] = za * eu[0];
+        Z[1] = za * eu[1];
+        Z[2] = zd * eu[2];
+        Z[3] = zd * eu[3];
+        const R p3 = R(3) * h.p * itg, ri = m.rho * itg;
+        Pw[0] = R(1.0 / 9.0) * p3;
+        Pw[1] = R(1.0 / 36.0) * p3;
+        Rw[0] = R(1.0 / 9.0) * ri;
+        Rw[1] = R(1.0 / 36.0) * ri;
+        Kw[0] = R(1.0 / 9.0) * kG;
+        Kw[1] = R(1.0 / 36.0) * kG;
+        // k = 0: g^eq_0 = 3p (w0 - 1) + rho w0 t0; G_0 = -w0 kG (t0 u.H + u.T)
+        const R w0 = R(4.0 / 9.0);
+        const R geq0 = fma(m.rho * w0, t0, R(3) * (w0 - R(1)) * h.p);
+        P0 = fma(geq0, itg, -(w0 * kG) * fma(t0, uH, uT));
     }
-    const R F1 = P.src_f[0] * w * (exk * d1x + eyk * d1y);
-    const R F2 = P.src_f[1] * w * (exk * d2x + eyk * d2y);
-    const R bx = sk * h.grx + R(3) * (sk + w) * h.Ftx;
-    const R by = sk * h.gry + R(3) * (sk + w) * h.Fty;
-    const R Gk = (R(1) - R(0.5) * h.inv_taug) * ((exk - h.ux) * bx + (eyk - h.uy) * by) +
-                 R(3) * w * (exk * h.Fax + eyk * h.Fay);
-    o1 = f1k - (f1k - f1eq) * P.inv_tau[0] + F1;
-    o2 = f2k - (f2k - f2eq) * P.inv_tau[1] + F2;
-    og = gk - (gk - geq) * h.inv_taug + Gk;
-}
+
+    template <int K>
+    __device__ __forceinline__ void post(R f1k, R f2k, R gk, R& o1, R& o2, R& og) const
+    {
+        if constexpr (K == 0) {
+            o1 = fma(omt1, f1k, E1);
+            o2 = fma(omt2, f2k, E2);
+            og = fma(omtg, gk, P0);
+        } else {
+            constexpr int C = comp(K), W = wclass(K);
+            constexpr R s = R(sgn(K));
+            const R e = s * eu[C];
+            const R q = fma(e, fma(R(4.5), e, R(3)), t0);
+            o1 = fma(omt1, f1k, fma(B1[W], e, fma(s, F1[C], A1[W])));
+            o2 = fma(omt2, f2k, fma(B2[W], e, fma(s, F2[C], A2[W])));
+            const R X = fma(s, H[C], -uH);
+            const R Y = fma(s, T[C], -uT);
+            const R Gk = fma(Kw[W], fma(q, X, Y), s * Z[C]);
+            og = fma(omtg, gk, fma(Rw[W], q, Pw[W]) + Gk);
+        }
+    }
+};
 
 // Equilibria alone (Eqs. 2a, 2b), used by the lid (Eq. 51) and set-up.
 template <typename R>

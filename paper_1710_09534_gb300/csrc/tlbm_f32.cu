@@ -2,5 +2,5 @@
 #include "tlbm_ops_impl.cuh"
 
 namespace tlb {
-const Ops& ops_f32() { return OpsImpl<float, float, kTileX32, kTileY32>::table(); }
+const Ops& ops_f32() { return OpsImpl<float, float, kBlock32, kRows32, true>::table(); }
 }  // namespace tlb

@@ -10,7 +10,7 @@
 //   k_step_wall      the same update for the compacted list of the other
 //                    fluid nodes, with the ghost rules of Eqs. 42-43,
 //                    bounce-back (Eq. 44) and the lid (Eqs. 51-53).
-//   k_init, k_read_fields, k_mass_partials/k_mass_final, k_state_to_f64
+//   k_init, k_read_fields, k_mass_partials/k_mass_final
 #pragma once
 #include <type_traits>
 #include "tlbm_device.cuh"
@@ -39,120 +39,152 @@ __device__ __forceinline__ long long wrap_off(const Geo& g, int x, int y)
 }
 
 // ---------------------------------------------------------------------------
-// K1: fused interior update.  Block = TX*TY threads, one node each.
+// K1: fused interior update, marching up a strip of columns.
+//
+// A block of BLOCK threads owns one column each: columns x0-2 .. x0+BLOCK-3
+// of which the middle TX = BLOCK-4 are updated, over rows y0 .. y0+ROWS-1.
+// Iteration for row yc keeps rolling rings in shared memory:
+//   c1, c2 of row yc        (sum of the 18 order-parameter populations)
+//   mu1, mu2 of row yc-1    (needs c rows yc-2 .. yc)
+//   update of row yc-2      (needs c and mu rows yc-3 .. yc-1)
+// so each order parameter is summed once per node (plus a 4-column, 4-row
+// halo per block) and no c or mu array ever reaches HBM.
 // ---------------------------------------------------------------------------
-template <typename S, typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH>
+__global__ void __launch_bounds__(BLOCK)
 k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
                 const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
 {
-    constexpr int HX = TX + 4, HY = TY + 4;  // c tile, halo 2
-    constexpr int MX = TX + 2, MY = TY + 2;  // mu tile, halo 1
-    constexpr int NT = TX * TY;
-    __shared__ R sc1[HY * HX], sc2[HY * HX], sm1[MY * MX], sm2[MY * MX];
-
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    __shared__ R sc1[5][BLOCK], sc2[5][BLOCK];  // c rings (row r in slot (r + 10) % 5)
+    __shared__ R sm1[3][BLOCK], sm2[3][BLOCK];  // mu rings (row r in slot (r + 9) % 3)
     const long long PL = g.plane;
-    const int tid = threadIdx.x;
-
-    // phase 1: c_i = sum_k f^i_k (Eq. 13a) on the tile + halo 2
-    for (int i = tid; i < HX * HY; i += NT) {
-        const int hx = i % HX, hy = i / HX;
-        int x = x0 - 2 + hx, y = y0 - 2 + hy;
-        R a = R(0), b = R(0);
-        // only x in [-2, nx+1], y in [-2, ny+1] are ever read; the rest of a
-        // tile that overhangs a small lattice is left at zero
-        bool inside = x < g.nx + 2 && y < g.ny + 2;
-        if (x < 0 || x >= g.nx) {
-            if (g.edge[0] == EDGE_PERIODIC) x = x < 0 ? x + g.nx : x - g.nx; else inside = false;
-        }
-        if (y < 0 || y >= g.ny) {
-            if (g.edge[2] == EDGE_PERIODIC) y = y < 0 ? y + g.ny : y - g.ny; else inside = false;
-        }
-        if (inside) {
-            const S* p = fA + (long long)y * g.pitch + x;
-#pragma unroll
-            for (int k = 0; k < 9; k++) a += R(ldg(p + k * PL));
-#pragma unroll
-            for (int k = 0; k < 9; k++) b += R(ldg(p + (9 + k) * PL));
-        }
-        sc1[i] = a;
-        sc2[i] = b;
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * (BLOCK - 4);
+    const int xs = x0 - 2 + t;  // this thread's column, in [-2, nx + BLOCK]
+    // wrapped column (periodic x) and whether it holds data at all; only
+    // columns -2 .. nx+1 are ever read
+    int xw = xs;
+    bool col_in = xs < g.nx + 2;
+    if (xs < 0 || xs >= g.nx) {
+        if (g.edge[0] == EDGE_PERIODIC) xw = xs < 0 ? xs + g.nx : xs - g.nx;
+        else col_in = false;
     }
-    __syncthreads();
+    const bool updater = t >= 2 && t < BLOCK - 2 && xs < g.nx;
+    const int y0 = blockIdx.y * ROWS;
+    const int y1 = min(y0 + ROWS, g.ny);
 
-    // phase 2: mu_1, mu_2 (Eq. 8 with Eq. 20b) on the tile + halo 1
-    for (int i = tid; i < MX * MY; i += NT) {
-        const int mx = i % MX, my = i / MX;
-        const int c = (my + 1) * HX + (mx + 1);
-        R v1[9], v2[9];
-#pragma unroll
-        for (int k = 0; k < 9; k++) {
-            v1[k] = sc1[c + ey(k) * HX + ex(k)];
-            v2[k] = sc2[c + ey(k) * HX + ex(k)];
+    for (int yc = y0 - 2; yc < y1 + 2; yc++) {
+        const int yu = yc - 2;  // row updated in this iteration
+        bool upd = updater && yu >= y0;
+        long long ou = 0;
+        if (upd) {
+            ou = (long long)yu * g.pitch + xs;
+            upd = (cls[ou] & CLS_INTERIOR) != 0;
         }
-        R mu1, mu2;
-        chem_pot(P, v1[0], v2[0], lap9(v1), lap9(v2), mu1, mu2);
-        sm1[i] = mu1;
-        sm2[i] = mu2;
-    }
-    __syncthreads();
-
-    // phase 3: per-node update
-    const int tx = tid % TX, ty = tid / TX;
-    const int x = x0 + tx, y = y0 + ty;
-    if (x >= g.nx || y >= g.ny) return;
-    const long long o = (long long)y * g.pitch + x;
-    if (!(cls[o] & CLS_INTERIOR)) return;
-
-    Macro<R> m;
-    {
-        const int c = (ty + 2) * HX + (tx + 2);
-        const int cm = (ty + 1) * MX + (tx + 1);
-        R v1[9], v2[9], w1[9], w2[9];
+        // g and c_i u of the update node: first touches of HBM, issued early
+        R gv[9], cp[4];
+        if (PREFETCH && upd) {
 #pragma unroll
-        for (int k = 0; k < 9; k++) {
-            v1[k] = sc1[c + ey(k) * HX + ex(k)];
-            v2[k] = sc2[c + ey(k) * HX + ex(k)];
-            w1[k] = sm1[cm + ey(k) * MX + ex(k)];
-            w2[k] = sm2[cm + ey(k) * MX + ex(k)];
+            for (int k = 0; k < 9; k++) gv[k] = R(ldg(fA + (18 + k) * PL + ou));
+#pragma unroll
+            for (int q = 0; q < 4; q++) cp[q] = R(cu[q * PL + ou]);
         }
-        m.c1 = v1[0];
-        m.c2 = v2[0];
-        m.mu1 = w1[0];
-        m.mu2 = w2[0];
-        grad9(v1, m.g1x, m.g1y);
-        grad9(v2, m.g2x, m.g2y);
-        m.lm1 = lap9(w1);
-        m.lm2 = lap9(w2);
-        m.rho = m.c1 * P.rho[0] + m.c2 * P.rho[1] + (R(1) - m.c1 - m.c2) * P.rho[2];
-    }
-    R gv[9];
+        // 1) c of row yc (Eq. 13a)
+        {
+            int yw = yc;
+            bool in = col_in && yc < g.ny + 2;
+            if (yc < 0 || yc >= g.ny) {
+                if (g.edge[2] == EDGE_PERIODIC) yw = yc < 0 ? yc + g.ny : yc - g.ny;
+                else in = false;
+            }
+            R a = R(0), b = R(0);
+            if (in) {
+                const S* q = fA + (long long)yw * g.pitch + xw;
+                R v[18];
 #pragma unroll
-    for (int k = 0; k < 9; k++) gv[k] = R(ldg(fA + (18 + k) * PL + o));
-    Hydro<R> h;
-    hydro_from_g(P, m, gv, h);
-
-    // Eq. 19: d/dt (c_i u) from the stored previous product
-    const R c1ux = m.c1 * h.ux, c1uy = m.c1 * h.uy, c2ux = m.c2 * h.ux, c2uy = m.c2 * h.uy;
-    const R d1x = c1ux - R(cu[0 * PL + o]), d1y = c1uy - R(cu[1 * PL + o]);
-    const R d2x = c2ux - R(cu[2 * PL + o]), d2y = c2uy - R(cu[3 * PL + o]);
-    cu[0 * PL + o] = S(c1ux);
-    cu[1 * PL + o] = S(c1uy);
-    cu[2 * PL + o] = S(c2ux);
-    cu[3 * PL + o] = S(c2uy);
-
-    static_for<0, 9>([&](auto kc) {
-        constexpr int K = decltype(kc)::value;
-        const R f1k = R(ldg(fA + K * PL + o));
-        const R f2k = R(ldg(fA + (9 + K) * PL + o));
-        R o1, o2, og;
-        collide_k<K>(P, m, h, d1x, d1y, d2x, d2y, f1k, f2k, gv[K], o1, o2, og);
-        const long long d = (K == 0) ? o : wrap_off(g, x + ex(K), y + ey(K));
-        fB[K * PL + d] = S(o1);
-        fB[(9 + K) * PL + d] = S(o2);
-        fB[(18 + K) * PL + d] = S(og);
-    });
+                for (int k = 0; k < 18; k++) v[k] = R(ldg(q + k * PL));
+#pragma unroll
+                for (int k = 0; k < 9; k++) {
+                    a += v[k];
+                    b += v[9 + k];
+                }
+            }
+            const int sl = (yc + 10) % 5;
+            sc1[sl][t] = a;
+            sc2[sl][t] = b;
+        }
+        __syncthreads();
+        // 2) mu of row yc-1 (Eq. 8 with Eq. 20b)
+        if (yc >= y0 && t >= 1 && t < BLOCK - 1) {
+            const int sm = (yc + 9) % 5, s0 = (yc + 8) % 5, sp = (yc + 10) % 5;  // rows yc-1, yc-2, yc
+            R v1[9], v2[9];
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                const int sl = ey(k) == 0 ? sm : (ey(k) > 0 ? sp : s0);
+                v1[k] = sc1[sl][t + ex(k)];
+                v2[k] = sc2[sl][t + ex(k)];
+            }
+            R mu1, mu2;
+            chem_pot(P, v1[0], v2[0], lap9(v1), lap9(v2), mu1, mu2);
+            const int ml = (yc + 8) % 3;  // slot of row yc-1
+            sm1[ml][t] = mu1;
+            sm2[ml][t] = mu2;
+        }
+        __syncthreads();
+        // 3) update of row yu = yc-2
+        if (!upd) continue;
+        Macro<R> m;
+        {
+            const int cm = (yc + 7) % 5, c0 = (yc + 8) % 5, cpl = (yc + 9) % 5;  // c rows yu-1, yu, yu+1
+            const int mm = (yc + 6) % 3, m0 = (yc + 7) % 3, mp = (yc + 8) % 3;     // mu rows yu-1, yu, yu+1
+            R v1[9], v2[9], w1[9], w2[9];
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                const int sl = ey(k) == 0 ? c0 : (ey(k) > 0 ? cpl : cm);
+                const int ml = ey(k) == 0 ? m0 : (ey(k) > 0 ? mp : mm);
+                v1[k] = sc1[sl][t + ex(k)];
+                v2[k] = sc2[sl][t + ex(k)];
+                w1[k] = sm1[ml][t + ex(k)];
+                w2[k] = sm2[ml][t + ex(k)];
+            }
+            m.c1 = v1[0];
+            m.c2 = v2[0];
+            m.mu1 = w1[0];
+            m.mu2 = w2[0];
+            grad9(v1, m.g1x, m.g1y);
+            grad9(v2, m.g2x, m.g2y);
+            m.lm1 = lap9(w1);
+            m.lm2 = lap9(w2);
+            m.rho = density(P, m.c1, m.c2);
+        }
+        if (!PREFETCH) {
+#pragma unroll
+            for (int k = 0; k < 9; k++) gv[k] = R(ldg(fA + (18 + k) * PL + ou));
+#pragma unroll
+            for (int q = 0; q < 4; q++) cp[q] = R(cu[q * PL + ou]);
+        }
+        Hydro<R> h;
+        hydro_from_g(P, m, gv, h);
+        // Eq. 19: d/dt (c_i u) against the stored product of the previous step
+        const R c1ux = m.c1 * h.ux, c1uy = m.c1 * h.uy, c2ux = m.c2 * h.ux, c2uy = m.c2 * h.uy;
+        cu[0 * PL + ou] = S(c1ux);
+        cu[1 * PL + ou] = S(c1uy);
+        cu[2 * PL + ou] = S(c2ux);
+        cu[3 * PL + ou] = S(c2uy);
+        Collider<R> col;
+        col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
+        static_for<0, 9>([&](auto kc) {
+            constexpr int K = decltype(kc)::value;
+            const R f1k = R(ldg(fA + K * PL + ou));
+            const R f2k = R(ldg(fA + (9 + K) * PL + ou));
+            R o1, o2, og;
+            col.template post<K>(f1k, f2k, gv[K], o1, o2, og);
+            const long long d = (K == 0) ? ou : wrap_off(g, xs + ex(K), yu + ey(K));
+            fB[K * PL + d] = S(o1);
+            fB[(9 + K) * PL + d] = S(o2);
+            fB[(18 + K) * PL + d] = S(og);
+        });
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -252,7 +284,7 @@ __device__ __forceinline__ void window_macros(const Geo& g, const uint8_t* __res
     grad9(v2, m.g2x, m.g2y);
     m.lm1 = lap9(w1);
     m.lm2 = lap9(w2);
-    m.rho = m.c1 * P.rho[0] + m.c2 * P.rho[1] + (R(1) - m.c1 - m.c2) * P.rho[2];
+    m.rho = density(P, m.c1, m.c2);
 }
 
 template <typename S, typename R>
@@ -344,12 +376,14 @@ k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
         cu[1 * PL + o] = S(c1uy);
         cu[2 * PL + o] = S(c2ux);
         cu[3 * PL + o] = S(c2uy);
+        Collider<R> col;
+        col.build(P, m, h, d1x, d1y, d2x, d2y);
         static_for<0, 9>([&](auto kc) {
             constexpr int K = decltype(kc)::value;
             const R f1k = R(ldg(fA + K * PL + o));
             const R f2k = R(ldg(fA + (9 + K) * PL + o));
             R o1, o2, og;
-            collide_k<K>(P, m, h, d1x, d1y, d2x, d2y, f1k, f2k, gv[K], o1, o2, og);
+            col.template post<K>(f1k, f2k, gv[K], o1, o2, og);
             push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
         });
     } else if (kind == ST_LID) {
@@ -366,9 +400,6 @@ k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
         h.ux = P.lid_u;
         h.uy = R(0);
         h.usq = P.lid_u * P.lid_u;
-        const R a = P.aM[0] * m.lm1 + P.aM[1] * m.lm2;
-        h.Fax = h.ux * a;
-        h.Fay = R(0);
         const R c1ux = m.c1 * h.ux, c2ux = m.c2 * h.ux;
         const R d1x = c1ux - R(cu[0 * PL + o]), d1y = R(0) - R(cu[1 * PL + o]);
         const R d2x = c2ux - R(cu[2 * PL + o]), d2y = R(0) - R(cu[3 * PL + o]);
@@ -376,6 +407,8 @@ k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
         cu[1 * PL + o] = S(0);
         cu[2 * PL + o] = S(c2ux);
         cu[3 * PL + o] = S(0);
+        Collider<R> col;
+        col.build(P, m, h, d1x, d1y, d2x, d2y);
         static_for<0, 9>([&](auto kc) {
             constexpr int K = decltype(kc)::value;
             R e1u, e2u, egu, e1f, e2f, egf;
@@ -386,7 +419,7 @@ k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
             const R f2k = e2u + (R(ldg(fA + (9 + K) * PL + of)) - e2f);
             const R gk = egu + (gf[K] - egf);
             R o1, o2, og;
-            collide_k<K>(P, m, h, d1x, d1y, d2x, d2y, f1k, f2k, gk, o1, o2, og);
+            col.template post<K>(f1k, f2k, gk, o1, o2, og);
             push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
             // slots fed from beyond the lid receive nothing: keep them zero
             if constexpr (ey(K) == -1) {
@@ -471,7 +504,7 @@ __global__ void k_read_fields(const S* __restrict__ fA, const uint8_t* __restric
             h.ux = P.lid_u;
             h.uy = R(0);
         }
-        const R mu3 = -(P.l3_l1 * m.mu1 + P.l3_l2 * m.mu2);
+        const R mu3 = -fma(P.l3_l1, m.mu1, P.l3_l2 * m.mu2);
         v[0] = m.c1;
         v[1] = m.c2;
         v[2] = R(1) - m.c1 - m.c2;
@@ -490,21 +523,6 @@ __global__ void k_read_fields(const S* __restrict__ fA, const uint8_t* __restric
             plane++;
         }
     }
-}
-
-// Raw state to dense FP64 planes [31][ny][nx].
-template <typename S>
-__global__ void k_state_to_f64(const S* __restrict__ fA, const S* __restrict__ cu, double* __restrict__ out, Geo g)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= g.nx) return;
-    const long long PL = g.plane;
-    const long long o = (long long)y * g.pitch + x;
-    const long long n = (long long)y * g.nx + x;
-    const long long N = (long long)g.nx * g.ny;
-    for (int q = 0; q < 27; q++) out[q * N + n] = to_d(fA[q * PL + o]);
-    for (int q = 0; q < 4; q++) out[(27 + q) * N + n] = to_d(cu[q * PL + o]);
 }
 
 // ---------------------------------------------------------------------------

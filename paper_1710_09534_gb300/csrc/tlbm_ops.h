@@ -27,8 +27,9 @@ struct Ops {
 const Ops& ops_f64();
 const Ops& ops_f32();
 
-// Tile of the fused interior kernel for each precision.
-constexpr int kTileX64 = 32, kTileY64 = 8;
-constexpr int kTileX32 = 32, kTileY32 = 8;
+// Fused interior kernel: threads per block (one column each, 4 of them halo)
+// and rows marched per block, per precision.
+constexpr int kBlock64 = 64, kRows64 = 64;
+constexpr int kBlock32 = 64, kRows32 = 64;
 
 }  // namespace tlb

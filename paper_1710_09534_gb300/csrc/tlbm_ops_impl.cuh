@@ -15,12 +15,23 @@ inline Prm<R> cast_prm(const Prm<double>& d)
         r.nu[i] = R(d.nu[i]);
     }
     for (int i = 0; i < 2; i++) {
+        r.k34Dlam[i] = R(d.k34Dlam[i]);
         r.eta[i] = R(d.eta[i]);
         r.inv_tau[i] = R(d.inv_tau[i]);
+        r.omt[i] = R(d.omt[i]);
         r.src_f[i] = R(d.src_f[i]);
+        r.e0[i] = R(d.e0[i]);
+        r.drho[i] = R(d.drho[i]);
+        r.dnu[i] = R(d.dnu[i]);
         r.aM[i] = R(d.aM[i]);
+        for (int c = 0; c < 2; c++) {
+            r.aw[i][c] = R(d.aw[i][c]);
+            r.bw[i][c] = R(d.bw[i][c]);
+            r.sw[i][c] = R(d.sw[i][c]);
+        }
     }
     r.lamT = R(d.lamT);
+    r.two_lamT = R(d.two_lamT);
     r.k12D = R(d.k12D);
     r.k34D = R(d.k34D);
     r.k4D = R(d.k4D);
@@ -35,14 +46,15 @@ inline Prm<R> cast_prm(const Prm<double>& d)
     return r;
 }
 
-template <typename S, typename R, int TX, int TY>
+template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH>
 struct OpsImpl {
     static cudaError_t interior(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
                                 const Prm<double>& Pd, cudaStream_t s)
     {
         const Prm<R> P = cast_prm<R>(Pd);
-        dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-        k_step_interior<S, R, TX, TY><<<grid, TX * TY, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, g, P);
+        constexpr int TX = BLOCK - 4;
+        dim3 grid((g.nx + TX - 1) / TX, (g.ny + ROWS - 1) / ROWS);
+        k_step_interior<S, R, BLOCK, ROWS, PREFETCH><<<grid, BLOCK, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, g, P);
         return cudaGetLastError();
     }
     static cudaError_t wall(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
