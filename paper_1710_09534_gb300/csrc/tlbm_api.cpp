@@ -71,8 +71,9 @@ Layout layout_for(int nx, int ny, int precision)
         off = align_up(off + bytes, kAlign);
         return at;
     };
-    L.fA = take(27 * L.plane * es);
-    L.fB = take(27 * L.plane * es);
+    const int nd = tlb::ndist_for(precision);
+    L.fA = take(nd * L.plane * es);
+    L.fB = take(nd * L.plane * es);
     L.cu = take(4 * L.plane * es);
     L.cls = take(L.plane);
     L.list = take((int64_t)nx * ny * 4);
@@ -408,7 +409,7 @@ int tlb_set_fields(tlb_lattice* L, const double* c1, const double* c2, const dou
         if (src[q]) TLB_CUDA(cudaMemcpyAsync(stage + q * N, src[q], N * 8, cudaMemcpyHostToDevice, L->stream));
     rc = set_fields_impl(L, stage, stage + N, stage + 2 * N, stage + 3 * N, p ? stage + 4 * N : nullptr);
     if (rc) return rc;
-    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(27 * L->lay.plane * L->ops->elem), L->stream));
+    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(L->ops->ndist * L->lay.plane * L->ops->elem), L->stream));
     TLB_CUDA(cudaStreamSynchronize(L->stream));
     return ok();
 }
@@ -422,7 +423,7 @@ int tlb_set_fields_device(tlb_lattice* L, const double* c1, const double* c2, co
     if (!c1 || !c2 || !ux || !uy) return fail(TLB_EINVAL, "c1, c2, ux, uy are required");
     rc = set_fields_impl(L, c1, c2, ux, uy, p);
     if (rc) return rc;
-    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(27 * L->lay.plane * L->ops->elem), L->stream));
+    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(L->ops->ndist * L->lay.plane * L->ops->elem), L->stream));
     return ok();
 }
 
@@ -488,7 +489,7 @@ int tlb_read_fields(tlb_lattice* L, uint32_t mask, double* host_out)
     double* stage = (double*)L->bufB();
     TLB_CUDA(L->ops->read(L->bufA(), L->dcls(), stage, mask, L->geo, L->prm, L->stream));
     TLB_CUDA(cudaMemcpyAsync(host_out, stage, (size_t)popcount10(mask) * N * 8, cudaMemcpyDeviceToHost, L->stream));
-    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(27 * L->lay.plane * L->ops->elem), L->stream));
+    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(L->ops->ndist * L->lay.plane * L->ops->elem), L->stream));
     TLB_CUDA(cudaStreamSynchronize(L->stream));
     return ok();
 }
@@ -518,32 +519,41 @@ int tlb_read_state(tlb_lattice* L, double* host_out)
     int rc = check_handle(L);
     if (rc) return rc;
     if (!host_out) return fail(TLB_EINVAL, "out is null");
-    const size_t es = L->ops->elem, PL = (size_t)L->lay.plane;
-    std::vector<char> raw(31 * PL * es);
-    TLB_CUDA(cudaMemcpyAsync(raw.data(), L->bufA(), 27 * PL * es, cudaMemcpyDeviceToHost, L->stream));
-    TLB_CUDA(cudaMemcpyAsync(raw.data() + 27 * PL * es, L->cu(), 4 * PL * es, cudaMemcpyDeviceToHost, L->stream));
+    const size_t es = L->ops->elem, PL = (size_t)L->lay.plane, nd = (size_t)L->ops->ndist;
+    std::vector<char> raw((nd + 4) * PL * es);
+    TLB_CUDA(cudaMemcpyAsync(raw.data(), L->bufA(), nd * PL * es, cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaMemcpyAsync(raw.data() + nd * PL * es, L->cu(), 4 * PL * es, cudaMemcpyDeviceToHost, L->stream));
     TLB_CUDA(cudaStreamSynchronize(L->stream));
+    auto at = [&](size_t q, size_t i) {
+        const size_t src = q * PL + i;
+        if (es == 8) {
+            double v;
+            memcpy(&v, raw.data() + src * 8, 8);
+            return v;
+        }
+        float f;
+        memcpy(&f, raw.data() + src * 4, 4);
+        return (double)f;
+    };
     const size_t N = (size_t)L->n();
-    for (int q = 0; q < 31; q++)
+    for (int q = 0; q < 31; q++) {
+        // raw plane of output plane q: 27 distributions, then the 4 c_i u planes
+        const size_t rq = q < 27 ? (size_t)q : nd + (size_t)(q - 27);
         for (int y = 0; y < L->ny; y++)
             for (int x = 0; x < L->nx; x++) {
-                const size_t src = q * PL + (size_t)y * L->lay.pitch + x;
-                double v;
-                if (es == 8) memcpy(&v, raw.data() + src * 8, 8);
-                else {
-                    float f;
-                    memcpy(&f, raw.data() + src * 4, 4);
-                    v = f;
-                }
+                const size_t i = (size_t)y * L->lay.pitch + x;
+                double v = at(rq, i);
+                if (nd > 27 && (q == 0 || q == 9)) v += at(q == 0 ? 27 : 28, i);  // rest population hi + lo
                 host_out[q * N + (size_t)y * L->nx + x] = v;
             }
+    }
     return ok();
 }
 
 int64_t tlb_state_bytes(tlb_lattice* L)
 {
     if (!L) return fail(TLB_EINVAL, "null lattice handle");
-    return 31 * L->lay.plane * (int64_t)L->ops->elem;
+    return (L->ops->ndist + 4) * L->lay.plane * (int64_t)L->ops->elem;
 }
 
 int tlb_export_state(tlb_lattice* L, void* host_buf, int64_t bytes)
@@ -552,7 +562,7 @@ int tlb_export_state(tlb_lattice* L, void* host_buf, int64_t bytes)
     if (rc) return rc;
     const int64_t need = tlb_state_bytes(L);
     if (!host_buf || bytes < need) return fail(TLB_EINVAL, "buffer needs %lld bytes", (long long)need);
-    const size_t a = 27 * (size_t)L->lay.plane * L->ops->elem;
+    const size_t a = (size_t)L->ops->ndist * L->lay.plane * L->ops->elem;
     TLB_CUDA(cudaMemcpyAsync(host_buf, L->bufA(), a, cudaMemcpyDeviceToHost, L->stream));
     TLB_CUDA(cudaMemcpyAsync((char*)host_buf + a, L->cu(), (size_t)need - a, cudaMemcpyDeviceToHost, L->stream));
     TLB_CUDA(cudaStreamSynchronize(L->stream));
@@ -566,7 +576,7 @@ int tlb_import_state(tlb_lattice* L, const void* host_buf, int64_t bytes)
     const int64_t need = tlb_state_bytes(L);
     if (!host_buf || bytes != need) return fail(TLB_EINVAL, "state must be exactly %lld bytes", (long long)need);
     if (!L->have_params) return fail(TLB_ESTATE, "set_params first");
-    const size_t a = 27 * (size_t)L->lay.plane * L->ops->elem;
+    const size_t a = (size_t)L->ops->ndist * L->lay.plane * L->ops->elem;
     TLB_CUDA(cudaMemcpyAsync(L->bufA(), host_buf, a, cudaMemcpyHostToDevice, L->stream));
     TLB_CUDA(cudaMemcpyAsync(L->cu(), (const char*)host_buf + a, (size_t)need - a, cudaMemcpyHostToDevice, L->stream));
     TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, a, L->stream));

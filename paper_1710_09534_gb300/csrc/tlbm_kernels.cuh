@@ -29,6 +29,103 @@ __device__ __forceinline__ void static_for(F&& f)
 template <typename S>
 __device__ __forceinline__ double to_d(S v) { return (double)v; }
 
+// c_i = sum_k f^i_k (Eq. 13a): the eight moving populations first, the rest
+// population last, so that the large term is rounded once.
+template <typename R>
+__device__ __forceinline__ R sum9(const R* v)
+{
+    return v[0] + (((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8])));
+}
+
+// FP32 storage keeps the two rest populations f^1_0, f^2_0 as unevaluated
+// float pairs hi + lo (planes 0/9 and 27/28), so that the per-node update
+// can conserve sum_k f^i_k (Eq. 1a conserves c_i) to ~2^-48 instead of to one
+// FP32 rounding per node and step.  FP64 storage has 27 planes.
+template <typename S>
+struct Store {
+    static constexpr bool kLo = std::is_same<S, float>::value;
+    static constexpr int kPlanes = kLo ? 29 : 27;
+};
+
+// Error-free transformation of a sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Unevaluated pair hi + lo accumulated with TwoSum (compensated summation).
+struct FF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float e;
+        two_sum(hi, x, hi, e);
+        lo += e;
+    }
+};
+
+// (a.hi + a.lo) - (b.hi + b.lo) rounded to a normalised pair.
+__device__ __forceinline__ void ff_sub(const FF& a, const FF& b, float& hi, float& lo)
+{
+    float s, e;
+    two_sum(a.hi, -b.hi, s, e);
+    const float t = e + (a.lo - b.lo);
+    hi = s + t;
+    lo = t - (hi - s);
+}
+
+// All nine directions of one node.  load(kc, f1k, f2k) fetches the
+// pre-collision order-parameter populations of direction kc (for kc = 0 the
+// hi part), load_lo(f1lo, f2lo) the lo parts of the rest populations (FP32
+// storage), store(kc, o1, o2, og) streams the post-collision triple and
+// store_lo(o1lo, o2lo) the rest lo parts.  With FP32 storage the rest
+// population is the exact input sum minus the eight moving outputs, so the
+// stored sum_k f'^i_k equals the stored sum_k f^i_k to ~2^-48 (Eq. 1a
+// conserves c_i; sum_k f^eq_k = c_i, sum_k F_k = 0); FP64 uses the direct form.
+template <typename S, typename R, typename Load, typename LoadLo, typename St, typename StLo>
+__device__ __forceinline__ void collide_all(const Collider<R>& col, const R gv[9], Load load, LoadLo load_lo,
+                                            St store, StLo store_lo)
+{
+    constexpr bool ff = Store<S>::kLo;
+    FF in1, in2, out1, out2;
+    static_for<1, 9>([&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        R f1k, f2k, o1, o2, og;
+        load(kc, f1k, f2k);
+        col.template post<K>(f1k, f2k, gv[K], o1, o2, og);
+        if constexpr (ff) {
+            in1.add(f1k);
+            in2.add(f2k);
+            out1.add(o1);
+            out2.add(o2);
+        }
+        store(kc, o1, o2, og);
+    });
+    std::integral_constant<int, 0> k0;
+    R f10, f20, o1, o2, og;
+    load(k0, f10, f20);
+    if constexpr (ff) {
+        R l1, l2;
+        load_lo(l1, l2);
+        // the collision sees the rest population as hi + lo
+        col.template post<0>(f10 + l1, f20 + l2, gv[0], o1, o2, og);
+        in1.add(f10);
+        in1.add(l1);
+        in2.add(f20);
+        in2.add(l2);
+        R h1, h2, lo1, lo2;
+        ff_sub(in1, out1, h1, lo1);
+        ff_sub(in2, out2, h2, lo2);
+        store(k0, h1, h2, og);
+        store_lo(lo1, lo2);
+    } else {
+        col.template post<0>(f10, f20, gv[0], o1, o2, og);
+        store(k0, o1, o2, og);
+    }
+}
+
 // Periodic wrap of a destination that may leave the lattice by one node on a
 // periodic axis (interior nodes never reach a non-periodic edge).
 __device__ __forceinline__ long long wrap_off(const Geo& g, int x, int y)
@@ -103,11 +200,12 @@ k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu
                 R v[18];
 #pragma unroll
                 for (int k = 0; k < 18; k++) v[k] = R(ldg(q + k * PL));
-#pragma unroll
-                for (int k = 0; k < 9; k++) {
-                    a += v[k];
-                    b += v[9 + k];
+                if constexpr (Store<S>::kLo) {
+                    v[0] += R(ldg(q + 27 * PL));
+                    v[9] += R(ldg(q + 28 * PL));
                 }
+                a = sum9(v);
+                b = sum9(v + 9);
             }
             const int sl = (yc + 10) % 5;
             sc1[sl][t] = a;
@@ -173,17 +271,27 @@ k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu
         cu[3 * PL + ou] = S(c2uy);
         Collider<R> col;
         col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
-        static_for<0, 9>([&](auto kc) {
-            constexpr int K = decltype(kc)::value;
-            const R f1k = R(ldg(fA + K * PL + ou));
-            const R f2k = R(ldg(fA + (9 + K) * PL + ou));
-            R o1, o2, og;
-            col.template post<K>(f1k, f2k, gv[K], o1, o2, og);
-            const long long d = (K == 0) ? ou : wrap_off(g, xs + ex(K), yu + ey(K));
-            fB[K * PL + d] = S(o1);
-            fB[(9 + K) * PL + d] = S(o2);
-            fB[(18 + K) * PL + d] = S(og);
-        });
+        collide_all<S, R>(col, gv,
+            [&](auto kc, R& f1k, R& f2k) {
+                constexpr int K = decltype(kc)::value;
+                f1k = R(ldg(fA + K * PL + ou));
+                f2k = R(ldg(fA + (9 + K) * PL + ou));
+            },
+            [&](R& l1, R& l2) {
+                l1 = R(ldg(fA + 27 * PL + ou));
+                l2 = R(ldg(fA + 28 * PL + ou));
+            },
+            [&](auto kc, R o1, R o2, R og) {
+                constexpr int K = decltype(kc)::value;
+                const long long d = (K == 0) ? ou : wrap_off(g, xs + ex(K), yu + ey(K));
+                fB[K * PL + d] = S(o1);
+                fB[(9 + K) * PL + d] = S(o2);
+                fB[(18 + K) * PL + d] = S(og);
+            },
+            [&](R l1, R l2) {
+                fB[27 * PL + ou] = S(l1);
+                fB[28 * PL + ou] = S(l2);
+            });
     }
 }
 
@@ -293,13 +401,15 @@ struct DistFetch {
     long long PL;
     __device__ __forceinline__ void operator()(long long off, R& a, R& b) const
     {
-        R s1 = R(0), s2 = R(0);
+        R v[18];
 #pragma unroll
-        for (int k = 0; k < 9; k++) s1 += R(ldg(f + k * PL + off));
-#pragma unroll
-        for (int k = 0; k < 9; k++) s2 += R(ldg(f + (9 + k) * PL + off));
-        a = s1;
-        b = s2;
+        for (int k = 0; k < 18; k++) v[k] = R(ldg(f + k * PL + off));
+        if constexpr (Store<S>::kLo) {
+            v[0] += R(ldg(f + 27 * PL + off));
+            v[9] += R(ldg(f + 28 * PL + off));
+        }
+        a = sum9(v);
+        b = sum9(v + 9);
     }
 };
 
@@ -378,14 +488,24 @@ k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
         cu[3 * PL + o] = S(c2uy);
         Collider<R> col;
         col.build(P, m, h, d1x, d1y, d2x, d2y);
-        static_for<0, 9>([&](auto kc) {
-            constexpr int K = decltype(kc)::value;
-            const R f1k = R(ldg(fA + K * PL + o));
-            const R f2k = R(ldg(fA + (9 + K) * PL + o));
-            R o1, o2, og;
-            col.template post<K>(f1k, f2k, gv[K], o1, o2, og);
-            push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
-        });
+        collide_all<S, R>(col, gv,
+            [&](auto kc, R& f1k, R& f2k) {
+                constexpr int K = decltype(kc)::value;
+                f1k = R(ldg(fA + K * PL + o));
+                f2k = R(ldg(fA + (9 + K) * PL + o));
+            },
+            [&](R& l1, R& l2) {
+                l1 = R(ldg(fA + 27 * PL + o));
+                l2 = R(ldg(fA + 28 * PL + o));
+            },
+            [&](auto kc, R o1, R o2, R og) {
+                constexpr int K = decltype(kc)::value;
+                push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
+            },
+            [&](R l1, R l2) {
+                fB[27 * PL + o] = S(l1);
+                fB[28 * PL + o] = S(l2);
+            });
     } else if (kind == ST_LID) {
         // x_f is the node below; x_u takes its macros and gradients, u = (U0, 0)
         const long long of = o - g.pitch;
@@ -409,28 +529,51 @@ k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
         cu[3 * PL + o] = S(0);
         Collider<R> col;
         col.build(P, m, h, d1x, d1y, d2x, d2y);
-        static_for<0, 9>([&](auto kc) {
-            constexpr int K = decltype(kc)::value;
+        // Eq. 51: f(x_u) = f^eq(x_u) + [f(x_f) - f^eq(x_f)], for f^1, f^2 and g
+        R gu[9], f1u[9], f2u[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
             R e1u, e2u, egu, e1f, e2f, egf;
-            equilibria(K, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, hf.p, h.ux, h.uy, e1u, e2u, egu);
-            equilibria(K, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, hf.p, hf.ux, hf.uy, e1f, e2f, egf);
-            // Eq. 51: f(x_u) = f^eq(x_u) + [f(x_f) - f^eq(x_f)]
-            const R f1k = e1u + (R(ldg(fA + K * PL + of)) - e1f);
-            const R f2k = e2u + (R(ldg(fA + (9 + K) * PL + of)) - e2f);
-            const R gk = egu + (gf[K] - egf);
-            R o1, o2, og;
-            col.template post<K>(f1k, f2k, gk, o1, o2, og);
-            push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
-            // slots fed from beyond the lid receive nothing: keep them zero
-            if constexpr (ey(K) == -1) {
-                long long dummy = 0;
-                if (site_of(g, cls, x - ex(K), y + 1, dummy) == ST_VOID) {
-                    fB[K * PL + o] = S(0);
-                    fB[(9 + K) * PL + o] = S(0);
-                    fB[(18 + K) * PL + o] = S(0);
+            equilibria(k, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, hf.p, h.ux, h.uy, e1u, e2u, egu);
+            equilibria(k, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, hf.p, hf.ux, hf.uy, e1f, e2f, egf);
+            R ff1 = R(ldg(fA + k * PL + of)), ff2 = R(ldg(fA + (9 + k) * PL + of));
+            if constexpr (Store<S>::kLo) {
+                if (k == 0) {
+                    ff1 += R(ldg(fA + 27 * PL + of));
+                    ff2 += R(ldg(fA + 28 * PL + of));
                 }
             }
-        });
+            f1u[k] = e1u + (ff1 - e1f);
+            f2u[k] = e2u + (ff2 - e2f);
+            gu[k] = egu + (gf[k] - egf);
+        }
+        collide_all<S, R>(col, gu,
+            [&](auto kc, R& f1k, R& f2k) {
+                constexpr int K = decltype(kc)::value;
+                f1k = f1u[K];
+                f2k = f2u[K];
+            },
+            [&](R& l1, R& l2) {
+                l1 = R(0);
+                l2 = R(0);
+            },
+            [&](auto kc, R o1, R o2, R og) {
+                constexpr int K = decltype(kc)::value;
+                push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
+                // slots fed from beyond the lid receive nothing: keep them zero
+                if constexpr (ey(K) == -1) {
+                    long long dummy = 0;
+                    if (site_of(g, cls, x - ex(K), y + 1, dummy) == ST_VOID) {
+                        fB[K * PL + o] = S(0);
+                        fB[(9 + K) * PL + o] = S(0);
+                        fB[(18 + K) * PL + o] = S(0);
+                    }
+                }
+            },
+            [&](R l1, R l2) {
+                fB[27 * PL + o] = S(l1);
+                fB[28 * PL + o] = S(l2);
+            });
     }
 }
 
@@ -451,6 +594,10 @@ __global__ void k_init(S* __restrict__ fA, S* __restrict__ cu, const uint8_t* __
     const long long o = (long long)y * g.pitch + x;
     const long long n = (long long)y * g.nx + x;
     const int kind = cls[o] & CLS_KIND_MASK;
+    if constexpr (Store<S>::kLo) {
+        fA[27 * PL + o] = S(0);
+        fA[28 * PL + o] = S(0);
+    }
     if (!fluidlike(kind)) {
         for (int q = 0; q < 27; q++) fA[q * PL + o] = S(0);
         for (int q = 0; q < 4; q++) cu[q * PL + o] = S(0);
@@ -545,11 +692,14 @@ k_mass_partials(const S* __restrict__ fA, const uint8_t* __restrict__ cls, doubl
         const int kind = cls[o] & CLS_KIND_MASK;
         if (!fluidlike(kind)) continue;
         if (kind == ST_LID) o -= g.pitch;
-        R a = R(0), b = R(0), gs = R(0);
-        for (int k = 0; k < 9; k++) a += R(fA[k * PL + o]);
-        for (int k = 0; k < 9; k++) b += R(fA[(9 + k) * PL + o]);
-        for (int k = 0; k < 9; k++) gs += R(fA[(18 + k) * PL + o]);
-        const double c1 = a, c2 = b;
+        double v[18], gs = 0;
+        for (int k = 0; k < 18; k++) v[k] = (double)fA[k * PL + o];
+        if constexpr (Store<S>::kLo) {
+            v[0] += (double)fA[27 * PL + o];
+            v[9] += (double)fA[28 * PL + o];
+        }
+        for (int k = 0; k < 9; k++) gs += (double)fA[(18 + k) * PL + o];
+        const double c1 = sum9(v), c2 = sum9(v + 9);
         s1 += c1;
         s2 += c2;
         s3 += 1.0 - c1 - c2;

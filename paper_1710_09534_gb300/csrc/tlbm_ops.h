@@ -9,6 +9,7 @@ namespace tlb {
 
 struct Ops {
     size_t elem;  // bytes per stored scalar
+    int ndist;    // planes per distribution buffer (27, or 29 with the FP32 rest lo parts)
     // one time step A -> B = interior tiles (fused kernel) + near-wall list
     cudaError_t (*interior)(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
                             const Prm<double>& P, cudaStream_t s);
@@ -24,12 +25,27 @@ struct Ops {
                         const Geo& g, cudaStream_t s);
 };
 
+// planes per distribution buffer for a storage precision
+inline int ndist_for(int precision) { return precision == 0 ? 27 : 29; }
+
 const Ops& ops_f64();
 const Ops& ops_f32();
 
 // Fused interior kernel: threads per block (one column each, 4 of them halo)
 // and rows marched per block, per precision.
-constexpr int kBlock64 = 64, kRows64 = 64;
-constexpr int kBlock32 = 64, kRows32 = 64;
+#ifndef TLB_BLOCK64
+#define TLB_BLOCK64 128
+#endif
+#ifndef TLB_ROWS64
+#define TLB_ROWS64 16
+#endif
+#ifndef TLB_BLOCK32
+#define TLB_BLOCK32 128
+#endif
+#ifndef TLB_ROWS32
+#define TLB_ROWS32 16
+#endif
+constexpr int kBlock64 = TLB_BLOCK64, kRows64 = TLB_ROWS64;
+constexpr int kBlock32 = TLB_BLOCK32, kRows32 = TLB_ROWS32;
 
 }  // namespace tlb

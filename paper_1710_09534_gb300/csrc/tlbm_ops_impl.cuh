@@ -92,7 +92,7 @@ struct OpsImpl {
     }
     static const Ops& table()
     {
-        static const Ops t{sizeof(S), &interior, &wall, &init, &read, &mass};
+        static const Ops t{sizeof(S), Store<S>::kPlanes, &interior, &wall, &init, &read, &mass};
         return t;
     }
 };
