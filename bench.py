@@ -29,16 +29,39 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & % of HBM roofline, batched/served vs plain; p50/p99 solve latency"
-# algorithmic bytes per node update: 27 distributions + 4 c_i u values, read
-# and written once (solid and near-wall nodes included in the node count)
-SCALARS_PER_NODE = 2 * (27 + 4)
-# algorithmic flops per node update (FMA = 2), the tally of the update's
-# arithmetic: moments, stencils, chemical potentials, forces, 9-direction
-# equilibria, sources and BGK relaxation of the three distributions
-FLOPS_PER_NODE = 700
-# FP64 vector peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+
+def bytes_per_node(precision):
+    """Algorithmic bytes per node update: the state that must persist, read
+    and written once -- 27 distributions (FP32 storage adds the lo halves of
+    the two rest populations) and the 4 c_i u values of Eq. 19."""
+    return 2 * (27 + 4) * 8 if precision == "fp64" else 2 * (29 + 4) * 4
+
+
+# FP64 arithmetic per node update of the fused interior kernel, as counted by
+# ncu (DADD + DMUL + DFMA instructions; flops with FMA = 2) on the 2048^2
+# lattice: see profiles/k_step_interior_fp64_tiled_drops_2048.md
+FP64_DP_INST_PER_NODE = 342
+FP64_FLOPS_PER_NODE = 496
+# FP64 vector unit: 152 SMs x 2 DP instructions/clk x 2.07 GHz (an FMA is 2 flops)
+FP64_DP_INST_PEAK = 152 * 2 * 2.07e9
+FP64_PEAK_TFLOPS = 2 * FP64_DP_INST_PEAK / 1e12
 SAMPLE_ROWS = 256
+
+
+def whole_job_mlups(nodes_per_rank, steps, world, ms_max):
+    """Aggregate throughput: every rank's node updates over the slowest rank's time."""
+    return nodes_per_rank * steps * world / (ms_max / 1e3) / 1e6
+
+
+def max_over_ranks(D, ms, device="cpu"):
+    """Max of a per-rank time over the process group (identity without one)."""
+    if D is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    D.all_reduce(t, op=D.ReduceOp.MAX)
+    return float(t.item())
 
 
 def parse():
@@ -54,6 +77,31 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default="fp32", help="comma list of extra precisions to time")
     return ap.parse_args()
+
+
+def kernel_source_hash():
+    """SHA-256 over the CUDA sources, to tell whether a stored ncu capture
+    still describes the kernels being timed."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1710_09534_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(precision, units):
+    """DRAM bytes per launch of the interior kernel from the committed ncu
+    capture (profiles/interior_traffic.json), scaled to `units` interior
+    nodes; None when the capture predates the current kernel sources."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "interior_traffic.json")))
+    except Exception:
+        return None
+    if d.get("csrc_sha256") != kernel_source_hash() or precision not in d:
+        return None
+    e = d[precision]
+    return round(e["dram_bytes"] / e["interior_nodes"] * units)
 
 
 def peaks():
@@ -213,31 +261,32 @@ def run_ours(args):
     L.profile(False)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
+    ms = max_over_ranks(D, ms, "cuda")
     if D:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        D.all_reduce(t, op=D.ReduceOp.MAX)
-        ms = float(t.item())
         D.barrier()
-    mlups = n_nodes * args.steps * ws / (ms / 1e3) / 1e6
-    es = 8 if args.precision == "fp64" else 4
+    mlups = whole_job_mlups(n_nodes, args.steps, ws, ms)
     hbm_gbs, peak_kind = peaks()
-    bytes_node = SCALARS_PER_NODE * es
+    bytes_node = bytes_per_node(args.precision)
     k1_avg = k1_ms / max(k1_n, 1)
     # the fused interior kernel dominates; its algorithmic units are the
     # interior nodes it updates per launch
     interior_nodes = n_nodes - L.wall_nodes()
     ach_gbs = interior_nodes * bytes_node / (k1_avg / 1e3) / 1e9
-    ach_tf = interior_nodes * FLOPS_PER_NODE / (k1_avg / 1e3) / 1e12
     hbm_frac = ach_gbs / hbm_gbs
+    traffic = measured_traffic(args.precision, interior_nodes)
     if args.precision == "fp64":
+        ach_tf = interior_nodes * FP64_FLOPS_PER_NODE / (k1_avg / 1e3) / 1e12
+        dp_issue = interior_nodes * FP64_DP_INST_PER_NODE / (k1_avg / 1e3) / FP64_DP_INST_PEAK
         roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(ach_tf / FP64_PEAK_TFLOPS, 4), "traffic": None,
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
-                "kernel": "k_step_interior<double>", "hbm_achieved_gbs": round(ach_gbs, 1),
-                "hbm_peak_gbs": hbm_gbs, "hbm_frac": round(hbm_frac, 4)}
+                "unit": "TFLOP/s", "frac": round(ach_tf / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 2 DP inst/clk x 2 flop x 2.07 GHz (FMA-chain probe measured 1.25-1.257 TFLOP/s)",
+                "kernel": "k_step_interior<double>",
+                "dp_issue_frac": round(dp_issue, 4),
+                "hbm_achieved_gbs": round(ach_gbs, 1), "hbm_peak_gbs": hbm_gbs, "hbm_frac": round(hbm_frac, 4)}
     else:
         roof = {"bound": "hbm", "achieved": round(ach_gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
-                "frac": round(hbm_frac, 4), "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "frac": round(hbm_frac, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "kernel": "k_step_interior<float>"}
     result = {
         "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": ws,
@@ -245,7 +294,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "precision": args.precision,
-                   "l2": f"state {2 * 27 * n_nodes * es / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
+                   "l2": f"state {bytes_node * n_nodes / 1e9:.2f} GB moved per step > 129 MB L2 (no flush needed)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "wall_nodes": int(L.wall_nodes())},
         "hbm_roofline_pct": round(100 * mlups / ws * 1e6 * bytes_node / (hbm_gbs * 1e9), 2),
@@ -264,9 +313,8 @@ def run_ours(args):
             V.sync()
             vms = time_steps(V, args.steps, torch, stream)
             v_mlups = n_nodes * args.steps / (vms / 1e3) / 1e6
-            ves = 8 if prec == "fp64" else 4
             variants[prec] = {"value": round(v_mlups, 2), "unit": "MLUPS",
-                              "hbm_roofline_pct": round(100 * v_mlups * 1e6 * SCALARS_PER_NODE * ves / (hbm_gbs * 1e9), 2)}
+                              "hbm_roofline_pct": round(100 * v_mlups * 1e6 * bytes_per_node(prec) / (hbm_gbs * 1e9), 2)}
             del V
         result["variants"] = variants
         if not args.no_cpu_baseline:

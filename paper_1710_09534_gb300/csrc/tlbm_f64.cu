@@ -2,5 +2,5 @@
 #include "tlbm_ops_impl.cuh"
 
 namespace tlb {
-const Ops& ops_f64() { return OpsImpl<double, double, kBlock64, kRows64, false>::table(); }
+const Ops& ops_f64() { return OpsImpl<double, double, kBlock64, kRows64, false, kMinB64>::table(); }
 }  // namespace tlb

@@ -147,8 +147,8 @@ __device__ __forceinline__ long long wrap_off(const Geo& g, int x, int y)
 // so each order parameter is summed once per node (plus a 4-column, 4-row
 // halo per block) and no c or mu array ever reaches HBM.
 // ---------------------------------------------------------------------------
-template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH>
-__global__ void __launch_bounds__(BLOCK)
+template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
 k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
                 const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
 {

@@ -45,7 +45,17 @@ const Ops& ops_f32();
 #ifndef TLB_ROWS32
 #define TLB_ROWS32 16
 #endif
-constexpr int kBlock64 = TLB_BLOCK64, kRows64 = TLB_ROWS64;
-constexpr int kBlock32 = TLB_BLOCK32, kRows32 = TLB_ROWS32;
+#ifndef TLB_MINB64
+#define TLB_MINB64 1
+#endif
+#ifndef TLB_MINB32
+#define TLB_MINB32 4
+#endif
+#ifndef TLB_PREFETCH32
+#define TLB_PREFETCH32 1
+#endif
+constexpr int kBlock64 = TLB_BLOCK64, kRows64 = TLB_ROWS64, kMinB64 = TLB_MINB64;
+constexpr int kBlock32 = TLB_BLOCK32, kRows32 = TLB_ROWS32, kMinB32 = TLB_MINB32;
+constexpr bool kPrefetch32 = TLB_PREFETCH32 != 0;
 
 }  // namespace tlb

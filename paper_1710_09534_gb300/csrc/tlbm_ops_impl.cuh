@@ -46,7 +46,7 @@ inline Prm<R> cast_prm(const Prm<double>& d)
     return r;
 }
 
-template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH>
+template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB>
 struct OpsImpl {
     static cudaError_t interior(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
                                 const Prm<double>& Pd, cudaStream_t s)
@@ -54,7 +54,7 @@ struct OpsImpl {
         const Prm<R> P = cast_prm<R>(Pd);
         constexpr int TX = BLOCK - 4;
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + ROWS - 1) / ROWS);
-        k_step_interior<S, R, BLOCK, ROWS, PREFETCH><<<grid, BLOCK, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, g, P);
+        k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB><<<grid, BLOCK, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, g, P);
         return cudaGetLastError();
     }
     static cudaError_t wall(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
