@@ -136,14 +136,17 @@ __device__ __forceinline__ long long wrap_off(const Geo& g, int x, int y)
 }
 
 // ---------------------------------------------------------------------------
-// K1: fused interior update, marching up a strip of columns.
+// K1: fused interior update, marching along a strip of columns.
 //
 // A block of BLOCK threads owns one column each: columns x0-2 .. x0+BLOCK-3
-// of which the middle TX = BLOCK-4 are updated, over rows y0 .. y0+ROWS-1.
-// Iteration for row yc keeps rolling rings in shared memory:
-//   c1, c2 of row yc        (sum of the 18 order-parameter populations)
-//   mu1, mu2 of row yc-1    (needs c rows yc-2 .. yc)
-//   update of row yc-2      (needs c and mu rows yc-3 .. yc-1)
+// of which the middle TX = BLOCK-4 are updated, over the ROWS rows of its
+// segment.  Even segments march up, odd segments down, so that two adjacent
+// segments read the two halo rows they share at about the same time (both
+// at their start or both at their end) and the second read hits L2.  The
+// iteration that reaches row r keeps rolling rings in shared memory:
+//   c1, c2 of row r         (sum of the 18 order-parameter populations)
+//   mu1, mu2 of row r - dir (needs c rows r - 2 dir .. r)
+//   update of row r - 2 dir (needs c and mu rows around it)
 // so each order parameter is summed once per node (plus a 4-column, 4-row
 // halo per block) and no c or mu array ever reaches HBM.
 // ---------------------------------------------------------------------------
@@ -169,10 +172,14 @@ k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu
     const bool updater = t >= 2 && t < BLOCK - 2 && xs < g.nx;
     const int y0 = blockIdx.y * ROWS;
     const int y1 = min(y0 + ROWS, g.ny);
+    const int dir = (blockIdx.y & 1) ? -1 : 1;
+    const int iters = (y1 - y0) + 4;
 
-    for (int yc = y0 - 2; yc < y1 + 2; yc++) {
-        const int yu = yc - 2;  // row updated in this iteration
-        bool upd = updater && yu >= y0;
+    for (int it = 0; it < iters; it++) {
+        const int yc = dir > 0 ? y0 - 2 + it : y1 + 1 - it;  // c row of this iteration
+        const int ym = yc - dir;                              // mu row
+        const int yu = yc - 2 * dir;                          // updated row
+        bool upd = updater && it >= 4;
         long long ou = 0;
         if (upd) {
             ou = (long long)yu * g.pitch + xs;
@@ -212,34 +219,31 @@ k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu
             sc2[sl][t] = b;
         }
         __syncthreads();
-        // 2) mu of row yc-1 (Eq. 8 with Eq. 20b)
-        if (yc >= y0 && t >= 1 && t < BLOCK - 1) {
-            const int sm = (yc + 9) % 5, s0 = (yc + 8) % 5, sp = (yc + 10) % 5;  // rows yc-1, yc-2, yc
+        // 2) mu of row ym (Eq. 8 with Eq. 20b)
+        if (it >= 2 && t >= 1 && t < BLOCK - 1) {
             R v1[9], v2[9];
 #pragma unroll
             for (int k = 0; k < 9; k++) {
-                const int sl = ey(k) == 0 ? sm : (ey(k) > 0 ? sp : s0);
+                const int sl = (ym + ey(k) + 10) % 5;
                 v1[k] = sc1[sl][t + ex(k)];
                 v2[k] = sc2[sl][t + ex(k)];
             }
             R mu1, mu2;
             chem_pot(P, v1[0], v2[0], lap9(v1), lap9(v2), mu1, mu2);
-            const int ml = (yc + 8) % 3;  // slot of row yc-1
+            const int ml = (ym + 9) % 3;
             sm1[ml][t] = mu1;
             sm2[ml][t] = mu2;
         }
         __syncthreads();
-        // 3) update of row yu = yc-2
+        // 3) update of row yu
         if (!upd) continue;
         Macro<R> m;
         {
-            const int cm = (yc + 7) % 5, c0 = (yc + 8) % 5, cpl = (yc + 9) % 5;  // c rows yu-1, yu, yu+1
-            const int mm = (yc + 6) % 3, m0 = (yc + 7) % 3, mp = (yc + 8) % 3;     // mu rows yu-1, yu, yu+1
             R v1[9], v2[9], w1[9], w2[9];
 #pragma unroll
             for (int k = 0; k < 9; k++) {
-                const int sl = ey(k) == 0 ? c0 : (ey(k) > 0 ? cpl : cm);
-                const int ml = ey(k) == 0 ? m0 : (ey(k) > 0 ? mp : mm);
+                const int sl = (yu + ey(k) + 10) % 5;
+                const int ml = (yu + ey(k) + 9) % 3;
                 v1[k] = sc1[sl][t + ex(k)];
                 v2[k] = sc2[sl][t + ex(k)];
                 w1[k] = sm1[ml][t + ex(k)];

@@ -46,7 +46,7 @@ const Ops& ops_f32();
 #define TLB_ROWS32 16
 #endif
 #ifndef TLB_MINB64
-#define TLB_MINB64 1
+#define TLB_MINB64 3
 #endif
 #ifndef TLB_MINB32
 #define TLB_MINB32 4
@@ -57,5 +57,6 @@ const Ops& ops_f32();
 constexpr int kBlock64 = TLB_BLOCK64, kRows64 = TLB_ROWS64, kMinB64 = TLB_MINB64;
 constexpr int kBlock32 = TLB_BLOCK32, kRows32 = TLB_ROWS32, kMinB32 = TLB_MINB32;
 constexpr bool kPrefetch32 = TLB_PREFETCH32 != 0;
+
 
 }  // namespace tlb
