@@ -166,6 +166,18 @@ int tlb_read_fields_device(tlb_lattice *lat, uint32_t field_mask, double *dev_ou
  * Returns TLB_EUNSTABLE (with *out filled) if nonfinite > 0. */
 int tlb_diagnostics(tlb_lattice *lat, tlb_diag *out);
 
+/* Contact-line diagnostic of a drop of fluid `component` (1 or 2) on the
+ * bottom wall, in FP64 on the device (Sec. III.A: theta_n = 2 atan(2 H_d /
+ * L_s)).  A drop is a run of wall-row nodes (row y = 0, periodic in x) with
+ * c >= 1/2; L_s is the distance between its two c = 1/2 crossings on that row
+ * (linear interpolation); H_d is the largest, over the run's columns, of the
+ * c = 1/2 crossing reached by walking up from the wall through c >= 1/2
+ * (linear interpolation) plus 1/2 for the half-way wall.  host_out receives
+ * 4 doubles per drop {L_s, H_d, theta_n in degrees, x of the base centre} for
+ * up to min(max_drops, 256) drops; *n_drops = number of drops found.
+ * Synchronizes. */
+int tlb_contact_angles(tlb_lattice *lat, int component, double *host_out, int max_drops, int *n_drops);
+
 /* Raw state as FP64 host planes [31][ny][nx]: f^1_k (k = 0..8), f^2_k,
  * g_k, then c1 ux, c1 uy, c2 ux, c2 uy of the previous step (Eq. 19).
  * Synchronizes. */

@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tlb_theta12_from": (i32, [ctypes.c_double] * 5 + [dp]),
         "tlb_wall_nodes": (i64, [vp]),
         "tlb_diagnostics_noalloc": (i32, [vp, vp]),
+        "tlb_contact_angles": (i32, [vp, i32, dp, i32, ctypes.POINTER(ctypes.c_int)]),
         "tlb_profile": (i32, [vp, i32]),
         "tlb_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "tlb_destroy": (None, [vp]),
@@ -221,6 +222,14 @@ class Lattice:
         """Allocation-free reduction into a device float64 tensor of >= 4
         elements: [sum c1, sum c2, sum c3, non-finite count] (asynchronous)."""
         _check(self.lib.tlb_diagnostics_noalloc(self._h, ctypes.c_void_p(dev_out.data_ptr())))
+
+    def contact_angles(self, component: int = 1, max_drops: int = 64):
+        """Drops of `component` on the bottom wall: list of (L_s, H_d, theta_n deg, x_mid)."""
+        out = np.zeros(4 * max_drops)
+        n = ctypes.c_int()
+        _check(self.lib.tlb_contact_angles(self._h, int(component), _dp(out), int(max_drops), ctypes.byref(n)))
+        k = min(n.value, max_drops)
+        return [tuple(out[4 * i:4 * i + 4]) for i in range(k)]
 
     def state(self) -> np.ndarray:
         out = np.empty((31, self.ny, self.nx))

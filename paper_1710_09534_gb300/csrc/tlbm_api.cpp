@@ -46,13 +46,14 @@ int ok()
 
 constexpr int64_t kAlign = 256;
 constexpr int kMassParts = 608;  // 4 x 152 SMs
+constexpr int kMaxDrops = 256;   // contact-line results kept per call
 
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     int pitch = 0;
     int64_t plane = 0;  // elements
-    int64_t fA = 0, fB = 0, cu = 0, cls = 0, list = 0, part = 0, diag = 0, total = 0;
+    int64_t fA = 0, fB = 0, cu = 0, cls = 0, list = 0, part = 0, diag = 0, contact = 0, total = 0;
 };
 
 bool precision_ok(int precision) { return precision == TLB_FP64 || precision == TLB_FP32; }
@@ -79,6 +80,9 @@ Layout layout_for(int nx, int ny, int precision)
     L.list = take((int64_t)nx * ny * 4);
     L.part = take((int64_t)kMassParts * 4 * 8);
     L.diag = take(4 * 8);
+    // contact-line scratch: wall-row c and column heights (2 nx doubles),
+    // up to kMaxDrops results (4 doubles each) and the drop count
+    L.contact = take((2 * (int64_t)nx + 4 * kMaxDrops) * 8 + 16);
     L.total = off;
     return L;
 }
@@ -511,6 +515,31 @@ int tlb_diagnostics(tlb_lattice* L, tlb_diag* out)
     out->mass[2] = h[2];
     out->nonfinite = (int64_t)h[3];
     if (out->nonfinite > 0) return fail(TLB_EUNSTABLE, "%lld fluid nodes hold non-finite values", (long long)out->nonfinite);
+    return ok();
+}
+
+int tlb_contact_angles(tlb_lattice* L, int component, double* host_out, int max_drops, int* n_drops)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (component != 1 && component != 2) return fail(TLB_EINVAL, "component must be 1 or 2");
+    if (!host_out || !n_drops || max_drops < 0) return fail(TLB_EINVAL, "bad output arguments");
+    if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "no state yet");
+    double* wallc = (double*)(L->ws + L->lay.contact);
+    double* colh = wallc + L->nx;
+    double* res = colh + L->nx;
+    int* cnt = (int*)(res + 4 * kMaxDrops);
+    const int keep = max_drops < kMaxDrops ? max_drops : kMaxDrops;
+    TLB_CUDA(L->ops->contact(L->bufA(), L->dcls(), component, wallc, colh, res, kMaxDrops, cnt, L->geo, L->stream));
+    int n = 0;
+    TLB_CUDA(cudaMemcpyAsync(&n, cnt, sizeof n, cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaStreamSynchronize(L->stream));
+    const int copy = n < keep ? n : keep;
+    if (copy > 0) {
+        TLB_CUDA(cudaMemcpyAsync(host_out, res, (size_t)copy * 4 * 8, cudaMemcpyDeviceToHost, L->stream));
+        TLB_CUDA(cudaStreamSynchronize(L->stream));
+    }
+    *n_drops = n;
     return ok();
 }
 

@@ -739,3 +739,93 @@ static __global__ void __launch_bounds__(256) k_mass_final(const double* __restr
 }
 
 }  // namespace tlb
+
+namespace tlb {
+
+// ---------------------------------------------------------------------------
+// Contact-line diagnostic (Sec. III.A: theta_n = 2 atan(2 H_d / L_s)), in
+// FP64 on the wall row y = 0.  Per column: the order parameter c_comp on the
+// wall row, and the height of the c = 1/2 crossing reached by walking up from
+// the wall through nodes with c >= 1/2 (linear interpolation), plus 1/2 for the
+// half-way wall; -1 where the wall node is outside a drop.
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void k_contact_columns(const S* __restrict__ fA, const uint8_t* __restrict__ cls, int comp,
+                                  double* __restrict__ wallc, double* __restrict__ colh, Geo g)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const long long PL = g.plane;
+    const int base = comp == 1 ? 0 : 9;
+    auto cval = [&](int y) {
+        const long long o = (long long)y * g.pitch + x;
+        const int kind = cls[o] & CLS_KIND_MASK;
+        if (!fluidlike(kind)) return 0.0;
+        const long long src = kind == ST_LID ? o - g.pitch : o;  // the lid row carries the row below
+        double v[9];
+        for (int k = 0; k < 9; k++) v[k] = (double)fA[(base + k) * PL + src];
+        if constexpr (Store<S>::kLo) v[0] += (double)fA[(comp == 1 ? 27 : 28) * PL + src];
+        return sum9(v);
+    };
+    const double c0 = cval(0);
+    wallc[x] = c0;
+    if (!(c0 >= 0.5)) {
+        colh[x] = -1.0;
+        return;
+    }
+    int y = 0;
+    double cy = c0, cn = 0.0;
+    while (y + 1 < g.ny) {
+        cn = cval(y + 1);
+        if (!(cn >= 0.5)) break;
+        y++;
+        cy = cn;
+    }
+    const double h = (y + 1 < g.ny) ? y + (cy - 0.5) / (cy - cn) : (double)y;
+    colh[x] = h + 0.5;
+}
+
+// One thread: the c >= 1/2 segments of the (periodic) wall row, with their
+// crossings, base length L_s, height H_d (largest column height over the
+// segment) and theta_n.  out[4*i + 0..3] = L_s, H_d, theta_n (degrees), x_mid.
+static __global__ void k_contact_scan(const double* __restrict__ wallc, const double* __restrict__ colh, int nx,
+                                      double* __restrict__ out, int max_drops, int* __restrict__ count)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int start = -1;
+    for (int i = 0; i < nx; i++)
+        if (!(wallc[i] >= 0.5)) {
+            start = i;
+            break;
+        }
+    int n = 0;
+    if (start >= 0) {
+        auto r = [&](int i) { return wallc[(i + start) % nx]; };
+        int i = 0;
+        while (i < nx) {
+            if (!(r(i) >= 0.5)) {
+                i++;
+                continue;
+            }
+            const int a = i;
+            while (i < nx && r(i) >= 0.5) i++;
+            const int b = i - 1;
+            const double xl = (a - 1) + (0.5 - r(a - 1)) / (r(a) - r(a - 1));
+            const double rb1 = wallc[(b + 1 + start) % nx];
+            const double xr = b + (r(b) - 0.5) / (r(b) - rb1);
+            double H = 0.0;
+            for (int xx = a; xx <= b; xx++) H = fmax(H, colh[(xx + start) % nx]);
+            const double Ls = xr - xl;
+            if (n < max_drops) {
+                out[4 * n + 0] = Ls;
+                out[4 * n + 1] = H;
+                out[4 * n + 2] = 2.0 * atan(2.0 * H / Ls) * (180.0 / 3.14159265358979323846);
+                out[4 * n + 3] = fmod((xl + xr) / 2 + start, (double)nx);
+            }
+            n++;
+        }
+    }
+    *count = n;
+}
+
+}  // namespace tlb

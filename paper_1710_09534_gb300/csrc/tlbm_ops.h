@@ -20,6 +20,10 @@ struct Ops {
                         const Prm<double>& P, cudaStream_t s);
     cudaError_t (*read)(const void* fA, const uint8_t* cls, double* out, uint32_t mask, const Geo& g,
                         const Prm<double>& P, cudaStream_t s);
+    // contact-line diagnostic of component comp on the wall row (FP64):
+    // wallc[nx], colh[nx] scratch, out[4*max_drops], *count
+    cudaError_t (*contact)(const void* fA, const uint8_t* cls, int comp, double* wallc, double* colh,
+                           double* out, int max_drops, int* count, const Geo& g, cudaStream_t s);
     // FP64 mass totals into out[4] via nparts block partials in part[4*nparts]
     cudaError_t (*mass)(const void* fA, const uint8_t* cls, double* part, int nparts, double* out,
                         const Geo& g, cudaStream_t s);

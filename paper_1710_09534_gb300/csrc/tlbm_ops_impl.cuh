@@ -90,9 +90,16 @@ struct OpsImpl {
         k_mass_final<<<1, 256, 0, s>>>(part, nparts, out);
         return cudaGetLastError();
     }
+    static cudaError_t contact(const void* fA, const uint8_t* cls, int comp, double* wallc, double* colh,
+                               double* out, int max_drops, int* count, const Geo& g, cudaStream_t s)
+    {
+        k_contact_columns<S><<<(g.nx + 127) / 128, 128, 0, s>>>((const S*)fA, cls, comp, wallc, colh, g);
+        k_contact_scan<<<1, 32, 0, s>>>(wallc, colh, g.nx, out, max_drops, count);
+        return cudaGetLastError();
+    }
     static const Ops& table()
     {
-        static const Ops t{sizeof(S), Store<S>::kPlanes, &interior, &wall, &init, &read, &mass};
+        static const Ops t{sizeof(S), Store<S>::kPlanes, &interior, &wall, &init, &read, &contact, &mass};
         return t;
     }
 };

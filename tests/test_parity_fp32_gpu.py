@@ -98,3 +98,6 @@ def test_fp32_contact_angle_within_half_degree(T, theta13):
     to = oracle.contact_angle_deg(O.fields()["c1"])[0]
     assert abs(tg - to) < 0.5
     assert abs(to - theta13) < 3.5
+    # the device-side FP64 contact-line diagnostic on the FP32 state
+    (_, _, td, _), = L.contact_angles(1)
+    assert abs(td - to) < 0.5

@@ -212,3 +212,38 @@ def test_nonfinite_state_is_reported(T):
     L.set_fields(c1, w.c2, w.ux, w.uy)
     d = L.diagnostics()
     assert d["rc"] == T.EUNSTABLE and d["nonfinite"] >= 1
+
+
+def test_contact_line_diagnostic_fp64(T):
+    """tlb_contact_angles (FP64 on the device) against the oracle's measurement
+    of theta_n = 2 atan(2 H_d / L_s) (Sec. III.A) on the oracle's own fields."""
+    import oracle
+    w = W.binary_drops_on_wall()
+    L, O = pair(T, w)
+    L.step(1000)
+    O.step(1000)
+    fo = O.fields()
+    for comp in (1, 2):
+        got = L.contact_angles(comp)
+        ref = oracle.drop_geometry(fo[f"c{comp}"])
+        assert len(got) == len(ref) == 1
+        (Ls, Hd, th, xm), (Ls0, Hd0, xm0) = got[0], ref[0]
+        assert abs(Ls - Ls0) < 1e-9 * Ls0 and abs(Hd - Hd0) < 1e-9 * Hd0
+        assert abs(th - oracle.contact_angle_deg(fo[f"c{comp}"])[0]) < 1e-8
+        assert abs(xm - xm0) < 1e-9 * w.nx
+
+
+def test_contact_line_diagnostic_counts_drops_across_the_periodic_edge(T):
+    nx, ny = 96, 32
+    x, y = W.grid(nx, ny)
+    c1 = np.maximum(W.profile(x, y, 4.0, -0.5, 10, 4.0, period_x=nx),
+                    W.profile(x, y, 50.0, -0.5, 8, 4.0, period_x=nx))
+    z = np.zeros((ny, nx))
+    w = W.Workload("two", nx, ny, (0, 0, 1, 2), np.zeros((ny, nx), np.uint8), W.params(), c1, z, z, z)
+    L = T.lattice_from_workload(w)
+    got = sorted(L.contact_angles(1), key=lambda r: r[3])
+    import oracle
+    ref = sorted(oracle.drop_geometry(L.fields()["c1"]), key=lambda r: r[2])
+    assert len(got) == len(ref) == 2
+    for (Ls, Hd, _, xm), (Ls0, Hd0, xm0) in zip(got, ref):
+        assert abs(Ls - Ls0) < 1e-12 * Ls0 and abs(Hd - Hd0) < 1e-12 * Hd0 and abs(xm - xm0) < 1e-9
