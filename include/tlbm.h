@@ -45,6 +45,7 @@ extern "C" {
 #endif
 
 typedef struct tlb_lattice tlb_lattice;
+typedef struct tlb_batch tlb_batch;
 
 /* Storage precision of the distributions.  TLB_FP64 computes in FP64;
  * TLB_FP32 stores and computes in FP32 (diagnostic sums in FP64). */
@@ -207,6 +208,41 @@ int tlb_profile_read(tlb_lattice *lat, double ms[2], int64_t launches[2]);
 
 /* Number of nodes in the near-wall list (handled by the near-wall kernel). */
 int64_t tlb_wall_nodes(tlb_lattice *lat);
+
+/* ---- Batches: many lattices advanced together -------------------------
+ * A batch steps all its member lattices in lockstep: per step, one
+ * persistent kernel whose blocks take (member, strip, segment) tiles of the
+ * fused interior update from a shared counter, then one loop over all the
+ * members' near-wall nodes (same per-node arithmetic as tlb_step, so a
+ * member's result does not depend on the rest of the batch).  Pairs of steps
+ * run as one captured CUDA graph on the batch's stream.  Members keep their
+ * own workspaces; the batch workspace holds the device descriptors and work
+ * lists.  Not in the paper: it serves many independent simulations.
+ *
+ * tlb_batch_workspace_bytes: bytes for up to max_lattices members, max_tiles
+ * tiles (sum of tlb_batch_tiles_needed over the members) and max_wall_nodes
+ * (sum of tlb_wall_nodes).  tlb_batch_create: the stream must not be the
+ * legacy default stream.  tlb_batch_add: the lattice must have the batch's
+ * precision and device and not belong to another batch; its own stream is
+ * synchronized; while it is a member, tlb_step on it returns TLB_ESTATE.
+ * tlb_batch_remove synchronizes the batch stream.  tlb_batch_step advances
+ * every member n steps, asynchronously.  tlb_batch_config sets the tile shape
+ * (threads 64 or 128; row segments rows_small for members with ny <=
+ * small_ny, rows_large otherwise); tlb_batch_tune times candidate shapes for
+ * trial_steps steps each (it advances every member by 8 * (trial_steps + 2)
+ * steps), keeps the fastest and reports {threads, rows_small, rows_large,
+ * small_ny} and its time per step. */
+int64_t tlb_batch_workspace_bytes(int max_lattices, int64_t max_tiles, int64_t max_wall_nodes);
+int64_t tlb_batch_tiles_needed(int nx, int ny);
+int tlb_batch_create(int precision, int max_lattices, int64_t max_tiles, int64_t max_wall_nodes,
+                     void *dev_workspace, int64_t ws_bytes, void *cuda_stream, tlb_batch **out);
+int tlb_batch_add(tlb_batch *batch, tlb_lattice *lat);
+int tlb_batch_remove(tlb_batch *batch, tlb_lattice *lat);
+int tlb_batch_size(tlb_batch *batch);
+int tlb_batch_step(tlb_batch *batch, int64_t n);
+int tlb_batch_config(tlb_batch *batch, int threads, int rows_small, int rows_large, int small_ny);
+int tlb_batch_tune(tlb_batch *batch, int trial_steps, int out_config[4], double *out_ms_per_step);
+void tlb_batch_destroy(tlb_batch *batch);
 
 /* Allocation-free variant of the tlb_diagnostics reduction.  The paper has
  * no counterpart: this exists for callers that cannot allocate device memory

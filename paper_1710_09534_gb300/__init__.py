@@ -88,6 +88,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tlb_profile": (i32, [vp, i32]),
         "tlb_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "tlb_destroy": (None, [vp]),
+        "tlb_batch_workspace_bytes": (i64, [i32, i64, i64]),
+        "tlb_batch_tiles_needed": (i64, [i32, i32]),
+        "tlb_batch_create": (i32, [i32, i32, i64, i64, vp, i64, vp, ctypes.POINTER(vp)]),
+        "tlb_batch_add": (i32, [vp, vp]),
+        "tlb_batch_remove": (i32, [vp, vp]),
+        "tlb_batch_size": (i32, [vp]),
+        "tlb_batch_step": (i32, [vp, i64]),
+        "tlb_batch_config": (i32, [vp, i32, i32, i32, i32]),
+        "tlb_batch_tune": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int), dp]),
+        "tlb_batch_destroy": (None, [vp]),
         "tlb_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -273,3 +283,74 @@ def lattice_from_workload(w, precision="fp64", stream=None) -> Lattice:
     L.set_params(w.params)
     L.set_fields(w.c1, w.c2, w.ux, w.uy, w.p)
     return L
+
+
+class Batch:
+    """Lattices advanced together by one persistent kernel per step (see the
+    "Batches" section of include/tlbm.h).  Capacity is fixed at creation:
+    `max_lattices` members whose tiles and near-wall nodes sum to at most
+    `max_tiles` (tlb_batch_tiles_needed per member) and `max_wall_nodes`."""
+
+    def __init__(self, precision="fp32", max_lattices=256, max_tiles=1 << 16, max_wall_nodes=1 << 20,
+                 stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("tlbm needs a CUDA device; there is no CPU fallback")
+        self.lib = load_library()
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            nbytes = _check(self.lib.tlb_batch_workspace_bytes(int(max_lattices), int(max_tiles),
+                                                              int(max_wall_nodes)))
+            self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+            h = ctypes.c_void_p()
+            _check(self.lib.tlb_batch_create(self.precision, int(max_lattices), int(max_tiles),
+                                             int(max_wall_nodes), ctypes.c_void_p(self.workspace.data_ptr()),
+                                             int(nbytes), ctypes.c_void_p(self.stream.cuda_stream),
+                                             ctypes.byref(h)))
+        self._h = h
+        self.members = []
+
+    @staticmethod
+    def tiles_needed(nx, ny) -> int:
+        return _check(load_library().tlb_batch_tiles_needed(int(nx), int(ny)))
+
+    def add(self, lattice: "Lattice"):
+        _check(self.lib.tlb_batch_add(self._h, lattice._h))
+        self.members.append(lattice)
+
+    def remove(self, lattice: "Lattice"):
+        _check(self.lib.tlb_batch_remove(self._h, lattice._h))
+        self.members.remove(lattice)
+
+    def __len__(self):
+        return _check(self.lib.tlb_batch_size(self._h))
+
+    def step(self, n: int = 1):
+        _check(self.lib.tlb_batch_step(self._h, int(n)))
+
+    def config(self, threads=128, rows_small=16, rows_large=16, small_ny=128):
+        _check(self.lib.tlb_batch_config(self._h, int(threads), int(rows_small), int(rows_large), int(small_ny)))
+
+    def tune(self, trial_steps: int = 5):
+        """Pick the fastest tile shape; advances every member 8*(trial_steps+2) steps."""
+        cfg = (ctypes.c_int * 4)()
+        ms = ctypes.c_double()
+        _check(self.lib.tlb_batch_tune(self._h, int(trial_steps), cfg, ctypes.byref(ms)))
+        return dict(threads=cfg[0], rows_small=cfg[1], rows_large=cfg[2], small_ny=cfg[3], ms_per_step=ms.value)
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.tlb_batch_destroy(self._h)
+            self._h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

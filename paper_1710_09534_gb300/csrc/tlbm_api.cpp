@@ -50,19 +50,14 @@ constexpr int kMaxDrops = 256;   // contact-line results kept per call
 
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-struct Layout {
-    int pitch = 0;
-    int64_t plane = 0;  // elements
-    int64_t fA = 0, fB = 0, cu = 0, cls = 0, list = 0, part = 0, diag = 0, contact = 0, total = 0;
-};
 
 bool precision_ok(int precision) { return precision == TLB_FP64 || precision == TLB_FP32; }
 
 size_t elem_size(int precision) { return precision == TLB_FP64 ? 8 : 4; }
 
-Layout layout_for(int nx, int ny, int precision)
+tlb::Layout layout_for(int nx, int ny, int precision)
 {
-    Layout L;
+    tlb::Layout L;
     L.pitch = (int)align_up(nx, 32);
     L.plane = (int64_t)L.pitch * ny;
     const int64_t es = (int64_t)elem_size(precision);
@@ -89,35 +84,6 @@ Layout layout_for(int nx, int ny, int precision)
 
 }  // namespace
 
-struct tlb_lattice {
-    int nx = 0, ny = 0, precision = 0, device = 0;
-    int32_t edge[4] = {0, 0, 0, 0};
-    cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
-    char* ws = nullptr;
-    Layout lay;
-    const tlb::Ops* ops = nullptr;
-    tlb::Geo geo{};
-    tlb::Prm<double> prm{};
-    int cur = 0;  // which of the two distribution buffers holds the state
-    bool have_params = false, have_fields = false;
-    std::vector<uint8_t> mask;    // host copy of the solid mask
-    std::vector<uint8_t> cls;     // host copy of the node classes (pitched)
-    int64_t nlist = 0;
-    // optional per-kernel timing: event triples around the two launches of a step
-    bool prof = false;
-    std::vector<cudaEvent_t> ev;
-    int ev_used = 0;
-    double prof_ms[2] = {0, 0};
-    int64_t prof_n[2] = {0, 0};
-
-    void* bufA() { return ws + (cur == 0 ? lay.fA : lay.fB); }
-    void* bufB() { return ws + (cur == 0 ? lay.fB : lay.fA); }
-    void* cu() { return ws + lay.cu; }
-    const uint8_t* dcls() { return (const uint8_t*)(ws + lay.cls); }
-    const uint32_t* dlist() { return (const uint32_t*)(ws + lay.list); }
-    int64_t n() const { return (int64_t)nx * ny; }
-};
 
 namespace {
 
@@ -167,6 +133,7 @@ int build_geometry(tlb_lattice* L)
         }
     }
     L->nlist = (int64_t)list.size();
+    L->hlist = list;
     TLB_CUDA(cudaMemcpyAsync(L->ws + L->lay.cls, L->cls.data(), L->cls.size(), cudaMemcpyHostToDevice,
                              L->stream));
     if (!list.empty())
@@ -200,7 +167,8 @@ int check_handle(tlb_lattice* L)
 {
     if (!L) return fail(TLB_EINVAL, "null lattice handle");
     TLB_CUDA(cudaSetDevice(L->device));
-    return TLB_OK;
+    // a member of a batch: let queued batch steps finish before touching it
+    return tlb::batch_sync(L->batch);
 }
 
 bool finite_all(const tlb_params* p)
@@ -247,7 +215,7 @@ int tlb_create_lattice(int nx, int ny, int precision, const int32_t edges[4], vo
     if (edges[0] == TLB_EDGE_LID || edges[1] == TLB_EDGE_LID || edges[2] == TLB_EDGE_LID)
         return fail(TLB_EINVAL, "a velocity lid is supported on the top edge only");
     if (edges[3] == TLB_EDGE_LID && ny < 6) return fail(TLB_EINVAL, "a lid needs ny >= 6");
-    const Layout lay = layout_for(nx, ny, precision);
+    const tlb::Layout lay = layout_for(nx, ny, precision);
     if (!dev_workspace) return fail(TLB_EINVAL, "workspace is null");
     if (((uintptr_t)dev_workspace) % kAlign) return fail(TLB_EINVAL, "workspace must be 256-byte aligned");
     if (ws_bytes < lay.total)
@@ -307,6 +275,7 @@ int tlb_set_geometry(tlb_lattice* L, const uint8_t* host_mask)
     L->mask.swap(m);
     rc = build_geometry(L);
     if (rc) return rc;
+    tlb::batch_member_changed(L->batch);
     L->have_fields = false;
     return ok();
 }
@@ -383,6 +352,7 @@ int tlb_set_params(tlb_lattice* L, const tlb_params* p)
     P.lid_u = p->lid_u;
     L->have_params = true;
     L->have_fields = false;
+    tlb::batch_member_changed(L->batch);
     g_err.clear();
     if (l1 <= 0.5 * lT || l2 <= 0.5 * lT || l3 <= 0.5 * lT)
         g_err = "warning: some lambda_i <= lambda_T / 2 (outside the well-posed range of the bulk free energy)";
@@ -437,6 +407,7 @@ int tlb_step(tlb_lattice* L, int64_t n)
     if (rc) return rc;
     if (n < 0) return fail(TLB_EINVAL, "negative step count");
     if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "set_params and set_fields before step");
+    if (L->batch) return fail(TLB_ESTATE, "lattice belongs to a batch: step the batch");
     for (int64_t s = 0; s < n; s++) {
         if (L->prof) {
             if (L->ev_used == kProfSlots && (rc = prof_fold(L))) return rc;
@@ -662,6 +633,7 @@ int tlb_profile_read(tlb_lattice* L, double ms[2], int64_t launches[2])
 void tlb_destroy(tlb_lattice* L)
 {
     if (!L) return;
+    if (L->batch) tlb_batch_remove(L->batch, L);
     for (auto e : L->ev) cudaEventDestroy(e);
     if (L->done) cudaEventDestroy(L->done);
     delete L;

@@ -150,16 +150,26 @@ __device__ __forceinline__ long long wrap_off(const Geo& g, int x, int y)
 // so each order parameter is summed once per node (plus a 4-column, 4-row
 // halo per block) and no c or mu array ever reaches HBM.
 // ---------------------------------------------------------------------------
-template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB>
-__global__ void __launch_bounds__(BLOCK, MINB)
-k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
-                const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
+template <typename R, int BLOCK>
+struct TileRings {
+    R c1[5][BLOCK], c2[5][BLOCK];  // c rings (row r in slot (r + 10) % 5)
+    R m1[3][BLOCK], m2[3][BLOCK];  // mu rings (row r in slot (r + 9) % 3)
+};
+
+// One tile: strip bx (columns bx*(BLOCK-4) .. +BLOCK-5), segment by (rows
+// by*rows .. +rows-1, marching up for even by and down for odd by).
+template <typename S, typename R, int BLOCK, bool PREFETCH>
+__device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+                                              const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
+                                              int bx, int by, int rows, TileRings<R, BLOCK>& sh)
 {
-    __shared__ R sc1[5][BLOCK], sc2[5][BLOCK];  // c rings (row r in slot (r + 10) % 5)
-    __shared__ R sm1[3][BLOCK], sm2[3][BLOCK];  // mu rings (row r in slot (r + 9) % 3)
+    R(&sc1)[5][BLOCK] = sh.c1;
+    R(&sc2)[5][BLOCK] = sh.c2;
+    R(&sm1)[3][BLOCK] = sh.m1;
+    R(&sm2)[3][BLOCK] = sh.m2;
     const long long PL = g.plane;
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * (BLOCK - 4);
+    const int x0 = bx * (BLOCK - 4);
     const int xs = x0 - 2 + t;  // this thread's column, in [-2, nx + BLOCK]
     // wrapped column (periodic x) and whether it holds data at all; only
     // columns -2 .. nx+1 are ever read
@@ -170,9 +180,9 @@ k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu
         else col_in = false;
     }
     const bool updater = t >= 2 && t < BLOCK - 2 && xs < g.nx;
-    const int y0 = blockIdx.y * ROWS;
-    const int y1 = min(y0 + ROWS, g.ny);
-    const int dir = (blockIdx.y & 1) ? -1 : 1;
+    const int y0 = by * rows;
+    const int y1 = min(y0 + rows, g.ny);
+    const int dir = (by & 1) ? -1 : 1;
     const int iters = (y1 - y0) + 4;
 
     for (int it = 0; it < iters; it++) {
@@ -297,6 +307,15 @@ k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu
                 fB[28 * PL + ou] = S(l2);
             });
     }
+}
+
+template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
+k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+                const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
+{
+    __shared__ TileRings<R, BLOCK> sh;
+    interior_tile<S, R, BLOCK, PREFETCH>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,13 +481,10 @@ __device__ __forceinline__ void push_wall(const Geo& g, const uint8_t* __restric
 // K2: near-wall and lid nodes from the compacted list.
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
-__global__ void __launch_bounds__(128)
-k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
-            const uint8_t* __restrict__ cls, const uint32_t* __restrict__ list, int nlist, Geo g, Prm<R> P)
+__device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+                                          const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
+                                          uint32_t packed)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nlist) return;
-    const uint32_t packed = list[t];
     const int x = (int)(packed & 0xffffu), y = (int)(packed >> 16);
     const long long PL = g.plane;
     const long long o = (long long)y * g.pitch + x;
@@ -579,6 +595,16 @@ k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
                 fB[28 * PL + o] = S(l2);
             });
     }
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(128)
+k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+            const uint8_t* __restrict__ cls, const uint32_t* __restrict__ list, int nlist, Geo g, Prm<R> P)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nlist) return;
+    wall_node<S, R>(fA, fB, cu, cls, g, P, list[t]);
 }
 
 // ---------------------------------------------------------------------------

@@ -24,6 +24,15 @@ struct Ops {
     // wallc[nx], colh[nx] scratch, out[4*max_drops], *count
     cudaError_t (*contact)(const void* fA, const uint8_t* cls, int comp, double* wallc, double* colh,
                            double* out, int max_drops, int* count, const Geo& g, cudaStream_t s);
+    // batched step: persistent interior kernel (variant 0: 64-thread blocks,
+    // 1: 128-thread blocks) over the tile list, then the near-wall loop
+    cudaError_t (*batch_step)(const void* descs, const void* tiles, const void* walls, void* ctr, int parity,
+                              int variant, int grid_interior, int grid_wall, cudaStream_t s);
+    // resident blocks per SM of the persistent interior kernel of a variant
+    int (*batch_blocks_per_sm)(int variant);
+    size_t desc_size;  // bytes of one device lattice descriptor
+    void (*fill_desc)(void* dst, const void* buf0, const void* buf1, void* cu, const uint8_t* cls, const Geo& g,
+                      const Prm<double>& P, int rows);
     // FP64 mass totals into out[4] via nparts block partials in part[4*nparts]
     cudaError_t (*mass)(const void* fA, const uint8_t* cls, double* part, int nparts, double* out,
                         const Geo& g, cudaStream_t s);

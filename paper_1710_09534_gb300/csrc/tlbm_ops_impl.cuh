@@ -1,5 +1,6 @@
 // Launchers of one precision; included by tlbm_f64.cu and tlbm_f32.cu.
 #pragma once
+#include "tlbm_batch.cuh"
 #include "tlbm_kernels.cuh"
 #include "tlbm_ops.h"
 
@@ -97,9 +98,48 @@ struct OpsImpl {
         k_contact_scan<<<1, 32, 0, s>>>(wallc, colh, g.nx, out, max_drops, count);
         return cudaGetLastError();
     }
+    // the two block shapes the batch tuner chooses between
+    static constexpr int kMinB64 = std::is_same<S, float>::value ? 8 : 6;
+    static cudaError_t batch_step(const void* descs, const void* tiles, const void* walls, void* ctr, int parity,
+                                  int variant, int grid_interior, int grid_wall, cudaStream_t s)
+    {
+        BatchCounters* c = (BatchCounters*)ctr;
+        cudaError_t e = cudaMemsetAsync(&c->next[parity], 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        if (variant == 0)
+            k_batch_interior<S, R, 64, PREFETCH, kMinB64><<<grid_interior, 64, 0, s>>>(
+                (const LatDesc<R>*)descs, (const TileItem*)tiles, c, parity);
+        else
+            k_batch_interior<S, R, 128, PREFETCH, MINB><<<grid_interior, 128, 0, s>>>(
+                (const LatDesc<R>*)descs, (const TileItem*)tiles, c, parity);
+        k_batch_wall<S, R><<<grid_wall, 128, 0, s>>>((const LatDesc<R>*)descs, (const WallItem*)walls, c, parity);
+        return cudaGetLastError();
+    }
+    static int batch_blocks_per_sm(int variant)
+    {
+        int n = 0;
+        if (variant == 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_interior<S, R, 64, PREFETCH, kMinB64>, 64, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_interior<S, R, 128, PREFETCH, MINB>, 128, 0);
+        return n;
+    }
+    static void fill_desc(void* dst, const void* buf0, const void* buf1, void* cu, const uint8_t* cls, const Geo& g,
+                          const Prm<double>& P, int rows)
+    {
+        LatDesc<R>* d = (LatDesc<R>*)dst;
+        d->buf[0] = buf0;
+        d->buf[1] = buf1;
+        d->cu = cu;
+        d->cls = cls;
+        d->g = g;
+        d->P = cast_prm<R>(P);
+        d->rows = rows;
+    }
     static const Ops& table()
     {
-        static const Ops t{sizeof(S), Store<S>::kPlanes, &interior, &wall, &init, &read, &contact, &mass};
+        static const Ops t{sizeof(S), Store<S>::kPlanes, &interior, &wall, &init, &read, &contact, &batch_step,
+                          &batch_blocks_per_sm, sizeof(LatDesc<R>), &fill_desc, &mass};
         return t;
     }
 };
