@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default="fp32", help="comma list of extra precisions to time")
+    ap.add_argument("--batch-count", type=int, default=256, help="lattices in the batched workload (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -317,12 +319,60 @@ def run_ours(args):
                               "hbm_roofline_pct": round(100 * v_mlups * 1e6 * bytes_per_node(prec) / (hbm_gbs * 1e9), 2)}
             del V
         result["variants"] = variants
+        if args.batch_count > 0:
+            result["batched"] = batched(args, torch, T)
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(result), flush=True)
     if D:
         D.barrier()
         D.destroy_process_group()
+
+
+def batched(args, torch, T):
+    """The batched workload: `batch_count` lattices with sides log-uniform in
+    [64, 512] (drops on a wetting wall, random tensions and angles), FP32.
+    Aggregate MLUPS of (a) the plain path, one tlb_step call per lattice, and
+    (b) one batch (persistent tile-queue kernel, graph-captured), after the
+    batch tuner picked its tile shape."""
+    import workloads as W
+    ws = W.batch_population(args.batch_count, seed=1710)
+    nodes = sum(w.nodes for w in ws)
+    k = args.batch_steps
+    plain = [T.lattice_from_workload(w, "fp32") for w in ws]
+    for L in plain:
+        L.step(2)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for L in plain:
+        L.step(k)
+    s1.record()
+    s1.synchronize()
+    plain_ms = s0.elapsed_time(s1)
+    del plain
+    mem = [T.lattice_from_workload(w, "fp32") for w in ws]
+    B = T.Batch("fp32", max_lattices=len(mem), max_tiles=sum(T.Batch.tiles_needed(w.nx, w.ny) for w in ws),
+                max_wall_nodes=sum(L.wall_nodes() for L in mem))
+    for L in mem:
+        B.add(L)
+    cfg = B.tune(trial_steps=3)
+    B.step(2)
+    B.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(B.stream)
+    B.step(k)
+    b1.record(B.stream)
+    b1.synchronize()
+    batch_ms = b0.elapsed_time(b1)
+    out = {"workload": f"{len(ws)} lattices, sides log-uniform 64..512 (seed 1710), drops on a wetting wall, FP32",
+           "nodes": nodes, "steps": k,
+           "plain_mlups": round(nodes * k / (plain_ms / 1e3) / 1e6, 1),
+           "batched_mlups": round(nodes * k / (batch_ms / 1e3) / 1e6, 1),
+           "tuned": cfg}
+    out["speedup"] = round(out["batched_mlups"] / out["plain_mlups"], 2)
+    B.close()
+    return out
 
 
 def e2e(L, w, args, torch, T):

@@ -256,3 +256,64 @@ def random_lattice(nx, ny, seed, edges=None, solids=("disc",), u_amp=0.01, rho=(
         uy[ny - 1, :] = 0
     return Workload(f"random_{nx}x{ny}_s{seed}", nx, ny, tuple(edges), mask, P, c1, c2, ux, uy,
                     steps=0)
+
+
+# ---- many independent lattices (batched / served workloads) ------------------
+
+def _draw_tensions_and_angles(rng):
+    """sigma_ij ~ U[5e-4, 2e-3] each, redrawn until lambda_i > lambda_T / 2 (the
+    well-posed range stated after Eq. 7); theta_13, theta_23 ~ U[30, 150] deg with
+    theta_12 from Eq. 39, redrawn until it exists."""
+    while True:
+        s = rng.uniform(5e-4, 2e-3, 3)
+        lam = np.array([s[0] + s[1] - s[2], s[0] + s[2] - s[1], s[1] + s[2] - s[0]])
+        if np.any(lam <= 0):
+            continue
+        lamT = 3.0 / np.sum(1.0 / lam)
+        if np.any(lam <= 0.5 * lamT):
+            continue
+        th13, th23 = rng.uniform(30.0, 150.0, 2)
+        try:
+            th12 = theta12_from(*s, th13, th23)
+        except ValueError:
+            continue
+        return tuple(s), (th12, th13, th23)
+
+
+def drops_on_wall(n, seed, rng=None):
+    """A square lattice of side n (x-periodic, wetting bottom wall, neutral top)
+    with 1-4 non-overlapping drops of radius U[8, 40] (fluid 1 or 2), on the wall
+    or free; random admissible tensions and contact angles."""
+    rng = rng or np.random.default_rng(seed)
+    x, y = grid(n, n)
+    c1 = np.zeros((n, n))
+    c2 = np.zeros((n, n))
+    placed = []
+    for _ in range(int(rng.integers(1, 5))):
+        for _attempt in range(20):
+            R = float(rng.uniform(8.0, min(40.0, n / 4)))
+            on_wall = rng.random() < 0.5
+            xc = float(rng.uniform(0, n))
+            yc = -0.5 if on_wall else float(rng.uniform(R + 4, n - R - 4))
+            if all(np.hypot(((xc - px + n / 2) % n) - n / 2, yc - py) > R + pr + 6 for px, py, pr in placed):
+                placed.append((xc, yc, R))
+                prof = profile(x, y, xc, yc, R, 4.0, period_x=n)
+                if rng.random() < 0.5:
+                    c1 = np.maximum(c1, prof)
+                else:
+                    c2 = np.maximum(c2, prof)
+                break
+    sigma, theta = _draw_tensions_and_angles(rng)
+    P = params(sigma=sigma, theta=theta, rho=(1.0, 1.0, 1.0), nu=(0.1, 0.1, 0.1), mobility=0.1, D=4.0)
+    z = np.zeros((n, n))
+    return Workload(f"drops_on_wall_{n}", n, n, (PERIODIC, PERIODIC, WETTING, NEUTRAL),
+                    np.zeros((n, n), np.uint8), P, c1, c2, z, z.copy())
+
+
+def batch_population(count=256, seed=1710, lo=64, hi=512):
+    """`count` lattices with square sides log-uniform in [lo, hi] rounded to
+    multiples of 8, each a drops-on-wall problem (the batched workload)."""
+    rng = np.random.default_rng(seed)
+    sides = np.exp(rng.uniform(np.log(lo), np.log(hi), count))
+    sides = np.clip((np.round(sides / 8) * 8).astype(int), lo, hi)
+    return [drops_on_wall(int(n), 0, rng) for n in sides]
