@@ -317,3 +317,34 @@ def batch_population(count=256, seed=1710, lo=64, hi=512):
     sides = np.exp(rng.uniform(np.log(lo), np.log(hi), count))
     sides = np.clip((np.round(sides / 8) * 8).astype(int), lo, hi)
     return [drops_on_wall(int(n), 0, rng) for n in sides]
+
+
+def drop_on_cylinder(n, rng):
+    """A fully periodic square lattice of side n with a wetting cylinder of
+    radius n/8 and a compound drop (core n/24, shell n/12) above it falling at
+    the speed of a random Weber number in [1, 50] (the impact set-up)."""
+    sig = float(rng.uniform(5e-3, 1.5e-2))
+    th = float(rng.uniform(30.0, 150.0))
+    w = compound_drop_on_cylinder(nx=n, ny=n, R_cyl=n / 8, R_core=n / 24, R_shell=n / 12,
+                                  We=float(rng.uniform(1.0, 50.0)), theta=th,
+                                  cyl_center=(n / 2, n / 2), drop_center=(n / 2, n / 2 + n / 8 + n / 12 + 6))
+    s12 = sig
+    w.params.update(params(sigma=(s12, sig, sig), theta=(90.0, th, th), rho=(10.0, 10.0, 1.0),
+                           nu=(0.02, 0.02, 0.02), mobility=0.1, D=4.0))
+    w.name = f"drop_on_cylinder_{n}"
+    return w
+
+
+def served_requests(count=200, seed=1710, lo=128, hi=2048, steps_lo=1000, steps_hi=20000):
+    """The served workload: `count` jobs, half drops on a wetting wall and half
+    compound drops onto a cylinder, square sides log-uniform in [lo, hi]
+    (multiples of 8) and step counts log-uniform in [steps_lo, steps_hi].
+    Returns a list of (workload, steps)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(np.clip(round(math.exp(rng.uniform(math.log(lo), math.log(hi))) / 8) * 8, lo, hi))
+        steps = int(round(math.exp(rng.uniform(math.log(steps_lo), math.log(steps_hi)))))
+        w = drops_on_wall(n, 0, rng) if rng.random() < 0.5 else drop_on_cylinder(n, rng)
+        out.append((w, steps))
+    return out
