@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--variants", default="fp32", help="comma list of extra precisions to time")
     ap.add_argument("--batch-count", type=int, default=256, help="lattices in the batched workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--serve-count", type=int, default=40, help="requests in the served workload (0: skip)")
+    ap.add_argument("--serve-budget-gb", type=float, default=2.0)
     return ap.parse_args()
 
 
@@ -321,6 +323,8 @@ def run_ours(args):
         result["variants"] = variants
         if args.batch_count > 0:
             result["batched"] = batched(args, torch, T)
+        if args.serve_count > 0:
+            result["served"] = served(args, torch, T)
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(result), flush=True)
@@ -372,6 +376,25 @@ def batched(args, torch, T):
            "tuned": cfg}
     out["speedup"] = round(out["batched_mlups"] / out["plain_mlups"], 2)
     B.close()
+    return out
+
+
+def served(args, torch, T):
+    """The served workload: Poisson arrivals (20 requests/s, seed 1710) of
+    drop-on-wall and drop-on-cylinder jobs, sides log-uniform 128..1024, steps
+    log-uniform 500..5000, FP32, admitted by device footprint against an HBM
+    budget; time to result and aggregate MLUPS over the whole run."""
+    import workloads as W
+    from paper_1710_09534_gb300.serve import Request, Server, poisson_arrivals
+    jobs = W.served_requests(args.serve_count, seed=1710, lo=128, hi=1024, steps_lo=500, steps_hi=5000)
+    t_arr = poisson_arrivals(len(jobs), 20.0, seed=1710)
+    reqs = [Request(i, w, s, "fp32", float(t)) for i, ((w, s), t) in enumerate(zip(jobs, t_arr))]
+    srv = Server(int(args.serve_budget_gb * 1e9), max_lattices=256, chunk=200)
+    stats = srv.run(reqs)
+    srv.close()
+    out = stats.summary()
+    out["workload"] = (f"{len(reqs)} requests, Poisson 20/s (seed 1710), sides 128..1024, steps 500..5000, "
+                       f"FP32, HBM budget {args.serve_budget_gb} GB")
     return out
 
 
