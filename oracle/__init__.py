@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
         "sigma12", "sigma13", "sigma23",
         "theta12_deg", "theta13_deg", "theta23_deg",
         "rho1", "rho2", "rho3", "nu1", "nu2", "nu3",
-        "M0", "D", "tau1", "tau2", "gx", "gy", "lid_u")]
+        "M0", "D", "tau1", "tau2", "gx", "gy", "lid_u", "collision", "mrt_s_f", "mrt_s_g")]
 
 
 def build(force: bool = False) -> str:
@@ -88,6 +88,9 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).argtypes = [ctypes.c_int]
             getattr(L, name).restype = ctypes.c_int
         L.orc_threads.restype = ctypes.c_int
+        L.orc_mrt_matrix.argtypes = [dp]
+        L.orc_mrt_inverse.argtypes = [dp]
+        L.orc_mrt_relax.argtypes = [dp, dp, dp, dp, dp]
         L.orc_w.argtypes = [ctypes.c_int]
         L.orc_w.restype = ctypes.c_double
         _lib = L
@@ -104,7 +107,7 @@ def _f64(a) -> np.ndarray:
 
 def make_params(**kw) -> Params:
     P = Params()
-    defaults = dict(tau1=0.8, tau2=0.8, gx=0.0, gy=0.0, lid_u=0.0)
+    defaults = dict(tau1=0.8, tau2=0.8, gx=0.0, gy=0.0, lid_u=0.0, collision=0.0, mrt_s_f=1.0, mrt_s_g=1.0)
     defaults.update(kw)
     for name, _ in Params._fields_:
         setattr(P, name, float(defaults[name]))
@@ -237,6 +240,22 @@ def src_g(k, taug, ux, uy, grx, gry, Ftx, Fty, Fax, Fay):
 def threads() -> int:
     """OpenMP threads the oracle's passes run on."""
     return lib().orc_threads()
+
+
+def mrt_matrices():
+    """The MRT moment matrix M and its inverse (reading R8 of tlb_oracle.c)."""
+    m = np.zeros(81)
+    mi = np.zeros(81)
+    lib().orc_mrt_matrix(_dp(m))
+    lib().orc_mrt_inverse(_dp(mi))
+    return m.reshape(9, 9), mi.reshape(9, 9)
+
+
+def mrt_relax(f, feq, src, s):
+    out = np.zeros(9)
+    args = [_f64(a) for a in (f, feq, src, s)]
+    lib().orc_mrt_relax(*(_dp(a) for a in args), _dp(out))
+    return out
 
 
 def lattice_vectors():

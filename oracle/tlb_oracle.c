@@ -36,6 +36,17 @@
  *   R6  At a lattice corner that is outside in both x and y, the x edge
  *       decides the kind of the outside site.
  *   R7  Body force G = rho * (gx, gy); the paper's gravity is (0, -g).
+ *   R8  MRT option (the paper uses BGK only): each distribution relaxes in the
+ *       orthogonal D2Q9 moment basis of Lallemand and Luo (density, energy,
+ *       energy squared, x flux, x energy flux, y flux, y energy flux, two
+ *       stresses) with f' = f - M^-1 S (M f - M f^eq) + M^-1 (I - S/2) M F,
+ *       F the source without its (1 - 1/(2 tau)) factor, so S = I / tau is
+ *       exactly the BGK update.  f^i: fluxes (and the conserved density) at
+ *       1/tau_i, which fixes the mobility of Eq. 18a; the other moments at
+ *       mrt_s_f.  g: density, fluxes and stresses at 1/tau_g, which fixes the
+ *       viscosity of Eq. 18b; energy, energy squared and energy fluxes at
+ *       mrt_s_g.  The F_a part of Eq. 11b carries no (1 - 1/(2 tau_g)) factor
+ *       and is added after the relaxation.
  */
 #include <math.h>
 #include <stdint.h>
@@ -67,6 +78,9 @@ typedef struct {
     double tau1, tau2;                         /* relaxation times, Eq. 1a */
     double gx, gy;                             /* body force per unit mass (R7) */
     double lid_u;                              /* U0 of the velocity lid, Eq. 53 */
+    double collision;                          /* 0 BGK (Eqs. 1a, 1b), 1 MRT (R8) */
+    double mrt_s_f;                            /* MRT rate of the non-flux moments of f^i */
+    double mrt_s_g;                            /* MRT rate of e, eps, q_x, q_y of g */
 } orc_params;
 
 enum { EDGE_PERIODIC = 0, EDGE_WETTING = 1, EDGE_NEUTRAL = 2, EDGE_LID = 3 };
@@ -206,6 +220,65 @@ int orc_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ---- MRT option (reading R8) ---------------------------------------------- */
+/* Moment matrix: rows are 1, e = -4 + 3|e_k|^2, eps = 4 - 21/2 |e_k|^2 + 9/2 |e_k|^4,
+ * j_x = e_kx, q_x = (-5 + 3|e_k|^2) e_kx, j_y, q_y, p_xx = e_kx^2 - e_ky^2, p_xy = e_kx e_ky. */
+static const double MM[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},
+    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},
+    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+/* squared row norms: the rows are orthogonal, so M^-1 = M^T diag(1 / norm) */
+static const double MNORM[9] = {9, 36, 36, 6, 12, 6, 12, 4, 4};
+
+void orc_mrt_matrix(double out[81])
+{
+    for (int r = 0; r < 9; r++)
+        for (int k = 0; k < 9; k++)
+            out[9 * r + k] = MM[r][k];
+}
+
+void orc_mrt_inverse(double out[81])
+{
+    for (int k = 0; k < 9; k++)
+        for (int r = 0; r < 9; r++)
+            out[9 * k + r] = MM[r][k] / MNORM[r];
+}
+
+/* f' = f - M^-1 S (M f - M feq) + M^-1 (I - S/2) M src for one distribution. */
+static void mrt_relax(const double f[9], const double feq[9], const double src[9], const double s[9],
+                      double out[9])
+{
+    double mp[9];
+    for (int r = 0; r < 9; r++) {
+        double m = 0.0, meq = 0.0, ms = 0.0;
+        for (int k = 0; k < 9; k++) {
+            m += MM[r][k] * f[k];
+            meq += MM[r][k] * feq[k];
+            ms += MM[r][k] * src[k];
+        }
+        mp[r] = m - s[r] * (m - meq) + (1.0 - s[r] / 2.0) * ms;
+    }
+    for (int k = 0; k < 9; k++) {
+        double v = 0.0;
+        for (int r = 0; r < 9; r++)
+            v += MM[r][k] * mp[r] / MNORM[r];
+        out[k] = v;
+    }
+}
+
+/* Exported for the tests: one MRT relaxation with the given rates. */
+void orc_mrt_relax(const double f[9], const double feq[9], const double src[9], const double s[9],
+                   double out[9])
+{
+    mrt_relax(f, feq, src, s, out);
 }
 
 int orc_ex(int k) { return EX[k]; }
@@ -594,8 +667,37 @@ int orc_step(orc_lattice *L, long nsteps)
                     fin[18 + k] = geq_u + (L->f[(long)(18 + k) * n + b] - geq_f);
                 }
             }
-            /* Collision, Eqs. 1a, 1b and 45. */
+            /* Collision, Eqs. 1a, 1b and 45 (BGK), or the MRT option (R8). */
             double fpost[NPL];
+            if (L->P.collision != 0.0) {
+                for (int q = 0; q < 2; q++) {
+                    double eq[9], src[9], s[9], out[9];
+                    for (int k = 0; k < 9; k++) {
+                        eq[k] = orc_feq(k, c[q], mu[q], L->eta[q], ux, uy);
+                        /* Eq. 11a without its (1 - 1/(2 tau_i)) factor */
+                        src[k] = orc_src_f(k, tau[q], dcu[q][0], dcu[q][1]) / (1.0 - 1.0 / (2.0 * tau[q]));
+                        s[k] = L->P.mrt_s_f;
+                    }
+                    s[0] = s[3] = s[5] = 1.0 / tau[q];
+                    mrt_relax(&fin[9 * q], eq, src, s, out);
+                    for (int k = 0; k < 9; k++)
+                        fpost[9 * q + k] = out[k];
+                }
+                double eq[9], src[9], s[9], out[9];
+                for (int k = 0; k < 9; k++) {
+                    eq[k] = orc_geq(k, p, rho, ux, uy);
+                    /* Eq. 11b: the bracket without (1 - 1/(2 tau_g)); F_a added below */
+                    double with_fa = orc_src_g(k, taug, ux, uy, L->grx[i], L->gry[i], Fs[0] + Gx,
+                                               Fs[1] + Gy, Fax, Fay);
+                    double fa = WK[k] * (EX[k] * Fax + EY[k] * Fay) / CS2;
+                    src[k] = (with_fa - fa) / (1.0 - 1.0 / (2.0 * taug));
+                    s[k] = 1.0 / taug;
+                }
+                s[1] = s[2] = s[4] = s[6] = L->P.mrt_s_g;
+                mrt_relax(&fin[18], eq, src, s, out);
+                for (int k = 0; k < 9; k++)
+                    fpost[18 + k] = out[k] + WK[k] * (EX[k] * Fax + EY[k] * Fay) / CS2;
+            } else
             for (int k = 0; k < 9; k++) {
                 for (int q = 0; q < 2; q++) {
                     double eq = orc_feq(k, c[q], mu[q], L->eta[q], ux, uy);

@@ -64,14 +64,18 @@ def theta12_from(s12, s13, s23, th13_deg, th23_deg):
 
 def params(*, sigma=(1e-3, 1e-3, 1e-3), theta=(90.0, 90.0, 90.0), rho=(1.0, 1.0, 1.0),
            nu=(0.1, 0.1, 0.1), mobility=0.1, D=4.0, tau=(0.8, 0.8), g=(0.0, 0.0),
-           lid_u=0.0, M0=None) -> dict:
+           lid_u=0.0, M0=None, mrt=None) -> dict:
+    """Parameter set; mrt = (s_f, s_g) selects the MRT collision with those rates
+    for the non-conserved, non-flux moments of f^i and the energy moments of g."""
     s12, s13, s23 = sigma
     if M0 is None:
         M0 = mobility * lambda1(s12, s13, s23)
     return dict(sigma12=s12, sigma13=s13, sigma23=s23,
                 theta12_deg=theta[0], theta13_deg=theta[1], theta23_deg=theta[2],
                 rho1=rho[0], rho2=rho[1], rho3=rho[2], nu1=nu[0], nu2=nu[1], nu3=nu[2],
-                M0=M0, D=D, tau1=tau[0], tau2=tau[1], gx=g[0], gy=g[1], lid_u=lid_u)
+                M0=M0, D=D, tau1=tau[0], tau2=tau[1], gx=g[0], gy=g[1], lid_u=lid_u,
+                collision=0.0 if mrt is None else 1.0,
+                mrt_s_f=1.0 if mrt is None else mrt[0], mrt_s_g=1.0 if mrt is None else mrt[1])
 
 
 def grid(nx, ny):
