@@ -78,7 +78,18 @@ enum {
  * must satisfy Eq. 39; rho_i, nu_i: phase densities and viscosities (Eqs. 14,
  * 15); M0: M_i = M0 / lambda_i (Eq. 12); D: interface thickness (Eq. 8);
  * tau1, tau2: relaxation times of Eq. 1a; gx, gy: body force per unit mass;
- * lid_u: U0 of Eq. 53 for a TLB_EDGE_LID top edge. */
+ * lid_u: U0 of Eq. 53 for a TLB_EDGE_LID top edge.
+ * collision: 0 = the BGK operators of Eqs. 1a, 1b (the paper's model); 1 = a
+ * multiple-relaxation-time option beyond the paper, which uses BGK only:
+ * every distribution is relaxed in the orthogonal D2Q9 moment basis of
+ * Lallemand and Luo, f' = f - M^-1 S (M f - M f^eq) + M^-1 (I - S/2) M F with
+ * F the source of Eq. 11a/11b without its (1 - 1/(2 tau)) factor (the F_a part
+ * of Eq. 11b is added unrelaxed).  Rates: for f^i the conserved and flux
+ * moments (rows rho, j_x, j_y) relax at 1/tau_i and the rest at mrt_s_f; for g
+ * the rows rho, j_x, j_y, p_xx, p_xy relax at 1/tau_g (so that Eq. 15 sets the
+ * shear viscosity) and the energy rows e, eps, q_x, q_y at mrt_s_g.  With
+ * mrt_s_f = 1/tau_i and mrt_s_g = 1/tau_g the update equals BGK.  Ignored by
+ * BGK; with collision = 1, 0 < mrt_s_f, mrt_s_g < 2. */
 typedef struct {
     double sigma12, sigma13, sigma23;
     double theta12_deg, theta13_deg, theta23_deg;
@@ -89,6 +100,8 @@ typedef struct {
     double tau1, tau2;
     double gx, gy;
     double lid_u;
+    double collision;
+    double mrt_s_f, mrt_s_g;
 } tlb_params;
 
 /* FP64 diagnostics of the current state (Sec. III.A measures; reduced on
@@ -126,7 +139,9 @@ int tlb_set_geometry(tlb_lattice *lat, const uint8_t *host_mask);
 /* Model parameters.  TLB_EINVAL if: any sigma_ij <= 0, lambda_1 or lambda_2
  * <= 0, lambda_3 < 0 (Eq. 7); D <= 0; rho_i <= 0; nu_i <= 0; tau_i <= 1/2;
  * M0 <= 0; the Eq. 39 residual |s12 cos t12 - s13 cos t13 + s23 cos t23| >
- * 1e-6 max(sigma); a non-finite value.  lambda_i <= lambda_T / 2 (outside the
+ * 1e-6 max(sigma); a non-finite value; collision not 0 or 1; with collision
+ * = 1, an MRT rate outside (0, 2).  Changing the collision model of a batch
+ * member makes the next batch step fail unless every member agrees.  lambda_i <= lambda_T / 2 (outside the
  * well-posed range stated after Eq. 7) is accepted; the message then says so. */
 int tlb_set_params(tlb_lattice *lat, const tlb_params *params);
 

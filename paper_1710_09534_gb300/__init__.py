@@ -38,12 +38,12 @@ class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "sigma12", "sigma13", "sigma23", "theta12_deg", "theta13_deg", "theta23_deg",
         "rho1", "rho2", "rho3", "nu1", "nu2", "nu3", "M0", "D", "tau1", "tau2",
-        "gx", "gy", "lid_u")]
+        "gx", "gy", "lid_u", "collision", "mrt_s_f", "mrt_s_g")]
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
         p = cls()
-        full = dict(tau1=0.8, tau2=0.8, gx=0.0, gy=0.0, lid_u=0.0)
+        full = dict(tau1=0.8, tau2=0.8, gx=0.0, gy=0.0, lid_u=0.0, collision=0.0, mrt_s_f=1.0, mrt_s_g=1.0)
         full.update(d)
         for name, _ in cls._fields_:
             setattr(p, name, float(full[name]))

@@ -228,7 +228,7 @@ int tlb_create_lattice(int nx, int ny, int precision, const int32_t edges[4], vo
     L->stream = (cudaStream_t)cuda_stream;
     L->ws = (char*)dev_workspace;
     L->lay = lay;
-    L->ops = precision == TLB_FP64 ? &tlb::ops_f64() : &tlb::ops_f32();
+    L->ops = &tlb::ops_for(precision, false);
     L->geo.nx = nx;
     L->geo.ny = ny;
     L->geo.pitch = lay.pitch;
@@ -296,6 +296,10 @@ int tlb_set_params(tlb_lattice* L, const tlb_params* p)
     if (p->nu1 <= 0 || p->nu2 <= 0 || p->nu3 <= 0) return fail(TLB_EINVAL, "viscosities must be > 0");
     if (p->tau1 <= 0.5 || p->tau2 <= 0.5) return fail(TLB_EINVAL, "tau_i must be > 1/2");
     if (p->M0 <= 0) return fail(TLB_EINVAL, "M0 must be > 0");
+    if (p->collision != 0.0 && p->collision != 1.0) return fail(TLB_EINVAL, "collision must be 0 (BGK) or 1 (MRT)");
+    const bool mrt = p->collision == 1.0;
+    if (mrt && !(p->mrt_s_f > 0 && p->mrt_s_f < 2 && p->mrt_s_g > 0 && p->mrt_s_g < 2))
+        return fail(TLB_EINVAL, "MRT rates must lie in (0, 2)");
     const double deg = 3.14159265358979323846 / 180.0;
     const double c12 = std::cos(p->theta12_deg * deg), c13 = std::cos(p->theta13_deg * deg),
                  c23 = std::cos(p->theta23_deg * deg);
@@ -350,6 +354,10 @@ int tlb_set_params(tlb_lattice* L, const tlb_params* p)
     P.gx = p->gx;
     P.gy = p->gy;
     P.lid_u = p->lid_u;
+    P.mrt = mrt ? 1.0 : 0.0;
+    P.mrt_s_f = mrt ? p->mrt_s_f : 1.0;
+    P.mrt_s_g = mrt ? p->mrt_s_g : 1.0;
+    L->ops = &tlb::ops_for(L->precision, mrt);
     L->have_params = true;
     L->have_fields = false;
     tlb::batch_member_changed(L->batch);

@@ -73,6 +73,7 @@ struct tlb_batch {
     int grid_interior = 0, grid_wall = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_variant = -1;
+    const tlb::Ops* graph_ops = nullptr;
 };
 
 namespace {
@@ -89,6 +90,13 @@ int64_t tiles_of(int variant, int rows, int nx, int ny)
 // contiguous so that neighbouring segments run together) and wall list.
 int rebuild(tlb_batch* B)
 {
+    // one collision model per batch: the members' launch tables must agree
+    if (!B->members.empty()) {
+        for (const tlb_lattice* L : B->members)
+            if (L->ops != B->members[0]->ops)
+                return err(TLB_EINVAL, "batch members use different collision models (BGK and MRT)");
+        B->ops = B->members[0]->ops;
+    }
     const size_t ds = B->ops->desc_size;
     std::vector<char> descs(ds * B->members.size());
     std::vector<int> order(B->members.size());
@@ -148,7 +156,7 @@ int launch_step(tlb_batch* B, int parity)
 // and descriptors live in device memory).
 int ensure_graph(tlb_batch* B)
 {
-    if (B->graph && B->graph_variant == B->variant) return TLB_OK;
+    if (B->graph && B->graph_variant == B->variant && B->graph_ops == B->ops) return TLB_OK;
     if (B->graph) {
         cudaGraphExecDestroy(B->graph);
         B->graph = nullptr;
@@ -164,6 +172,7 @@ int ensure_graph(tlb_batch* B)
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) return err(TLB_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
     B->graph_variant = B->variant;
+    B->graph_ops = B->ops;
     return TLB_OK;
 }
 
@@ -253,7 +262,7 @@ int tlb_batch_create(int precision, int max_lattices, int64_t max_tiles, int64_t
     B->max_lattices = max_lattices;
     B->max_tiles = max_tiles;
     B->max_wall = max_wall_nodes;
-    B->ops = precision == TLB_FP64 ? &tlb::ops_f64() : &tlb::ops_f32();
+    B->ops = &tlb::ops_for(precision, false);
     if (cudaGetDevice(&B->device) != cudaSuccess) {
         delete B;
         return err(TLB_ECUDA, "no current device");

@@ -61,6 +61,9 @@ struct Prm {
     R cos12, cos13, cos23;
     R gx, gy;
     R lid_u;
+    R mrt;            // 1: MRT collision (moment basis below), 0: BGK
+    R mrt_s_f;        // MRT rate of the non-flux moments of f^i
+    R mrt_s_g;        // MRT rate of the energy moments of g
 };
 
 // Site of (x, y), possibly outside the lattice; on an inside site sets the
@@ -313,6 +316,143 @@ __device__ __forceinline__ void equilibria(int k, const Prm<R>& P, R c1, R c2, R
         geq = R(3) * p * w + rho * sk;
     }
 }
+
+// ---- MRT option: orthogonal D2Q9 moment basis (Lallemand and Luo) --------
+// rows: 1, -4 + 3|e|^2, 4 - 21/2 |e|^2 + 9/2 |e|^4, e_x, (-5 + 3|e|^2) e_x, e_y,
+// (-5 + 3|e|^2) e_y, e_x^2 - e_y^2, e_x e_y; squared norms 9 36 36 6 12 6 12 4 4.
+__host__ __device__ constexpr int mrt_m(int r, int k)
+{
+    return r == 0 ? 1
+         : r == 1 ? -4 + 3 * (ex(k) * ex(k) + ey(k) * ey(k))
+         : r == 2 ? (8 - 21 * (ex(k) * ex(k) + ey(k) * ey(k)) + 9 * (ex(k) * ex(k) + ey(k) * ey(k)) * (ex(k) * ex(k) + ey(k) * ey(k))) / 2
+         : r == 3 ? ex(k)
+         : r == 4 ? (-5 + 3 * (ex(k) * ex(k) + ey(k) * ey(k))) * ex(k)
+         : r == 5 ? ey(k)
+         : r == 6 ? (-5 + 3 * (ex(k) * ex(k) + ey(k) * ey(k))) * ey(k)
+         : r == 7 ? ex(k) * ex(k) - ey(k) * ey(k)
+                  : ex(k) * ey(k);
+}
+__host__ __device__ constexpr double mrt_inv_norm(int r)
+{
+    return r == 0 ? 1.0 / 9 : (r == 1 || r == 2) ? 1.0 / 36 : (r == 3 || r == 5) ? 1.0 / 6 : (r == 4 || r == 6) ? 1.0 / 12 : 1.0 / 4;
+}
+
+// v' = v + M^-1 [ -S M (v - veq) + (I - S/2) M src ]  (equal rates: the BGK update)
+template <typename R>
+__device__ __forceinline__ void mrt_relax(const R v[9], const R veq[9], const R src[9], const R s[9], R out[9])
+{
+    R mp[9];
+#pragma unroll
+    for (int r = 0; r < 9; r++) {
+        R mn = R(0), ms = R(0);
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            if (mrt_m(r, k) != 0) {
+                mn = fma(R(mrt_m(r, k)), v[k] - veq[k], mn);
+                ms = fma(R(mrt_m(r, k)), src[k], ms);
+            }
+        }
+        mp[r] = fma(fma(R(-0.5), s[r], R(1)), ms, -s[r] * mn) * R(mrt_inv_norm(r));
+    }
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        R acc = v[k];
+#pragma unroll
+        for (int r = 0; r < 9; r++)
+            if (mrt_m(r, k) != 0) acc = fma(R(mrt_m(r, k)), mp[r], acc);
+        out[k] = acc;
+    }
+}
+
+// Per-node inputs of the MRT update: equilibria (Eqs. 2a, 2b) and the source
+// terms of Eqs. 11a, 11b without their (1 - 1/(2 tau)) factors; the F_a part of
+// Eq. 11b is added after the relaxation.
+template <typename R>
+struct MrtNode {
+    R c[2], emu[2], d[2][2];  // c_i, eta_i mu_i, d/dt (c_i u)
+    R ux, uy, t0, p, rho;
+    R H[4], T[4], uH, uT, Z[4];
+    R s_f[2][9], s_g[9];
+
+    __device__ __forceinline__ void build(const Prm<R>& P, const Macro<R>& m, const Hydro<R>& h,
+                                          R d1x, R d1y, R d2x, R d2y)
+    {
+        c[0] = m.c1;
+        c[1] = m.c2;
+        emu[0] = P.eta[0] * m.mu1;
+        emu[1] = P.eta[1] * m.mu2;
+        d[0][0] = d1x;
+        d[0][1] = d1y;
+        d[1][0] = d2x;
+        d[1][1] = d2y;
+        ux = h.ux;
+        uy = h.uy;
+        t0 = R(-1.5) * h.usq;
+        p = h.p;
+        rho = m.rho;
+        const R Tx = R(3) * h.Ftx, Ty = R(3) * h.Fty;
+        const R Hx = h.grx + Tx, Hy = h.gry + Ty;
+        H[0] = Hx;
+        H[1] = Hy;
+        H[2] = Hx + Hy;
+        H[3] = Hx - Hy;
+        T[0] = Tx;
+        T[1] = Ty;
+        T[2] = Tx + Ty;
+        T[3] = Tx - Ty;
+        uH = fma(ux, Hx, uy * Hy);
+        uT = fma(ux, Tx, uy * Ty);
+        const R za = R(3.0 / 9.0) * h.a, zd = R(3.0 / 36.0) * h.a;
+        Z[0] = za * ux;
+        Z[1] = za * uy;
+        Z[2] = zd * (ux + uy);
+        Z[3] = zd * (ux - uy);
+#pragma unroll
+        for (int r = 0; r < 9; r++) {
+            const bool flux = r == 0 || r == 3 || r == 5;
+            s_f[0][r] = flux ? P.inv_tau[0] : P.mrt_s_f;
+            s_f[1][r] = flux ? P.inv_tau[1] : P.mrt_s_f;
+            s_g[r] = (r == 1 || r == 2 || r == 4 || r == 6) ? P.mrt_s_g : h.inv_taug;
+        }
+    }
+
+    // post-collision populations of f^1, f^2, g from the pre-collision ones
+    __device__ __forceinline__ void apply(const R f1[9], const R f2[9], const R g[9], R o1[9], R o2[9], R og[9]) const
+    {
+        R eq[9], src[9];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                const R w = R(wk(k));
+                const R eu = R(ex(k)) * ux + R(ey(k)) * uy;
+                eq[k] = k == 0 ? c[i] + (w - R(1)) * emu[i] : w * fma(R(3) * c[i], eu, emu[i]);
+                src[k] = R(3) * w * (R(ex(k)) * d[i][0] + R(ey(k)) * d[i][1]);
+            }
+            mrt_relax(i == 0 ? f1 : f2, eq, src, s_f[i], i == 0 ? o1 : o2);
+        }
+        R fa[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const R w = R(wk(k));
+            if (k == 0) {
+                eq[0] = fma(rho * w, t0, R(3) * (w - R(1)) * p);
+                src[0] = w * -fma(t0, uH, uT);
+                fa[0] = R(0);
+            } else {
+                const R sg = R(sgn(k));
+                const R e = sg * (comp(k) == 0 ? ux : comp(k) == 1 ? uy : comp(k) == 2 ? ux + uy : ux - uy);
+                const R q = fma(e, fma(R(4.5), e, R(3)), t0);
+                eq[k] = w * fma(rho, q, R(3) * p);
+                src[k] = w * fma(q, fma(sg, H[comp(k)], -uH), fma(sg, T[comp(k)], -uT));
+                fa[k] = sg * Z[comp(k)];
+            }
+        }
+        mrt_relax(g, eq, src, s_g, og);
+#pragma unroll
+        for (int k = 0; k < 9; k++) og[k] += fa[k];
+    }
+};
 
 template <typename S>
 __device__ __forceinline__ S ldg(const S* p) { return __ldg(p); }

@@ -1,6 +1,6 @@
-// FP32 storage, FP32 arithmetic.
+// FP32 storage, FP32 arithmetic, BGK collision.
 #include "tlbm_ops_impl.cuh"
 
 namespace tlb {
-const Ops& ops_f32() { return OpsImpl<float, float, kBlock32, kRows32, kPrefetch32, kMinB32>::table(); }
+const Ops& ops_f32() { return OpsImpl<float, float, kBlock32, kRows32, kPrefetch32, kMinB32, false>::table(); }
 }  // namespace tlb

@@ -126,6 +126,57 @@ __device__ __forceinline__ void collide_all(const Collider<R>& col, const R gv[9
     }
 }
 
+// The same contract with the MRT collision: the nine populations of each
+// distribution are relaxed together in moment space, so all are loaded first.
+template <typename S, typename R, typename Load, typename LoadLo, typename St, typename StLo>
+__device__ __forceinline__ void collide_all(const MrtNode<R>& col, const R gv[9], Load load, LoadLo load_lo,
+                                            St store, StLo store_lo)
+{
+    constexpr bool ff = Store<S>::kLo;
+    R f1[9], f2[9], o1[9], o2[9], og[9];
+    static_for<0, 9>([&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        load(kc, f1[K], f2[K]);
+    });
+    const R h10 = f1[0], h20 = f2[0];
+    R l1 = R(0), l2 = R(0);
+    if constexpr (ff) {
+        load_lo(l1, l2);
+        f1[0] += l1;
+        f2[0] += l2;
+    }
+    col.apply(f1, f2, gv, o1, o2, og);
+    if constexpr (ff) {
+        FF in1, in2, out1, out2;
+#pragma unroll
+        for (int k = 1; k < 9; k++) {
+            in1.add(f1[k]);
+            in2.add(f2[k]);
+            out1.add(o1[k]);
+            out2.add(o2[k]);
+        }
+        in1.add(h10);
+        in1.add(l1);
+        in2.add(h20);
+        in2.add(l2);
+        R hh1, hh2, lo1, lo2;
+        ff_sub(in1, out1, hh1, lo1);
+        ff_sub(in2, out2, hh2, lo2);
+        store(std::integral_constant<int, 0>{}, hh1, hh2, og[0]);
+        store_lo(lo1, lo2);
+    } else {
+        store(std::integral_constant<int, 0>{}, o1[0], o2[0], og[0]);
+    }
+    static_for<1, 9>([&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        store(kc, o1[K], o2[K], og[K]);
+    });
+}
+
+// Per-node collision data of the BGK (MRT = false) or MRT update.
+template <bool MRT, typename R>
+using CollideOf = typename std::conditional<MRT, MrtNode<R>, Collider<R>>::type;
+
 // Periodic wrap of a destination that may leave the lattice by one node on a
 // periodic axis (interior nodes never reach a non-periodic edge).
 __device__ __forceinline__ long long wrap_off(const Geo& g, int x, int y)
@@ -158,7 +209,7 @@ struct TileRings {
 
 // One tile: strip bx (columns bx*(BLOCK-4) .. +BLOCK-5), segment by (rows
 // by*rows .. +rows-1, marching up for even by and down for odd by).
-template <typename S, typename R, int BLOCK, bool PREFETCH>
+template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT>
 __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
                                               const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
                                               int bx, int by, int rows, TileRings<R, BLOCK>& sh)
@@ -283,7 +334,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         cu[1 * PL + ou] = S(c1uy);
         cu[2 * PL + ou] = S(c2ux);
         cu[3 * PL + ou] = S(c2uy);
-        Collider<R> col;
+        CollideOf<MRT, R> col;
         col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
         collide_all<S, R>(col, gv,
             [&](auto kc, R& f1k, R& f2k) {
@@ -309,13 +360,13 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
     }
 }
 
-template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB>
+template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT>
 __global__ void __launch_bounds__(BLOCK, MINB)
 k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
                 const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
 {
     __shared__ TileRings<R, BLOCK> sh;
-    interior_tile<S, R, BLOCK, PREFETCH>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
+    interior_tile<S, R, BLOCK, PREFETCH, MRT>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -480,7 +531,7 @@ __device__ __forceinline__ void push_wall(const Geo& g, const uint8_t* __restric
 // ---------------------------------------------------------------------------
 // K2: near-wall and lid nodes from the compacted list.
 // ---------------------------------------------------------------------------
-template <typename S, typename R>
+template <typename S, typename R, bool MRT>
 __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
                                           const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
                                           uint32_t packed)
@@ -506,7 +557,7 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
         cu[1 * PL + o] = S(c1uy);
         cu[2 * PL + o] = S(c2ux);
         cu[3 * PL + o] = S(c2uy);
-        Collider<R> col;
+        CollideOf<MRT, R> col;
         col.build(P, m, h, d1x, d1y, d2x, d2y);
         collide_all<S, R>(col, gv,
             [&](auto kc, R& f1k, R& f2k) {
@@ -547,7 +598,7 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
         cu[1 * PL + o] = S(0);
         cu[2 * PL + o] = S(c2ux);
         cu[3 * PL + o] = S(0);
-        Collider<R> col;
+        CollideOf<MRT, R> col;
         col.build(P, m, h, d1x, d1y, d2x, d2y);
         // Eq. 51: f(x_u) = f^eq(x_u) + [f(x_f) - f^eq(x_f)], for f^1, f^2 and g
         R gu[9], f1u[9], f2u[9];
@@ -597,14 +648,14 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
     }
 }
 
-template <typename S, typename R>
+template <typename S, typename R, bool MRT>
 __global__ void __launch_bounds__(128)
 k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
             const uint8_t* __restrict__ cls, const uint32_t* __restrict__ list, int nlist, Geo g, Prm<R> P)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nlist) return;
-    wall_node<S, R>(fA, fB, cu, cls, g, P, list[t]);
+    wall_node<S, R, MRT>(fA, fB, cu, cls, g, P, list[t]);
 }
 
 // ---------------------------------------------------------------------------

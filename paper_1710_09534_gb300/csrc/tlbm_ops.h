@@ -43,6 +43,15 @@ inline int ndist_for(int precision) { return precision == 0 ? 27 : 29; }
 
 const Ops& ops_f64();
 const Ops& ops_f32();
+const Ops& ops_f64_mrt();
+const Ops& ops_f32_mrt();
+
+// launch table of a storage precision (0 FP64, 1 FP32) and collision model
+inline const Ops& ops_for(int precision, bool mrt)
+{
+    if (precision == 0) return mrt ? ops_f64_mrt() : ops_f64();
+    return mrt ? ops_f32_mrt() : ops_f32();
+}
 
 // Fused interior kernel: threads per block (one column each, 4 of them halo)
 // and rows marched per block, per precision.

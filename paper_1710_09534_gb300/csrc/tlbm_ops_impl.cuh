@@ -44,10 +44,13 @@ inline Prm<R> cast_prm(const Prm<double>& d)
     r.gx = R(d.gx);
     r.gy = R(d.gy);
     r.lid_u = R(d.lid_u);
+    r.mrt = R(d.mrt);
+    r.mrt_s_f = R(d.mrt_s_f);
+    r.mrt_s_g = R(d.mrt_s_g);
     return r;
 }
 
-template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB>
+template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT>
 struct OpsImpl {
     static cudaError_t interior(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
                                 const Prm<double>& Pd, cudaStream_t s)
@@ -55,7 +58,7 @@ struct OpsImpl {
         const Prm<R> P = cast_prm<R>(Pd);
         constexpr int TX = BLOCK - 4;
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + ROWS - 1) / ROWS);
-        k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB><<<grid, BLOCK, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, g, P);
+        k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT><<<grid, BLOCK, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, g, P);
         return cudaGetLastError();
     }
     static cudaError_t wall(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
@@ -63,7 +66,7 @@ struct OpsImpl {
     {
         const Prm<R> P = cast_prm<R>(Pd);
         if (nlist > 0)
-            k_step_wall<S, R><<<(nlist + 127) / 128, 128, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, list,
+            k_step_wall<S, R, MRT><<<(nlist + 127) / 128, 128, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, list,
                                                                    nlist, g, P);
         return cudaGetLastError();
     }
@@ -107,21 +110,21 @@ struct OpsImpl {
         cudaError_t e = cudaMemsetAsync(&c->next[parity], 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
         if (variant == 0)
-            k_batch_interior<S, R, 64, PREFETCH, kMinB64><<<grid_interior, 64, 0, s>>>(
+            k_batch_interior<S, R, 64, PREFETCH, kMinB64, MRT><<<grid_interior, 64, 0, s>>>(
                 (const LatDesc<R>*)descs, (const TileItem*)tiles, c, parity);
         else
-            k_batch_interior<S, R, 128, PREFETCH, MINB><<<grid_interior, 128, 0, s>>>(
+            k_batch_interior<S, R, 128, PREFETCH, MINB, MRT><<<grid_interior, 128, 0, s>>>(
                 (const LatDesc<R>*)descs, (const TileItem*)tiles, c, parity);
-        k_batch_wall<S, R><<<grid_wall, 128, 0, s>>>((const LatDesc<R>*)descs, (const WallItem*)walls, c, parity);
+        k_batch_wall<S, R, MRT><<<grid_wall, 128, 0, s>>>((const LatDesc<R>*)descs, (const WallItem*)walls, c, parity);
         return cudaGetLastError();
     }
     static int batch_blocks_per_sm(int variant)
     {
         int n = 0;
         if (variant == 0)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_interior<S, R, 64, PREFETCH, kMinB64>, 64, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_interior<S, R, 64, PREFETCH, kMinB64, MRT>, 64, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_interior<S, R, 128, PREFETCH, MINB>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_interior<S, R, 128, PREFETCH, MINB, MRT>, 128, 0);
         return n;
     }
     static void fill_desc(void* dst, const void* buf0, const void* buf1, void* cu, const uint8_t* cls, const Geo& g,

@@ -72,3 +72,17 @@ def test_create_rejects_bad_arguments_without_touching_the_device(lib):
     assert lib.tlb_create_lattice(16, 16, 0, e, None, 0, None, ctypes.byref(h)) == T.EINVAL
     assert "workspace" in T.last_error()
     assert lib.tlb_step(None, 1) == T.EINVAL
+
+
+def test_python_params_mirror_the_header_struct():
+    """The binding's ctypes Params has the fields of tlb_params, in order."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\} tlb_params;", src).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            assert decl.startswith("double ")
+            names += [n.strip() for n in decl[len("double "):].split(",")]
+    import paper_1710_09534_gb300 as T
+    assert [n for n, _ in T.Params._fields_] == names
