@@ -48,8 +48,17 @@ typedef struct tlb_lattice tlb_lattice;
 typedef struct tlb_batch tlb_batch;
 
 /* Storage precision of the distributions.  TLB_FP64 computes in FP64;
- * TLB_FP32 stores and computes in FP32 (diagnostic sums in FP64). */
-enum { TLB_FP64 = 0, TLB_FP32 = 1 };
+ * TLB_FP32 stores and computes in FP32 (diagnostic sums in FP64).  TLB_FP16
+ * and TLB_BF16 compute in FP32 and store every population except the two rest
+ * populations f^i_0 in 16 bits, after subtracting its equilibrium at rest
+ * (u = 0, mu = 0, p = 0: zero for all of them in this model, Eqs. 2a, 2b) and,
+ * for FP16, scaling by 2^12 so that small populations stay normal numbers; the
+ * rest populations (equilibrium at rest c_i) and the c_i u planes of Eq. 19 stay
+ * FP32, and the rest populations absorb the 16-bit rounding of the moving ones,
+ * so each component's mass is conserved as in FP32 storage.  In all precisions
+ * the rest populations of f^1, f^2 in the FP32 and 16-bit formats are float
+ * pairs hi + lo. */
+enum { TLB_FP64 = 0, TLB_FP32 = 1, TLB_FP16 = 2, TLB_BF16 = 3 };
 
 enum { TLB_EDGE_PERIODIC = 0, TLB_EDGE_WETTING = 1, TLB_EDGE_NEUTRAL = 2, TLB_EDGE_LID = 3 };
 

@@ -16,12 +16,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtlbm.so")
 
-FP64, FP32 = 0, 1
+FP64, FP32, FP16, BF16 = 0, 1, 2, 3
 EDGE_PERIODIC, EDGE_WETTING, EDGE_NEUTRAL, EDGE_LID = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
 FIELDS = ("c1", "c2", "c3", "rho", "ux", "uy", "p", "mu1", "mu2", "mu3")
 F_ALL = (1 << 10) - 1
-PRECISIONS = {"fp64": FP64, "f64": FP64, "fp32": FP32, "f32": FP32}
+PRECISIONS = {"fp64": FP64, "f64": FP64, "fp32": FP32, "f32": FP32, "fp16": FP16, "f16": FP16, "bf16": BF16}
 
 _lib = None
 

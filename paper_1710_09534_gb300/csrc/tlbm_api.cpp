@@ -4,6 +4,7 @@
 // per-step launches on the caller's stream.
 #include "tlbm.h"
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -51,16 +52,15 @@ constexpr int kMaxDrops = 256;   // contact-line results kept per call
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 
-bool precision_ok(int precision) { return precision == TLB_FP64 || precision == TLB_FP32; }
+bool precision_ok(int precision) { return precision >= TLB_FP64 && precision <= TLB_BF16; }
 
-size_t elem_size(int precision) { return precision == TLB_FP64 ? 8 : 4; }
 
 tlb::Layout layout_for(int nx, int ny, int precision)
 {
     tlb::Layout L;
     L.pitch = (int)align_up(nx, 32);
     L.plane = (int64_t)L.pitch * ny;
-    const int64_t es = (int64_t)elem_size(precision);
+    const int64_t es = (int64_t)tlb::elem_for(precision);
     int64_t off = 0;
     auto take = [&](int64_t bytes) {
         const int64_t at = off;
@@ -70,7 +70,7 @@ tlb::Layout layout_for(int nx, int ny, int precision)
     const int nd = tlb::ndist_for(precision);
     L.fA = take(nd * L.plane * es);
     L.fB = take(nd * L.plane * es);
-    L.cu = take(4 * L.plane * es);
+    L.cu = take(4 * L.plane * (int64_t)tlb::cu_elem_for(precision));
     L.cls = take(L.plane);
     L.list = take((int64_t)nx * ny * 4);
     L.part = take((int64_t)kMassParts * 4 * 8);
@@ -468,11 +468,27 @@ int tlb_read_fields(tlb_lattice* L, uint32_t mask, double* host_out)
     if (rc) return rc;
     if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "no state yet");
     if (!host_out || (mask & ~(uint32_t)TLB_F_ALL) || !mask) return fail(TLB_EINVAL, "bad output or field mask");
+    // stage in the spare distribution buffer, as many FP64 planes per pass as
+    // it holds (8 or more: it has >= 70 bytes per node in every precision)
     const size_t N = (size_t)L->n();
+    const size_t spare = (size_t)(L->ops->ndist * L->lay.plane * L->ops->elem);
+    const int per_pass = (int)std::min<size_t>(10, spare / (N * 8));
     double* stage = (double*)L->bufB();
-    TLB_CUDA(L->ops->read(L->bufA(), L->dcls(), stage, mask, L->geo, L->prm, L->stream));
-    TLB_CUDA(cudaMemcpyAsync(host_out, stage, (size_t)popcount10(mask) * N * 8, cudaMemcpyDeviceToHost, L->stream));
-    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(L->ops->ndist * L->lay.plane * L->ops->elem), L->stream));
+    size_t done = 0;
+    for (int q = 0; q < 10;) {
+        uint32_t sub = 0;
+        int cnt = 0;
+        for (; q < 10 && cnt < per_pass; q++)
+            if (mask & (1u << q)) {
+                sub |= 1u << q;
+                cnt++;
+            }
+        if (!sub) continue;
+        TLB_CUDA(L->ops->read(L->bufA(), L->dcls(), stage, sub, L->geo, L->prm, L->stream));
+        TLB_CUDA(cudaMemcpyAsync(host_out + done * N, stage, (size_t)cnt * N * 8, cudaMemcpyDeviceToHost, L->stream));
+        done += (size_t)cnt;
+    }
+    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, spare, L->stream));
     TLB_CUDA(cudaStreamSynchronize(L->stream));
     return ok();
 }
@@ -522,37 +538,67 @@ int tlb_contact_angles(tlb_lattice* L, int component, double* host_out, int max_
     return ok();
 }
 
+// IEEE 754 binary16 and bfloat16 bit patterns to double (host side of the
+// 16-bit storage formats).
+static double half_bits(uint16_t h)
+{
+    const int e = (h >> 10) & 31, m = h & 1023;
+    double v;
+    if (e == 0) v = std::ldexp((double)m, -24);  // subnormal: m 2^-24
+    else if (e == 31) v = m ? std::nan("") : INFINITY;
+    else v = std::ldexp((double)(1024 + m), e - 25);  // (1 + m/1024) 2^(e-15)
+    return (h & 0x8000) ? -v : v;
+}
+static double bf16_bits(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 int tlb_read_state(tlb_lattice* L, double* host_out)
 {
     int rc = check_handle(L);
     if (rc) return rc;
     if (!host_out) return fail(TLB_EINVAL, "out is null");
-    const size_t es = L->ops->elem, PL = (size_t)L->lay.plane, nd = (size_t)L->ops->ndist;
-    std::vector<char> raw((nd + 4) * PL * es);
-    TLB_CUDA(cudaMemcpyAsync(raw.data(), L->bufA(), nd * PL * es, cudaMemcpyDeviceToHost, L->stream));
-    TLB_CUDA(cudaMemcpyAsync(raw.data() + nd * PL * es, L->cu(), 4 * PL * es, cudaMemcpyDeviceToHost, L->stream));
+    const size_t es = L->ops->elem, ces = L->ops->cu_elem, PL = (size_t)L->lay.plane, nd = (size_t)L->ops->ndist;
+    const size_t dbytes = nd * PL * es;
+    std::vector<char> raw(dbytes + 4 * PL * ces);
+    TLB_CUDA(cudaMemcpyAsync(raw.data(), L->bufA(), dbytes, cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaMemcpyAsync(raw.data() + dbytes, L->cu(), 4 * PL * ces, cudaMemcpyDeviceToHost, L->stream));
     TLB_CUDA(cudaStreamSynchronize(L->stream));
-    auto at = [&](size_t q, size_t i) {
-        const size_t src = q * PL + i;
-        if (es == 8) {
-            double v;
-            memcpy(&v, raw.data() + src * 8, 8);
-            return v;
-        }
+    auto f32 = [&](size_t byte) {
         float f;
-        memcpy(&f, raw.data() + src * 4, 4);
+        memcpy(&f, raw.data() + byte, 4);
         return (double)f;
     };
+    auto f64 = [&](size_t byte) {
+        double v;
+        memcpy(&v, raw.data() + byte, 8);
+        return v;
+    };
+    const double inv16 = std::ldexp(1.0, -tlb::kF16ScaleExp);
+    // population q (0..26) of pitched node i, rest populations as hi + lo
+    auto pop = [&](size_t q, size_t i) {
+        const bool rest = q == 0 || q == 9;
+        const size_t r = q == 9 ? 1 : 0;
+        if (es == 8) return f64((q * PL + i) * 8);
+        if (es == 4) return rest ? f32((q * PL + i) * 4) + f32(((27 + r) * PL + i) * 4) : f32((q * PL + i) * 4);
+        const size_t fr = 27 * PL * 2;  // FP32 region after the 16-bit planes
+        if (rest) return f32(fr + (r * PL + i) * 4) + f32(fr + ((2 + r) * PL + i) * 4);
+        uint16_t b;
+        memcpy(&b, raw.data() + (q * PL + i) * 2, 2);
+        return L->precision == TLB_FP16 ? half_bits(b) * inv16 : bf16_bits(b);
+    };
+    auto cuv = [&](size_t q, size_t i) { return ces == 8 ? f64(dbytes + (q * PL + i) * 8) : f32(dbytes + (q * PL + i) * 4); };
     const size_t N = (size_t)L->n();
     for (int q = 0; q < 31; q++) {
-        // raw plane of output plane q: 27 distributions, then the 4 c_i u planes
-        const size_t rq = q < 27 ? (size_t)q : nd + (size_t)(q - 27);
+        // output plane q: 27 distributions, then the 4 c_i u planes
         for (int y = 0; y < L->ny; y++)
             for (int x = 0; x < L->nx; x++) {
                 const size_t i = (size_t)y * L->lay.pitch + x;
-                double v = at(rq, i);
-                if (nd > 27 && (q == 0 || q == 9)) v += at(q == 0 ? 27 : 28, i);  // rest population hi + lo
-                host_out[q * N + (size_t)y * L->nx + x] = v;
+                host_out[q * N + (size_t)y * L->nx + x] = q < 27 ? pop((size_t)q, i) : cuv((size_t)(q - 27), i);
             }
     }
     return ok();
@@ -561,7 +607,7 @@ int tlb_read_state(tlb_lattice* L, double* host_out)
 int64_t tlb_state_bytes(tlb_lattice* L)
 {
     if (!L) return fail(TLB_EINVAL, "null lattice handle");
-    return (L->ops->ndist + 4) * L->lay.plane * (int64_t)L->ops->elem;
+    return L->lay.plane * ((int64_t)L->ops->ndist * (int64_t)L->ops->elem + 4 * (int64_t)L->ops->cu_elem);
 }
 
 int tlb_export_state(tlb_lattice* L, void* host_buf, int64_t bytes)
@@ -663,6 +709,7 @@ int lattice_view(tlb_lattice* L, LatticeView* v)
     v->cls = L->dcls();
     v->geo = L->geo;
     v->precision = L->precision;
+    v->ops = L->ops;
     v->device = L->device;
     v->stream = L->stream;
     return TLB_OK;

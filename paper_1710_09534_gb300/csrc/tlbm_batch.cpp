@@ -248,7 +248,7 @@ int tlb_batch_create(int precision, int max_lattices, int64_t max_tiles, int64_t
 {
     if (!out) return err(TLB_EINVAL, "out is null");
     *out = nullptr;
-    if (precision != TLB_FP64 && precision != TLB_FP32) return err(TLB_EINVAL, "unknown precision %d", precision);
+    if (precision < TLB_FP64 || precision > TLB_BF16) return err(TLB_EINVAL, "unknown precision %d", precision);
     if (max_lattices < 1 || max_tiles < 1 || max_wall_nodes < 0) return err(TLB_EINVAL, "bad batch capacity");
     if (!cuda_stream) return err(TLB_EINVAL, "a batch needs a non-default stream (it is graph-captured)");
     const BatchLayout lay = batch_layout(max_lattices, max_tiles, max_wall_nodes);

@@ -60,7 +60,7 @@ k_batch_interior(const LatDesc<R>* __restrict__ descs, const TileItem* __restric
             reinterpret_cast<R*>(&Ps)[threadIdx.x] = reinterpret_cast<const R*>(&d->P)[threadIdx.x];
         __syncthreads();
         const Geo g = d->g;
-        interior_tile<S, R, BLOCK, PREFETCH, MRT>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1], (S*)d->cu, d->cls,
+        interior_tile<S, R, BLOCK, PREFETCH, MRT>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1], (CuT<S>*)d->cu, d->cls,
                                              g, Ps, ti.bx, ti.by, d->rows, sh);
         __syncthreads();  // rings, parameters and item_s are reused by the next tile
     }
@@ -75,7 +75,7 @@ k_batch_wall(const LatDesc<R>* __restrict__ descs, const WallItem* __restrict__ 
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const WallItem wi = items[i];
         const LatDesc<R>* d = descs + wi.lat;
-        wall_node<S, R, MRT>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1], (S*)d->cu, d->cls, d->g, d->P,
+        wall_node<S, R, MRT>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1], (CuT<S>*)d->cu, d->cls, d->g, d->P,
                         wi.packed);
     }
 }

@@ -1,0 +1,6 @@
+// BF16 storage (shifted), FP32 arithmetic, BGK collision.
+#include "tlbm_ops_impl.cuh"
+
+namespace tlb {
+const Ops& ops_bf16() { return OpsImpl<__nv_bfloat16, float, kBlock32, kRows32, kPrefetch32, kMinB32, false>::table(); }
+}  // namespace tlb

@@ -25,6 +25,9 @@ __host__ __device__ constexpr int comp(int k) { return (k == 1 || k == 3) ? 0 : 
 __host__ __device__ constexpr int sgn(int k) { return (k == 1 || k == 2 || k == 5 || k == 8) ? 1 : -1; }
 __host__ __device__ constexpr int wclass(int k) { return k <= 4 ? 0 : 1; }  // 0 axis, 1 diagonal
 
+// FP16 storage holds 2^kF16ScaleExp times each 16-bit population.
+constexpr int kF16ScaleExp = 12;
+
 // Site kinds (same semantics as the FP64 oracle's classification).
 enum : int { ST_FLUID = 0, ST_LID = 1, ST_WET = 2, ST_NEUTRAL = 3, ST_VOID = 4 };
 enum : int { EDGE_PERIODIC = 0, EDGE_WETTING = 1, EDGE_NEUTRAL = 2, EDGE_LID = 3 };

@@ -54,10 +54,11 @@ namespace tlb {
 
 // Read-only view of a lattice's current state inside the caller's workspace.
 struct LatticeView {
-    const void* dist;      // current distribution buffer (27 planes)
+    const void* dist;      // current distribution buffer
     const uint8_t* cls;    // node classes
     Geo geo;
     int precision;
+    const Ops* ops;        // launch table of the lattice's precision
     int device;
     cudaStream_t stream;
 };

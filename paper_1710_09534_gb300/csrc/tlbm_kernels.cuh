@@ -13,6 +13,8 @@
 //   k_init, k_read_fields, k_mass_partials/k_mass_final
 #pragma once
 #include <type_traits>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include "tlbm_device.cuh"
 
 namespace tlb {
@@ -37,15 +39,122 @@ __device__ __forceinline__ R sum9(const R* v)
     return v[0] + (((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8])));
 }
 
-// FP32 storage keeps the two rest populations f^1_0, f^2_0 as unevaluated
-// float pairs hi + lo (planes 0/9 and 27/28), so that the per-node update
-// can conserve sum_k f^i_k (Eq. 1a conserves c_i) to ~2^-48 instead of to one
-// FP32 rounding per node and step.  FP64 storage has 27 planes.
+// Storage formats of the distributions (template parameter S):
+//   double  27 FP64 planes (q = 0..8 f^1_k, 9..17 f^2_k, 18..26 g_k).
+//   float   27 FP32 planes, plus the rest populations f^1_0, f^2_0 kept as
+//           unevaluated float pairs hi + lo (hi in planes 0/9, lo in planes
+//           27/28), so that the per-node update can conserve sum_k f^i_k
+//           (Eq. 1a conserves c_i) to ~2^-48 instead of to one FP32 rounding
+//           per node and step.
+//   __half, __nv_bfloat16
+//           the 25 other populations as 16-bit values after subtracting their
+//           equilibrium at rest (u = 0, mu = 0, p = 0), which is zero for every
+//           one of them in this model (Eq. 2a: f^{i,eq}_k, k != 0, is
+//           proportional to mu_i and u; Eq. 2b: g^eq is pressure-based), and
+//           (FP16) scaled by 2^kF16ScaleExp so that small populations stay normal
+//           numbers; the rest populations, whose equilibrium at rest is c_i
+//           itself, stay FP32 pairs.  Layout: 27 16-bit planes (0 and 9
+//           unused) then 4 FP32 planes: f^1_0 hi, f^2_0 hi, f^1_0 lo, f^2_0 lo.
+// The c_i u planes of Eq. 19 are FP64 with FP64 storage and FP32 otherwise.
 template <typename S>
 struct Store {
-    static constexpr bool kLo = std::is_same<S, float>::value;
-    static constexpr int kPlanes = kLo ? 29 : 27;
+    static constexpr bool k16 = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
+    static constexpr bool kLo = !std::is_same<S, double>::value;
+    static constexpr int kPlanes = std::is_same<S, double>::value ? 27 : (k16 ? 35 : 29);  // in units of S
+    static constexpr int kScaleExp = std::is_same<S, __half>::value ? kF16ScaleExp : 0;
+    using Cu = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+    using R = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
 };
+template <typename S>
+using CuT = typename Store<S>::Cu;
+
+__device__ __forceinline__ float dec16(__half, unsigned short b) { return __half2float(__ushort_as_half(b)); }
+__device__ __forceinline__ float dec16(__nv_bfloat16, unsigned short b) { return __uint_as_float((unsigned)b << 16); }
+__device__ __forceinline__ unsigned short enc16(__half, float v) { return __half_as_ushort(__float2half_rn(v)); }
+__device__ __forceinline__ unsigned short enc16(__nv_bfloat16, float v)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// FP32 region of a 16-bit buffer (after the 27 16-bit planes)
+template <typename S>
+__device__ __forceinline__ const float* rest_region(const S* f, long long PL)
+{
+    return reinterpret_cast<const float*>(f + 27 * PL);
+}
+template <typename S>
+__device__ __forceinline__ float* rest_region(S* f, long long PL)
+{
+    return reinterpret_cast<float*>(f + 27 * PL);
+}
+
+// Population q (0..26) of node offset o, as the arithmetic type R (for the
+// rest populations of the paired formats: the hi part).
+template <typename R, typename S>
+__device__ __forceinline__ R ld_pop(const S* __restrict__ f, int q, long long PL, long long o)
+{
+    if constexpr (Store<S>::k16) {
+        if (q == 0 || q == 9) return R(__ldg(rest_region(f, PL) + (q == 9 ? PL : 0) + o));
+        constexpr float inv = 1.0f / float(1 << Store<S>::kScaleExp);
+        return R(dec16(S{}, __ldg(reinterpret_cast<const unsigned short*>(f) + q * PL + o)) * inv);
+    } else {
+        return R(__ldg(f + q * PL + o));
+    }
+}
+// lo part of rest population i (0: f^1_0, 1: f^2_0); zero for FP64
+template <typename R, typename S>
+__device__ __forceinline__ R ld_lo(const S* __restrict__ f, int i, long long PL, long long o)
+{
+    if constexpr (Store<S>::k16) return R(__ldg(rest_region(f, PL) + (2 + i) * PL + o));
+    else if constexpr (Store<S>::kLo) return R(__ldg(f + (27 + i) * PL + o));
+    else return R(0);
+}
+// The value population q takes once stored (16-bit formats round; others keep it)
+template <typename S, typename R>
+__device__ __forceinline__ R as_stored(int q, R v)
+{
+    if constexpr (Store<S>::k16) {
+        if (q == 0 || q == 9) return v;
+        constexpr float sc = float(1 << Store<S>::kScaleExp), inv = 1.0f / sc;
+        return R(dec16(S{}, enc16(S{}, float(v) * sc)) * inv);
+    } else {
+        return v;
+    }
+}
+template <typename S, typename R>
+__device__ __forceinline__ void st_pop(S* __restrict__ f, int q, long long PL, long long o, R v)
+{
+    if constexpr (Store<S>::k16) {
+        if (q == 0 || q == 9) {
+            rest_region(f, PL)[(q == 9 ? PL : 0) + o] = float(v);
+        } else {
+            constexpr float sc = float(1 << Store<S>::kScaleExp);
+            reinterpret_cast<unsigned short*>(f)[q * PL + o] = enc16(S{}, float(v) * sc);
+        }
+    } else {
+        f[q * PL + o] = S(v);
+    }
+}
+template <typename S, typename R>
+__device__ __forceinline__ void st_lo(S* __restrict__ f, int i, long long PL, long long o, R v)
+{
+    if constexpr (Store<S>::k16) rest_region(f, PL)[(2 + i) * PL + o] = float(v);
+    else if constexpr (Store<S>::kLo) f[(27 + i) * PL + o] = S(v);
+}
+// c_i = sum_k f^i_k of node o for i = 1, 2 (rest population hi + lo)
+template <typename R, typename S>
+__device__ __forceinline__ void order_params(const S* __restrict__ f, long long PL, long long o, R& c1, R& c2)
+{
+    R v[18];
+#pragma unroll
+    for (int k = 0; k < 18; k++) v[k] = ld_pop<R>(f, k, PL, o);
+    if constexpr (Store<S>::kLo) {
+        v[0] += ld_lo<R>(f, 0, PL, o);
+        v[9] += ld_lo<R>(f, 1, PL, o);
+    }
+    c1 = sum9(v);
+    c2 = sum9(v + 9);
+}
 
 // Error-free transformation of a sum (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
@@ -95,6 +204,8 @@ __device__ __forceinline__ void collide_all(const Collider<R>& col, const R gv[9
         R f1k, f2k, o1, o2, og;
         load(kc, f1k, f2k);
         col.template post<K>(f1k, f2k, gv[K], o1, o2, og);
+        o1 = as_stored<S>(K, o1);
+        o2 = as_stored<S>(9 + K, o2);
         if constexpr (ff) {
             in1.add(f1k);
             in2.add(f2k);
@@ -146,6 +257,11 @@ __device__ __forceinline__ void collide_all(const MrtNode<R>& col, const R gv[9]
         f2[0] += l2;
     }
     col.apply(f1, f2, gv, o1, o2, og);
+#pragma unroll
+    for (int k = 1; k < 9; k++) {
+        o1[k] = as_stored<S>(k, o1[k]);
+        o2[k] = as_stored<S>(9 + k, o2[k]);
+    }
     if constexpr (ff) {
         FF in1, in2, out1, out2;
 #pragma unroll
@@ -210,7 +326,7 @@ struct TileRings {
 // One tile: strip bx (columns bx*(BLOCK-4) .. +BLOCK-5), segment by (rows
 // by*rows .. +rows-1, marching up for even by and down for odd by).
 template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT>
-__device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+__device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
                                               const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
                                               int bx, int by, int rows, TileRings<R, BLOCK>& sh)
 {
@@ -250,7 +366,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         R gv[9], cp[4];
         if (PREFETCH && upd) {
 #pragma unroll
-            for (int k = 0; k < 9; k++) gv[k] = R(ldg(fA + (18 + k) * PL + ou));
+            for (int k = 0; k < 9; k++) gv[k] = ld_pop<R>(fA, 18 + k, PL, ou);
 #pragma unroll
             for (int q = 0; q < 4; q++) cp[q] = R(cu[q * PL + ou]);
         }
@@ -263,18 +379,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                 else in = false;
             }
             R a = R(0), b = R(0);
-            if (in) {
-                const S* q = fA + (long long)yw * g.pitch + xw;
-                R v[18];
-#pragma unroll
-                for (int k = 0; k < 18; k++) v[k] = R(ldg(q + k * PL));
-                if constexpr (Store<S>::kLo) {
-                    v[0] += R(ldg(q + 27 * PL));
-                    v[9] += R(ldg(q + 28 * PL));
-                }
-                a = sum9(v);
-                b = sum9(v + 9);
-            }
+            if (in) order_params<R>(fA, PL, (long long)yw * g.pitch + xw, a, b);
             const int sl = (yc + 10) % 5;
             sc1[sl][t] = a;
             sc2[sl][t] = b;
@@ -322,7 +427,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         }
         if (!PREFETCH) {
 #pragma unroll
-            for (int k = 0; k < 9; k++) gv[k] = R(ldg(fA + (18 + k) * PL + ou));
+            for (int k = 0; k < 9; k++) gv[k] = ld_pop<R>(fA, 18 + k, PL, ou);
 #pragma unroll
             for (int q = 0; q < 4; q++) cp[q] = R(cu[q * PL + ou]);
         }
@@ -330,39 +435,39 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         hydro_from_g(P, m, gv, h);
         // Eq. 19: d/dt (c_i u) against the stored product of the previous step
         const R c1ux = m.c1 * h.ux, c1uy = m.c1 * h.uy, c2ux = m.c2 * h.ux, c2uy = m.c2 * h.uy;
-        cu[0 * PL + ou] = S(c1ux);
-        cu[1 * PL + ou] = S(c1uy);
-        cu[2 * PL + ou] = S(c2ux);
-        cu[3 * PL + ou] = S(c2uy);
+        cu[0 * PL + ou] = CuT<S>(c1ux);
+        cu[1 * PL + ou] = CuT<S>(c1uy);
+        cu[2 * PL + ou] = CuT<S>(c2ux);
+        cu[3 * PL + ou] = CuT<S>(c2uy);
         CollideOf<MRT, R> col;
         col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
         collide_all<S, R>(col, gv,
             [&](auto kc, R& f1k, R& f2k) {
                 constexpr int K = decltype(kc)::value;
-                f1k = R(ldg(fA + K * PL + ou));
-                f2k = R(ldg(fA + (9 + K) * PL + ou));
+                f1k = ld_pop<R>(fA, K, PL, ou);
+                f2k = ld_pop<R>(fA, 9 + K, PL, ou);
             },
             [&](R& l1, R& l2) {
-                l1 = R(ldg(fA + 27 * PL + ou));
-                l2 = R(ldg(fA + 28 * PL + ou));
+                l1 = ld_lo<R>(fA, 0, PL, ou);
+                l2 = ld_lo<R>(fA, 1, PL, ou);
             },
             [&](auto kc, R o1, R o2, R og) {
                 constexpr int K = decltype(kc)::value;
                 const long long d = (K == 0) ? ou : wrap_off(g, xs + ex(K), yu + ey(K));
-                fB[K * PL + d] = S(o1);
-                fB[(9 + K) * PL + d] = S(o2);
-                fB[(18 + K) * PL + d] = S(og);
+                st_pop(fB, K, PL, d, o1);
+                st_pop(fB, 9 + K, PL, d, o2);
+                st_pop(fB, 18 + K, PL, d, og);
             },
             [&](R l1, R l2) {
-                fB[27 * PL + ou] = S(l1);
-                fB[28 * PL + ou] = S(l2);
+                st_lo(fB, 0, PL, ou, l1);
+                st_lo(fB, 1, PL, ou, l2);
             });
     }
 }
 
 template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT>
 __global__ void __launch_bounds__(BLOCK, MINB)
-k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
                 const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
 {
     __shared__ TileRings<R, BLOCK> sh;
@@ -475,15 +580,7 @@ struct DistFetch {
     long long PL;
     __device__ __forceinline__ void operator()(long long off, R& a, R& b) const
     {
-        R v[18];
-#pragma unroll
-        for (int k = 0; k < 18; k++) v[k] = R(ldg(f + k * PL + off));
-        if constexpr (Store<S>::kLo) {
-            v[0] += R(ldg(f + 27 * PL + off));
-            v[9] += R(ldg(f + 28 * PL + off));
-        }
-        a = sum9(v);
-        b = sum9(v + 9);
+        order_params<R>(f, PL, off, a, b);
     }
 };
 
@@ -509,22 +606,22 @@ __device__ __forceinline__ void push_wall(const Geo& g, const uint8_t* __restric
 {
     const long long PL = g.plane;
     if (K == 0) {
-        fB[o] = S(o1);
-        fB[9 * PL + o] = S(o2);
-        fB[18 * PL + o] = S(og);
+        st_pop(fB, 0, PL, o, o1);
+        st_pop(fB, 9, PL, o, o2);
+        st_pop(fB, 18, PL, o, og);
         return;
     }
     long long d = 0;
     const int s = site_of(g, cls, x + ex(K), y + ey(K), d);
     if (fluidlike(s)) {
-        fB[K * PL + d] = S(o1);
-        fB[(9 + K) * PL + d] = S(o2);
-        fB[(18 + K) * PL + d] = S(og);
+        st_pop(fB, K, PL, d, o1);
+        st_pop(fB, 9 + K, PL, d, o2);
+        st_pop(fB, 18 + K, PL, d, og);
     } else if (s == ST_WET || s == ST_NEUTRAL) {
         constexpr int KB = opp(K);
-        fB[KB * PL + o] = S(o1);
-        fB[(9 + KB) * PL + o] = S(o2);
-        fB[(18 + KB) * PL + o] = S(og);
+        st_pop(fB, KB, PL, o, o1);
+        st_pop(fB, 9 + KB, PL, o, o2);
+        st_pop(fB, 18 + KB, PL, o, og);
     }
 }
 
@@ -532,7 +629,7 @@ __device__ __forceinline__ void push_wall(const Geo& g, const uint8_t* __restric
 // K2: near-wall and lid nodes from the compacted list.
 // ---------------------------------------------------------------------------
 template <typename S, typename R, bool MRT>
-__device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+__device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
                                           const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
                                           uint32_t packed)
 {
@@ -547,35 +644,35 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
         window_macros(g, cls, P, x, y, fetch, m);
         R gv[9];
 #pragma unroll
-        for (int k = 0; k < 9; k++) gv[k] = R(ldg(fA + (18 + k) * PL + o));
+        for (int k = 0; k < 9; k++) gv[k] = ld_pop<R>(fA, 18 + k, PL, o);
         Hydro<R> h;
         hydro_from_g(P, m, gv, h);
         const R c1ux = m.c1 * h.ux, c1uy = m.c1 * h.uy, c2ux = m.c2 * h.ux, c2uy = m.c2 * h.uy;
         const R d1x = c1ux - R(cu[0 * PL + o]), d1y = c1uy - R(cu[1 * PL + o]);
         const R d2x = c2ux - R(cu[2 * PL + o]), d2y = c2uy - R(cu[3 * PL + o]);
-        cu[0 * PL + o] = S(c1ux);
-        cu[1 * PL + o] = S(c1uy);
-        cu[2 * PL + o] = S(c2ux);
-        cu[3 * PL + o] = S(c2uy);
+        cu[0 * PL + o] = CuT<S>(c1ux);
+        cu[1 * PL + o] = CuT<S>(c1uy);
+        cu[2 * PL + o] = CuT<S>(c2ux);
+        cu[3 * PL + o] = CuT<S>(c2uy);
         CollideOf<MRT, R> col;
         col.build(P, m, h, d1x, d1y, d2x, d2y);
         collide_all<S, R>(col, gv,
             [&](auto kc, R& f1k, R& f2k) {
                 constexpr int K = decltype(kc)::value;
-                f1k = R(ldg(fA + K * PL + o));
-                f2k = R(ldg(fA + (9 + K) * PL + o));
+                f1k = ld_pop<R>(fA, K, PL, o);
+                f2k = ld_pop<R>(fA, 9 + K, PL, o);
             },
             [&](R& l1, R& l2) {
-                l1 = R(ldg(fA + 27 * PL + o));
-                l2 = R(ldg(fA + 28 * PL + o));
+                l1 = ld_lo<R>(fA, 0, PL, o);
+                l2 = ld_lo<R>(fA, 1, PL, o);
             },
             [&](auto kc, R o1, R o2, R og) {
                 constexpr int K = decltype(kc)::value;
                 push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
             },
             [&](R l1, R l2) {
-                fB[27 * PL + o] = S(l1);
-                fB[28 * PL + o] = S(l2);
+                st_lo(fB, 0, PL, o, l1);
+                st_lo(fB, 1, PL, o, l2);
             });
     } else if (kind == ST_LID) {
         // x_f is the node below; x_u takes its macros and gradients, u = (U0, 0)
@@ -584,7 +681,7 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
         window_macros(g, cls, P, x, y - 1, fetch, m);
         R gf[9];
 #pragma unroll
-        for (int k = 0; k < 9; k++) gf[k] = R(ldg(fA + (18 + k) * PL + of));
+        for (int k = 0; k < 9; k++) gf[k] = ld_pop<R>(fA, 18 + k, PL, of);
         Hydro<R> hf;
         hydro_from_g(P, m, gf, hf);
         Hydro<R> h = hf;
@@ -594,10 +691,10 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
         const R c1ux = m.c1 * h.ux, c2ux = m.c2 * h.ux;
         const R d1x = c1ux - R(cu[0 * PL + o]), d1y = R(0) - R(cu[1 * PL + o]);
         const R d2x = c2ux - R(cu[2 * PL + o]), d2y = R(0) - R(cu[3 * PL + o]);
-        cu[0 * PL + o] = S(c1ux);
-        cu[1 * PL + o] = S(0);
-        cu[2 * PL + o] = S(c2ux);
-        cu[3 * PL + o] = S(0);
+        cu[0 * PL + o] = CuT<S>(c1ux);
+        cu[1 * PL + o] = CuT<S>(0);
+        cu[2 * PL + o] = CuT<S>(c2ux);
+        cu[3 * PL + o] = CuT<S>(0);
         CollideOf<MRT, R> col;
         col.build(P, m, h, d1x, d1y, d2x, d2y);
         // Eq. 51: f(x_u) = f^eq(x_u) + [f(x_f) - f^eq(x_f)], for f^1, f^2 and g
@@ -607,11 +704,11 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
             R e1u, e2u, egu, e1f, e2f, egf;
             equilibria(k, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, hf.p, h.ux, h.uy, e1u, e2u, egu);
             equilibria(k, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, hf.p, hf.ux, hf.uy, e1f, e2f, egf);
-            R ff1 = R(ldg(fA + k * PL + of)), ff2 = R(ldg(fA + (9 + k) * PL + of));
+            R ff1 = ld_pop<R>(fA, k, PL, of), ff2 = ld_pop<R>(fA, 9 + k, PL, of);
             if constexpr (Store<S>::kLo) {
                 if (k == 0) {
-                    ff1 += R(ldg(fA + 27 * PL + of));
-                    ff2 += R(ldg(fA + 28 * PL + of));
+                    ff1 += ld_lo<R>(fA, 0, PL, of);
+                    ff2 += ld_lo<R>(fA, 1, PL, of);
                 }
             }
             f1u[k] = e1u + (ff1 - e1f);
@@ -635,22 +732,22 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
                 if constexpr (ey(K) == -1) {
                     long long dummy = 0;
                     if (site_of(g, cls, x - ex(K), y + 1, dummy) == ST_VOID) {
-                        fB[K * PL + o] = S(0);
-                        fB[(9 + K) * PL + o] = S(0);
-                        fB[(18 + K) * PL + o] = S(0);
+                        st_pop(fB, K, PL, o, R(0));
+                        st_pop(fB, 9 + K, PL, o, R(0));
+                        st_pop(fB, 18 + K, PL, o, R(0));
                     }
                 }
             },
             [&](R l1, R l2) {
-                fB[27 * PL + o] = S(l1);
-                fB[28 * PL + o] = S(l2);
+                st_lo(fB, 0, PL, o, l1);
+                st_lo(fB, 1, PL, o, l2);
             });
     }
 }
 
 template <typename S, typename R, bool MRT>
 __global__ void __launch_bounds__(128)
-k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
+k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
             const uint8_t* __restrict__ cls, const uint32_t* __restrict__ list, int nlist, Geo g, Prm<R> P)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -663,7 +760,7 @@ k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, S* __restrict__ cu,
 // Inputs are dense [ny][nx] FP64 device arrays.
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
-__global__ void k_init(S* __restrict__ fA, S* __restrict__ cu, const uint8_t* __restrict__ cls,
+__global__ void k_init(S* __restrict__ fA, CuT<S>* __restrict__ cu, const uint8_t* __restrict__ cls,
                        const double* __restrict__ c1, const double* __restrict__ c2,
                        const double* __restrict__ ux, const double* __restrict__ uy,
                        const double* __restrict__ p, Geo g, Prm<R> P)
@@ -675,13 +772,11 @@ __global__ void k_init(S* __restrict__ fA, S* __restrict__ cu, const uint8_t* __
     const long long o = (long long)y * g.pitch + x;
     const long long n = (long long)y * g.nx + x;
     const int kind = cls[o] & CLS_KIND_MASK;
-    if constexpr (Store<S>::kLo) {
-        fA[27 * PL + o] = S(0);
-        fA[28 * PL + o] = S(0);
-    }
+    st_lo(fA, 0, PL, o, R(0));
+    st_lo(fA, 1, PL, o, R(0));
     if (!fluidlike(kind)) {
-        for (int q = 0; q < 27; q++) fA[q * PL + o] = S(0);
-        for (int q = 0; q < 4; q++) cu[q * PL + o] = S(0);
+        for (int q = 0; q < 27; q++) st_pop(fA, q, PL, o, R(0));
+        for (int q = 0; q < 4; q++) cu[q * PL + o] = CuT<S>(0);
         return;
     }
     FieldFetch<R> fetch{c1, c2, g.nx, g.pitch};
@@ -692,14 +787,14 @@ __global__ void k_init(S* __restrict__ fA, S* __restrict__ cu, const uint8_t* __
     for (int k = 0; k < 9; k++) {
         R e1, e2, eg;
         equilibria(k, P, m.c1, m.c2, m.mu1, m.mu2, m.rho, pp, u, v, e1, e2, eg);
-        fA[k * PL + o] = S(e1);
-        fA[(9 + k) * PL + o] = S(e2);
-        fA[(18 + k) * PL + o] = S(eg);
+        st_pop(fA, k, PL, o, e1);
+        st_pop(fA, 9 + k, PL, o, e2);
+        st_pop(fA, 18 + k, PL, o, eg);
     }
-    cu[0 * PL + o] = S(m.c1 * u);
-    cu[1 * PL + o] = S(m.c1 * v);
-    cu[2 * PL + o] = S(m.c2 * u);
-    cu[3 * PL + o] = S(m.c2 * v);
+    cu[0 * PL + o] = CuT<S>(m.c1 * u);
+    cu[1 * PL + o] = CuT<S>(m.c1 * v);
+    cu[2 * PL + o] = CuT<S>(m.c2 * u);
+    cu[3 * PL + o] = CuT<S>(m.c2 * v);
 }
 
 // ---------------------------------------------------------------------------
@@ -725,7 +820,7 @@ __global__ void k_read_fields(const S* __restrict__ fA, const uint8_t* __restric
         Macro<R> m;
         window_macros(g, cls, P, x, kind == ST_LID ? y - 1 : y, fetch, m);
         R gv[9];
-        for (int k = 0; k < 9; k++) gv[k] = R(fA[(18 + k) * PL + of]);
+        for (int k = 0; k < 9; k++) gv[k] = ld_pop<R>(fA, 18 + k, PL, of);
         Hydro<R> h;
         hydro_from_g(P, m, gv, h);
         if (kind == ST_LID) {
@@ -774,12 +869,10 @@ k_mass_partials(const S* __restrict__ fA, const uint8_t* __restrict__ cls, doubl
         if (!fluidlike(kind)) continue;
         if (kind == ST_LID) o -= g.pitch;
         double v[18], gs = 0;
-        for (int k = 0; k < 18; k++) v[k] = (double)fA[k * PL + o];
-        if constexpr (Store<S>::kLo) {
-            v[0] += (double)fA[27 * PL + o];
-            v[9] += (double)fA[28 * PL + o];
-        }
-        for (int k = 0; k < 9; k++) gs += (double)fA[(18 + k) * PL + o];
+        for (int k = 0; k < 18; k++) v[k] = ld_pop<double>(fA, k, PL, o);
+        v[0] += ld_lo<double>(fA, 0, PL, o);
+        v[9] += ld_lo<double>(fA, 1, PL, o);
+        for (int k = 0; k < 9; k++) gs += ld_pop<double>(fA, 18 + k, PL, o);
         const double c1 = sum9(v), c2 = sum9(v + 9);
         s1 += c1;
         s2 += c2;
@@ -840,8 +933,8 @@ __global__ void k_contact_columns(const S* __restrict__ fA, const uint8_t* __res
         if (!fluidlike(kind)) return 0.0;
         const long long src = kind == ST_LID ? o - g.pitch : o;  // the lid row carries the row below
         double v[9];
-        for (int k = 0; k < 9; k++) v[k] = (double)fA[(base + k) * PL + src];
-        if constexpr (Store<S>::kLo) v[0] += (double)fA[(comp == 1 ? 27 : 28) * PL + src];
+        for (int k = 0; k < 9; k++) v[k] = ld_pop<double>(fA, base + k, PL, src);
+        v[0] += ld_lo<double>(fA, comp == 1 ? 0 : 1, PL, src);
         return sum9(v);
     };
     const double c0 = cval(0);

@@ -12,7 +12,7 @@
 
 #include "tlbm.h"
 #include "tlbm_internal.h"
-#include "tlbm_kernels.cuh"
+#include "tlbm_ops.h"
 
 namespace {
 
@@ -69,12 +69,8 @@ extern "C" int tlb_diagnostics_noalloc(tlb_lattice* lat, double* dev_out)
     double* part = nullptr;
     if ((rc = scratch_address(v.device, &part))) return rc;
     const int nparts = (int)((n + kNodesPerPart - 1) / kNodesPerPart);
-    if (v.precision == TLB_FP64)
-        tlb::k_mass_partials<double, double><<<nparts, 256, 0, v.stream>>>((const double*)v.dist, v.cls, part, v.geo);
-    else
-        tlb::k_mass_partials<float, float><<<nparts, 256, 0, v.stream>>>((const float*)v.dist, v.cls, part, v.geo);
-    tlb::k_mass_final<<<1, 256, 0, v.stream>>>(part, nparts, dev_out);
-    const cudaError_t e = cudaGetLastError();
+    // the lattice's own reduction kernels (partials, then the fixed-order final sum)
+    const cudaError_t e = v.ops->mass(v.dist, v.cls, part, nparts, dev_out, v.geo, v.stream);
     if (e != cudaSuccess) {
         char msg[256];
         snprintf(msg, sizeof msg, "launch failed: %s", cudaGetErrorString(e));

@@ -8,8 +8,9 @@
 namespace tlb {
 
 struct Ops {
-    size_t elem;  // bytes per stored scalar
-    int ndist;    // planes per distribution buffer (27, or 29 with the FP32 rest lo parts)
+    size_t elem;     // bytes per stored distribution scalar
+    int ndist;       // planes of `elem` bytes per distribution buffer
+    size_t cu_elem;  // bytes per scalar of the c_i u planes
     // one time step A -> B = interior tiles (fused kernel) + near-wall list
     cudaError_t (*interior)(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
                             const Prm<double>& P, cudaStream_t s);
@@ -38,19 +39,31 @@ struct Ops {
                         const Geo& g, cudaStream_t s);
 };
 
-// planes per distribution buffer for a storage precision
-inline int ndist_for(int precision) { return precision == 0 ? 27 : 29; }
+// Storage precisions (the TLB_FP64 .. TLB_BF16 values of the C ABI):
+// bytes per distribution scalar, planes of that size per buffer, bytes per
+// c_i u scalar.
+inline size_t elem_for(int precision) { return precision == 0 ? 8 : (precision == 1 ? 4 : 2); }
+inline int ndist_for(int precision) { return precision == 0 ? 27 : (precision == 1 ? 29 : 35); }
+inline size_t cu_elem_for(int precision) { return precision == 0 ? 8 : 4; }
 
 const Ops& ops_f64();
 const Ops& ops_f32();
+const Ops& ops_f16();
+const Ops& ops_bf16();
 const Ops& ops_f64_mrt();
 const Ops& ops_f32_mrt();
+const Ops& ops_f16_mrt();
+const Ops& ops_bf16_mrt();
 
-// launch table of a storage precision (0 FP64, 1 FP32) and collision model
+// launch table of a storage precision and collision model
 inline const Ops& ops_for(int precision, bool mrt)
 {
-    if (precision == 0) return mrt ? ops_f64_mrt() : ops_f64();
-    return mrt ? ops_f32_mrt() : ops_f32();
+    switch (precision) {
+    case 0: return mrt ? ops_f64_mrt() : ops_f64();
+    case 1: return mrt ? ops_f32_mrt() : ops_f32();
+    case 2: return mrt ? ops_f16_mrt() : ops_f16();
+    default: return mrt ? ops_bf16_mrt() : ops_bf16();
+    }
 }
 
 // Fused interior kernel: threads per block (one column each, 4 of them halo)

@@ -58,7 +58,7 @@ struct OpsImpl {
         const Prm<R> P = cast_prm<R>(Pd);
         constexpr int TX = BLOCK - 4;
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + ROWS - 1) / ROWS);
-        k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT><<<grid, BLOCK, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, g, P);
+        k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT><<<grid, BLOCK, 0, s>>>((const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P);
         return cudaGetLastError();
     }
     static cudaError_t wall(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
@@ -66,7 +66,7 @@ struct OpsImpl {
     {
         const Prm<R> P = cast_prm<R>(Pd);
         if (nlist > 0)
-            k_step_wall<S, R, MRT><<<(nlist + 127) / 128, 128, 0, s>>>((const S*)fA, (S*)fB, (S*)cu, cls, list,
+            k_step_wall<S, R, MRT><<<(nlist + 127) / 128, 128, 0, s>>>((const S*)fA, (S*)fB, (CuT<S>*)cu, cls, list,
                                                                    nlist, g, P);
         return cudaGetLastError();
     }
@@ -76,7 +76,7 @@ struct OpsImpl {
     {
         const Prm<R> P = cast_prm<R>(Pd);
         dim3 grid((g.nx + 127) / 128, g.ny);
-        k_init<S, R><<<grid, 128, 0, s>>>((S*)fA, (S*)cu, cls, c1, c2, ux, uy, p, g, P);
+        k_init<S, R><<<grid, 128, 0, s>>>((S*)fA, (CuT<S>*)cu, cls, c1, c2, ux, uy, p, g, P);
         return cudaGetLastError();
     }
     static cudaError_t read(const void* fA, const uint8_t* cls, double* out, uint32_t mask, const Geo& g,
@@ -102,7 +102,7 @@ struct OpsImpl {
         return cudaGetLastError();
     }
     // the two block shapes the batch tuner chooses between
-    static constexpr int kMinB64 = std::is_same<S, float>::value ? 8 : 6;
+    static constexpr int kMinB64 = std::is_same<R, float>::value ? 8 : 6;
     static cudaError_t batch_step(const void* descs, const void* tiles, const void* walls, void* ctr, int parity,
                                   int variant, int grid_interior, int grid_wall, cudaStream_t s)
     {
@@ -141,7 +141,7 @@ struct OpsImpl {
     }
     static const Ops& table()
     {
-        static const Ops t{sizeof(S), Store<S>::kPlanes, &interior, &wall, &init, &read, &contact, &batch_step,
+        static const Ops t{sizeof(S), Store<S>::kPlanes, sizeof(CuT<S>), &interior, &wall, &init, &read, &contact, &batch_step,
                           &batch_blocks_per_sm, sizeof(LatDesc<R>), &fill_desc, &mass};
         return t;
     }

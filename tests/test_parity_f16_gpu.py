@@ -1,0 +1,152 @@
+"""16-bit storage (FP16 scaled by 2^12, and BF16) with FP32 arithmetic,
+against the FP64 oracle.
+
+Every population except the two rest populations is stored in 16 bits (its
+equilibrium at rest is zero in this model, so the shift subtracts nothing);
+the rest populations stay FP32 pairs and absorb the 16-bit rounding of the
+moving ones, so each component's mass is conserved as with FP32 storage.
+Bars: mass of each component conserved to 1e-6 relative over 20000 steps,
+equilibrium contact angles within 0.5 deg of the oracle's, and field errors
+bounded at about ten times what was measured on GB300 (FP16: order
+parameters ~2e-5 absolute, velocity ~3e-3 and pressure ~6e-3 of their scale;
+BF16, with 8 significand bits, about ten times more).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import OracleLattice
+
+pytestmark = pytest.mark.gpu
+
+# field: (kind, bound) -- "abs" absolute, "rel" relative to max|oracle|
+BOUNDS = {
+    "fp16": dict(c1=("abs", 2e-4), c2=("abs", 2e-4), c3=("abs", 2e-4), rho=("abs", 4e-4),
+                 ux=("rel", 3e-2), uy=("rel", 3e-2), p=("rel", 6e-2), mu1=("rel", 6e-3), mu2=("rel", 6e-3)),
+    "bf16": dict(c1=("abs", 2e-3), c2=("abs", 2e-3), c3=("abs", 2e-3), rho=("abs", 3e-3),
+                 ux=("rel", 0.2), uy=("rel", 0.2), p=("rel", 0.5), mu1=("rel", 5e-2), mu2=("rel", 5e-2)),
+}
+PRECISIONS = ["fp16", "bf16"]
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_09534_gb300 import build
+    build.build()
+    import paper_1710_09534_gb300 as T
+    return T
+
+
+def pair(T, w, precision):
+    L = T.lattice_from_workload(w, precision)
+    O = OracleLattice(w.nx, w.ny, w.edges, w.mask, w.params)
+    O.set_fields(w.c1, w.c2, w.ux, w.uy, w.p)
+    return L, O
+
+
+def check_fields(L, O, precision, what):
+    fg, fo = L.fields(), O.fields()
+    for k, (kind, bound) in BOUNDS[precision].items():
+        err = float(np.abs(fg[k] - fo[k]).max())
+        if kind == "rel":
+            err /= max(float(np.abs(fo[k]).max()), 1e-12)
+        assert err < bound, f"{what} {precision}: {k} error {err:.3e} >= {bound}"
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_binary_drops_2000_steps(T, precision):
+    w = W.binary_drops_on_wall()
+    L, O = pair(T, w, precision)
+    L.step(2000)
+    O.step(2000)
+    check_fields(L, O, precision, "128x64")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("seed,edges,lid_u,mrt", [(11, (0, 0, 1, 2), 0.0, None), (14, (0, 0, 1, 3), 0.02, None),
+                                                   (13, (0, 0, 0, 0), 0.0, None), (15, (2, 1, 1, 3), 0.01, None),
+                                                   (14, (0, 0, 1, 3), 0.02, (1.3, 1.3))])
+def test_random_lattices(T, precision, seed, edges, lid_u, mrt):
+    w = W.random_lattice(67, 45, seed, edges=edges, solids=("disc", "corner"), lid_u=lid_u)
+    if mrt:
+        w.params.update(collision=1.0, mrt_s_f=mrt[0], mrt_s_g=mrt[1])
+    L, O = pair(T, w, precision)
+    L.step(150)
+    O.step(150)
+    check_fields(L, O, precision, w.name)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_mass_drift_20000_steps(T, precision):
+    w = W.binary_drops_on_wall()
+    L = T.lattice_from_workload(w, precision)
+    m0 = np.array(L.diagnostics()["mass"])
+    L.step(20000)
+    d = L.diagnostics()
+    assert d["nonfinite"] == 0
+    drift = np.abs(np.array(d["mass"]) - m0) / np.abs(m0)
+    assert np.all(drift < 1e-6), drift
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("theta13", [60.0, 120.0])
+def test_contact_angle_within_half_degree(T, precision, theta13):
+    nx, ny, R, sig = 80, 32, 12.0, 1e-2
+    th12 = W.theta12_from(sig, sig, sig, theta13, 90.0)
+    prm = W.params(sigma=(sig, sig, sig), theta=(th12, theta13, 90.0), mobility=0.2)
+    x, y = W.grid(nx, ny)
+    c1 = W.profile(x, y, nx / 2, -0.5, R, 4.0, period_x=nx)
+    z = np.zeros((ny, nx))
+    w = W.Workload("drop", nx, ny, (0, 0, 1, 2), np.zeros((ny, nx), np.uint8), prm, c1, z, z, z)
+    L, O = pair(T, w, precision)
+    L.step(12000)
+    O.step(12000)
+    tg = oracle.contact_angle_deg(L.fields()["c1"])[0]
+    to = oracle.contact_angle_deg(O.fields()["c1"])[0]
+    assert abs(tg - to) < 0.5
+    (_, _, td, _), = L.contact_angles(1)
+    assert abs(td - to) < 0.5
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_state_export_import_round_trip(T, precision):
+    w = W.random_lattice(50, 37, 5, edges=(0, 0, 1, 3), solids=("disc",), lid_u=0.01)
+    A = T.lattice_from_workload(w, precision)
+    A.step(30)
+    blob = A.export_state()
+    B = T.lattice_from_workload(w, precision)
+    B.import_state(blob)
+    A.step(20)
+    B.step(20)
+    assert np.array_equal(A.state(), B.state())
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_batch_members_match_alone(T, precision):
+    ws = [W.random_lattice(nx, ny, 100 + i, edges=e, solids=s, lid_u=u) for i, (nx, ny, e, s, u) in
+          enumerate([(90, 50, (0, 0, 1, 2), ("disc",), 0.0), (40, 70, (0, 0, 1, 3), ("corner",), 0.01),
+                     (150, 33, (1, 2, 2, 1), ("pillar",), 0.0)])]
+    alone = [T.lattice_from_workload(w, precision) for w in ws]
+    mem = [T.lattice_from_workload(w, precision) for w in ws]
+    B = T.Batch(precision, max_lattices=4)
+    for L in mem:
+        B.add(L)
+    B.step(7)
+    B.synchronize()
+    for L in alone:
+        L.step(7)
+    for a, m in zip(alone, mem):
+        sa, sm = a.state(), m.state()
+        assert float(np.abs(sa - sm).max() / np.abs(sa).max()) < 1e-5
+
+
+def test_16bit_workspace_is_smaller(T):
+    lib = T.load_library()
+    b32 = lib.tlb_workspace_bytes(1024, 1024, T.FP32)
+    b16 = lib.tlb_workspace_bytes(1024, 1024, T.FP16)
+    assert lib.tlb_workspace_bytes(1024, 1024, T.BF16) == b16
+    assert b16 < 0.7 * b32
