@@ -34,8 +34,18 @@ METRIC = "MLUPS & % of HBM roofline, batched/served vs plain; p50/p99 solve late
 def bytes_per_node(precision):
     """Algorithmic bytes per node update: the state that must persist, read
     and written once -- 27 distributions (FP32 storage adds the lo halves of
-    the two rest populations) and the 4 c_i u values of Eq. 19."""
-    return 2 * (27 + 4) * 8 if precision == "fp64" else 2 * (29 + 4) * 4
+    the two rest populations) and the 4 c_i u values of Eq. 19.  16-bit
+    storage: 25 populations of 2 bytes, the two rest populations as FP32
+    pairs (16 bytes) and the c_i u values in FP32."""
+    if precision == "fp64":
+        return 2 * (27 + 4) * 8
+    if precision == "fp32":
+        return 2 * (29 + 4) * 4
+    return 2 * (25 * 2 + 4 * 4 + 4 * 4)
+
+
+KERNEL = {"fp64": "k_step_interior<double>", "fp32": "k_step_interior<float>",
+          "fp16": "k_step_interior<__half>", "bf16": "k_step_interior<__nv_bfloat16>"}
 
 
 # FP64 arithmetic per node update of the fused interior kernel, as counted by
@@ -70,12 +80,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--variants", default="fp32", help="comma list of extra precisions to time")
+    ap.add_argument("--variants", default="fp32,fp16,bf16", help="comma list of extra precisions to time")
+    ap.add_argument("--impact-steps", type=int, default=200,
+                    help="steps timed on the 1024x2048 cylinder-impact workload per precision (0: skip)")
     ap.add_argument("--batch-count", type=int, default=256, help="lattices in the batched workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--serve-count", type=int, default=40, help="requests in the served workload (0: skip)")
@@ -291,13 +303,15 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": round(ach_gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
                 "frac": round(hbm_frac, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": "k_step_interior<float>"}
+                "kernel": KERNEL[args.precision]}
     result = {
         "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "precision": args.precision,
+                   "storage": {"fp64": "f64", "fp32": "f32", "fp16": "f16 (shifted, x2^12) + f32 rest pairs",
+                               "bf16": "bf16 (shifted) + f32 rest pairs"}[args.precision],
                    "l2": f"state {bytes_node * n_nodes / 1e9:.2f} GB moved per step > 129 MB L2 (no flush needed)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "wall_nodes": int(L.wall_nodes())},
@@ -321,6 +335,8 @@ def run_ours(args):
                               "hbm_roofline_pct": round(100 * v_mlups * 1e6 * bytes_per_node(prec) / (hbm_gbs * 1e9), 2)}
             del V
         result["variants"] = variants
+        if args.impact_steps > 0:
+            result["impact"] = impact(args, torch, T)
         if args.batch_count > 0:
             result["batched"] = batched(args, torch, T)
         if args.serve_count > 0:
@@ -335,66 +351,91 @@ def run_ours(args):
 
 def batched(args, torch, T):
     """The batched workload: `batch_count` lattices with sides log-uniform in
-    [64, 512] (drops on a wetting wall, random tensions and angles), FP32.
-    Aggregate MLUPS of (a) the plain path, one tlb_step call per lattice, and
-    (b) one batch (persistent tile-queue kernel, graph-captured), after the
-    batch tuner picked its tile shape."""
+    [64, 512] (drops on a wetting wall, random tensions and angles), in FP32
+    and in shifted-FP16 storage.  Aggregate MLUPS of (a) the plain path, one
+    tlb_step call per lattice, and (b) one batch (persistent tile-queue
+    kernel, graph-captured), after the batch tuner picked its tile shape."""
     import workloads as W
     ws = W.batch_population(args.batch_count, seed=1710)
     nodes = sum(w.nodes for w in ws)
     k = args.batch_steps
-    plain = [T.lattice_from_workload(w, "fp32") for w in ws]
-    for L in plain:
-        L.step(2)
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record()
-    for L in plain:
-        L.step(k)
-    s1.record()
-    s1.synchronize()
-    plain_ms = s0.elapsed_time(s1)
-    del plain
-    mem = [T.lattice_from_workload(w, "fp32") for w in ws]
-    B = T.Batch("fp32", max_lattices=len(mem), max_tiles=sum(T.Batch.tiles_needed(w.nx, w.ny) for w in ws),
-                max_wall_nodes=sum(L.wall_nodes() for L in mem))
-    for L in mem:
-        B.add(L)
-    cfg = B.tune(trial_steps=3)
-    B.step(2)
-    B.synchronize()
-    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    b0.record(B.stream)
-    B.step(k)
-    b1.record(B.stream)
-    b1.synchronize()
-    batch_ms = b0.elapsed_time(b1)
-    out = {"workload": f"{len(ws)} lattices, sides log-uniform 64..512 (seed 1710), drops on a wetting wall, FP32",
-           "nodes": nodes, "steps": k,
-           "plain_mlups": round(nodes * k / (plain_ms / 1e3) / 1e6, 1),
-           "batched_mlups": round(nodes * k / (batch_ms / 1e3) / 1e6, 1),
-           "tuned": cfg}
-    out["speedup"] = round(out["batched_mlups"] / out["plain_mlups"], 2)
-    B.close()
+    out = {"workload": f"{len(ws)} lattices, sides log-uniform 64..512 (seed 1710), drops on a wetting wall",
+           "nodes": nodes, "steps": k}
+    for prec in ("fp32", "fp16"):
+        plain = [T.lattice_from_workload(w, prec) for w in ws]
+        for L in plain:
+            L.step(2)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for L in plain:
+            L.step(k)
+        s1.record()
+        s1.synchronize()
+        plain_ms = s0.elapsed_time(s1)
+        del plain
+        mem = [T.lattice_from_workload(w, prec) for w in ws]
+        B = T.Batch(prec, max_lattices=len(mem), max_tiles=sum(T.Batch.tiles_needed(w.nx, w.ny) for w in ws),
+                    max_wall_nodes=sum(L.wall_nodes() for L in mem))
+        for L in mem:
+            B.add(L)
+        cfg = B.tune(trial_steps=3)
+        B.step(2)
+        B.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(B.stream)
+        B.step(k)
+        b1.record(B.stream)
+        b1.synchronize()
+        batch_ms = b0.elapsed_time(b1)
+        r = {"plain_mlups": round(nodes * k / (plain_ms / 1e3) / 1e6, 1),
+             "batched_mlups": round(nodes * k / (batch_ms / 1e3) / 1e6, 1), "tuned": cfg}
+        r["speedup"] = round(r["batched_mlups"] / r["plain_mlups"], 2)
+        B.close()
+        del mem
+        if prec == "fp32":
+            out.update(r)  # the FP32 figures at the top level
+        else:
+            out[prec] = r
+    return out
+
+
+def impact(args, torch, T):
+    """Compound drop falling onto a wetting cylinder (1024 x 2048, R_cyl = 120,
+    core R = 60, shell R = 100, We = 10, cylinder angles 90 deg), FP32 vs
+    shifted-FP16 storage: MLUPS over `impact_steps` steps each."""
+    import workloads as W
+    w = W.compound_drop_on_cylinder(1024, 2048, We=10.0)
+    out = {"workload": f"{w.name}, We = 10, periodic, cylinder R = 120 (curved wetting wall)",
+           "steps": args.impact_steps}
+    for prec in ("fp32", "fp16"):
+        L = T.lattice_from_workload(w, prec)
+        L.step(max(3, args.warmup))
+        L.sync()
+        ms = time_steps(L, args.impact_steps, torch, torch.cuda.current_stream())
+        out[prec + "_mlups"] = round(w.nx * w.ny * args.impact_steps / (ms / 1e3) / 1e6, 1)
+        L.close()
     return out
 
 
 def served(args, torch, T):
     """The served workload: Poisson arrivals (20 requests/s, seed 1710) of
     drop-on-wall and drop-on-cylinder jobs, sides log-uniform 128..1024, steps
-    log-uniform 500..5000, FP32, admitted by device footprint against an HBM
-    budget; time to result and aggregate MLUPS over the whole run."""
+    log-uniform 500..5000, FP32 and FP16 storage alternating, admitted by
+    device footprint against an HBM budget; time to result and aggregate
+    MLUPS over the whole run."""
     import workloads as W
     from paper_1710_09534_gb300.serve import Request, Server, poisson_arrivals
     jobs = W.served_requests(args.serve_count, seed=1710, lo=128, hi=1024, steps_lo=500, steps_hi=5000)
     t_arr = poisson_arrivals(len(jobs), 20.0, seed=1710)
-    reqs = [Request(i, w, s, "fp32", float(t)) for i, ((w, s), t) in enumerate(zip(jobs, t_arr))]
+    # every other request asks for shifted-FP16 storage; the server keeps one batch per precision
+    reqs = [Request(i, w, s, "fp16" if i % 2 else "fp32", float(t)) for i, ((w, s), t) in enumerate(zip(jobs, t_arr))]
     srv = Server(int(args.serve_budget_gb * 1e9), max_lattices=256, chunk=200)
     stats = srv.run(reqs)
     srv.close()
     out = stats.summary()
     out["workload"] = (f"{len(reqs)} requests, Poisson 20/s (seed 1710), sides 128..1024, steps 500..5000, "
-                       f"FP32, HBM budget {args.serve_budget_gb} GB")
+                       f"FP32 and shifted-FP16 alternating, HBM budget {args.serve_budget_gb} GB")
     return out
 
 

@@ -179,13 +179,6 @@ bool finite_all(const tlb_params* p)
     return true;
 }
 
-int popcount10(uint32_t m)
-{
-    int c = 0;
-    for (int q = 0; q < 10; q++) c += (m >> q) & 1u;
-    return c;
-}
-
 }  // namespace
 
 extern "C" {

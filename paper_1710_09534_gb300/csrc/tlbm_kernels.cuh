@@ -293,14 +293,24 @@ __device__ __forceinline__ void collide_all(const MrtNode<R>& col, const R gv[9]
 template <bool MRT, typename R>
 using CollideOf = typename std::conditional<MRT, MrtNode<R>, Collider<R>>::type;
 
-// Periodic wrap of a destination that may leave the lattice by one node on a
-// periodic axis (interior nodes never reach a non-periodic edge).
-__device__ __forceinline__ long long wrap_off(const Geo& g, int x, int y)
-{
-    x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
-    y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
-    return (long long)y * g.pitch + x;
-}
+// Destinations of the push from an interior node (x, y): the neighbouring
+// columns and rows, wrapped on a periodic axis (interior nodes never reach a
+// non-periodic edge), so that each direction costs one add.
+struct PushOffsets {
+    int col[3];        // x - 1, x, x + 1 (wrapped)
+    long long row[3];  // (y - 1, y, y + 1) * pitch (wrapped)
+    __device__ __forceinline__ PushOffsets(const Geo& g, int x, int y)
+    {
+        col[0] = x > 0 ? x - 1 : g.nx - 1;
+        col[1] = x;
+        col[2] = x < g.nx - 1 ? x + 1 : 0;
+        row[0] = (long long)(y > 0 ? y - 1 : g.ny - 1) * g.pitch;
+        row[1] = (long long)y * g.pitch;
+        row[2] = (long long)(y < g.ny - 1 ? y + 1 : 0) * g.pitch;
+    }
+    template <int K>
+    __device__ __forceinline__ long long dest() const { return row[1 + ey(K)] + col[1 + ex(K)]; }
+};
 
 // ---------------------------------------------------------------------------
 // K1: fused interior update, marching along a strip of columns.
@@ -441,6 +451,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         cu[3 * PL + ou] = CuT<S>(c2uy);
         CollideOf<MRT, R> col;
         col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
+        const PushOffsets po(g, xs, yu);
         collide_all<S, R>(col, gv,
             [&](auto kc, R& f1k, R& f2k) {
                 constexpr int K = decltype(kc)::value;
@@ -453,7 +464,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
             },
             [&](auto kc, R o1, R o2, R og) {
                 constexpr int K = decltype(kc)::value;
-                const long long d = (K == 0) ? ou : wrap_off(g, xs + ex(K), yu + ey(K));
+                const long long d = (K == 0) ? ou : po.template dest<K>();
                 st_pop(fB, K, PL, d, o1);
                 st_pop(fB, 9 + K, PL, d, o2);
                 st_pop(fB, 18 + K, PL, d, og);

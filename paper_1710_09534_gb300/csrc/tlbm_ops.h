@@ -84,7 +84,7 @@ inline const Ops& ops_for(int precision, bool mrt)
 #define TLB_MINB64 3
 #endif
 #ifndef TLB_MINB32
-#define TLB_MINB32 4
+#define TLB_MINB32 5
 #endif
 #ifndef TLB_PREFETCH32
 #define TLB_PREFETCH32 1

@@ -69,6 +69,16 @@ def test_fp32_random_lattices(T, seed, edges, lid_u):
     check_fields(L, O, w.name)
 
 
+def test_fp32_cylinder_impact_600_steps(T):
+    """Compound-drop impact on a cylinder (density ratio 10): FP32 stays within
+    the same bounds (measured on GB300: c 7.6e-6, rho 6.3e-5, p 4e-5 of scale)."""
+    w = W.compound_drop_on_cylinder(nx=256, ny=512, R_cyl=30, R_core=15, R_shell=25, We=10.0, theta=30.0)
+    L, O = pair(T, w)
+    L.step(600)
+    O.step(600)
+    check_fields(L, O, "cylinder impact")
+
+
 def test_fp32_mass_drift_20000_steps(T):
     """Each component's mass is conserved to 1e-6 relative over 20000 steps
     (walls and a wetting substrate; no lid)."""

@@ -25,7 +25,7 @@ def test_served_results_equal_runs_alone(T):
     jobs = W.served_requests(10, seed=7, lo=64, hi=192, steps_lo=40, steps_hi=300)
     reqs = []
     for i, (w, steps) in enumerate(jobs):
-        reqs.append(Request(i, w, steps, "fp64" if i % 4 == 3 else "fp32", arrival=0.02 * i))
+        reqs.append(Request(i, w, steps, ("fp32", "fp16", "fp32", "fp64", "bf16")[i % 5], arrival=0.02 * i))
     lib = T.load_library()
     sizes = sorted(int(lib.tlb_workspace_bytes(w.nx, w.ny, T.PRECISIONS[r.precision])) for r, (w, _) in zip(reqs, jobs))
     budget = sizes[-1] + sizes[-2] + sizes[-3]  # at most a few resident at once
