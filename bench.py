@@ -207,10 +207,11 @@ def oracle_run(w, steps, warmup=0):
     return w.nx * w.ny * steps / dt / 1e6, dt, oracle.threads()
 
 
-def cpu_baseline(w, budget_s=15.0):
+def cpu_baseline(w, budget_s=12.0):
+    """The oracle on a bounded sample (~budget_s seconds of host work)."""
     s = sample_workload(w)
-    _, t1, _ = oracle_run(s, 1)
-    steps = max(1, min(200, int(budget_s / max(t1, 1e-3))))
+    _, t1, _ = oracle_run(s, 2)
+    steps = max(1, min(5000, int(budget_s / max(t1 / 2, 1e-3))))
     mlups, dt, thr = oracle_run(s, steps)
     return {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
             "sample": f"{s.nx}x{s.ny} bottom strip of the {w.nx}x{w.ny} lattice, {steps} steps, "
