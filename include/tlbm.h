@@ -203,6 +203,17 @@ int tlb_diagnostics(tlb_lattice *lat, tlb_diag *out);
  * Synchronizes. */
 int tlb_contact_angles(tlb_lattice *lat, int component, double *host_out, int max_drops, int *n_drops);
 
+/* Film thickness on top of a solid (Sec. III.D: the film of the impacting
+ * compound drop on the cylinder, Fig. 14's h), in FP64 on the device.  In
+ * column x (0 <= x < nx), from the fluid node above the solid node y_top
+ * (-1 <= y_top <= ny - 2; -1 is the bottom edge wall), walk up through nodes
+ * whose order-parameter sum selected by comps (1: c1, 2: c2, 3: c1 + c2) is
+ * >= 1/2.  *h_out = the height of the c = 1/2 crossing (linear interpolation)
+ * above the half-way wall at y_top + 1/2; 0 if the first node is below 1/2;
+ * measured to row ny - 1 if the sum never drops below 1/2.  No wrap in y.
+ * Synchronizes. */
+int tlb_film_thickness(tlb_lattice *lat, int x, int y_top, int comps, double *h_out);
+
 /* Raw state as FP64 host planes [31][ny][nx]: f^1_k (k = 0..8), f^2_k,
  * g_k, then c1 ux, c1 uy, c2 ux, c2 uy of the previous step (Eq. 19).
  * Synchronizes. */

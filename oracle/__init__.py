@@ -317,6 +317,26 @@ def drop_geometry(c: np.ndarray, wall_row: int = 0):
     return out
 
 
+def film_thickness(c: np.ndarray, x: int, y_top: int) -> float:
+    """Thickness of the liquid film on top of a solid in column x (Sec. III.D,
+    the film of the impacting drop on the cylinder top).
+
+    Reading of the measurement (the paper names h but not how it is taken):
+    the film is the run of nodes above the solid node y_top with c >= 1/2
+    (c the order parameter, or sum of order parameters, of the liquid); h is
+    its c = 1/2 crossing (linear interpolation in y) minus the half-way wall
+    at y_top + 1/2; 0 if the node above the solid is below 1/2; the top row
+    bounds the walk (no wrap)."""
+    ny = c.shape[0]
+    y = y_top + 1
+    if not c[y, x] >= 0.5:
+        return 0.0
+    while y + 1 < ny and c[y + 1, x] >= 0.5:
+        y += 1
+    top = y + (c[y, x] - 0.5) / (c[y, x] - c[y + 1, x]) if y + 1 < ny else float(y)
+    return top - (y_top + 0.5)
+
+
 def contact_angle_deg(c: np.ndarray, wall_row: int = 0):
     """theta_n = 2 atan(2 H_d / L_s) for each drop (Sec. III.A)."""
     return [np.degrees(2.0 * np.arctan(2.0 * H / Ls)) for Ls, H, _ in drop_geometry(c, wall_row)]

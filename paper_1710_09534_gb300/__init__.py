@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tlb_wall_nodes": (i64, [vp]),
         "tlb_diagnostics_noalloc": (i32, [vp, vp]),
         "tlb_contact_angles": (i32, [vp, i32, dp, i32, ctypes.POINTER(ctypes.c_int)]),
+        "tlb_film_thickness": (i32, [vp, i32, i32, i32, dp]),
         "tlb_profile": (i32, [vp, i32]),
         "tlb_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "tlb_destroy": (None, [vp]),
@@ -240,6 +241,13 @@ class Lattice:
         _check(self.lib.tlb_contact_angles(self._h, int(component), _dp(out), int(max_drops), ctypes.byref(n)))
         k = min(n.value, max_drops)
         return [tuple(out[4 * i:4 * i + 4]) for i in range(k)]
+
+    def film_thickness(self, x: int, y_top: int, comps: int = 3) -> float:
+        """Film thickness above solid node (x, y_top) of c1 (comps=1), c2 (2) or
+        c1 + c2 (3): see tlb_film_thickness."""
+        h = ctypes.c_double()
+        _check(self.lib.tlb_film_thickness(self._h, int(x), int(y_top), int(comps), ctypes.byref(h)))
+        return h.value
 
     def state(self) -> np.ndarray:
         out = np.empty((31, self.ny, self.nx))

@@ -531,6 +531,22 @@ int tlb_contact_angles(tlb_lattice* L, int component, double* host_out, int max_
     return ok();
 }
 
+int tlb_film_thickness(tlb_lattice* L, int x, int y_top, int comps, double* h_out)
+{
+    int rc = check_handle(L);
+    if (rc) return rc;
+    if (!h_out) return fail(TLB_EINVAL, "h_out is null");
+    if (x < 0 || x >= L->nx || y_top < -1 || y_top > L->ny - 2)
+        return fail(TLB_EINVAL, "column %d / solid row %d outside the lattice", x, y_top);
+    if (comps < 1 || comps > 3) return fail(TLB_EINVAL, "comps must be 1, 2 or 3");
+    if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "no state yet");
+    double* res = (double*)(L->ws + L->lay.contact) + 2 * (size_t)L->nx;
+    TLB_CUDA(L->ops->film(L->bufA(), L->dcls(), x, y_top, comps, res, L->geo, L->stream));
+    TLB_CUDA(cudaMemcpyAsync(h_out, res, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    TLB_CUDA(cudaStreamSynchronize(L->stream));
+    return ok();
+}
+
 // IEEE 754 binary16 and bfloat16 bit patterns to double (host side of the
 // 16-bit storage formats).
 static double half_bits(uint16_t h)

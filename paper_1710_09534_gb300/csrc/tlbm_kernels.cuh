@@ -966,6 +966,50 @@ __global__ void k_contact_columns(const S* __restrict__ fA, const uint8_t* __res
     colh[x] = h + 0.5;
 }
 
+// Film thickness above a solid (Sec. III.D, the film on top of the cylinder):
+// in column x, starting at the fluid node above the solid node y_top (the
+// half-way wall at y_top + 1/2), walk up through nodes whose selected order
+// parameter sum (comps bit 0: c1, bit 1: c2) is >= 1/2; the film thickness is
+// the c = 1/2 crossing (linear interpolation) minus y_top + 1/2, in FP64;
+// 0 where the first node is below 1/2; up to row ny - 1 where it never drops.
+template <typename S>
+__global__ void k_film(const S* __restrict__ fA, const uint8_t* __restrict__ cls, int x, int y_top, int comps,
+                       double* __restrict__ out, Geo g)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const long long PL = g.plane;
+    auto cval = [&](int y) {
+        const long long o = (long long)y * g.pitch + x;
+        const int kind = cls[o] & CLS_KIND_MASK;
+        if (!fluidlike(kind)) return 0.0;
+        const long long src = kind == ST_LID ? o - g.pitch : o;
+        double s = 0.0;
+        for (int i = 0; i < 2; i++) {
+            if (!(comps & (1 << i))) continue;
+            double v[9];
+            for (int k = 0; k < 9; k++) v[k] = ld_pop<double>(fA, 9 * i + k, PL, src);
+            v[0] += ld_lo<double>(fA, i, PL, src);
+            s += sum9(v);
+        }
+        return s;
+    };
+    int y = y_top + 1;
+    double cy = cval(y);
+    if (!(cy >= 0.5)) {
+        out[0] = 0.0;
+        return;
+    }
+    double cn = 0.0;
+    while (y + 1 < g.ny) {
+        cn = cval(y + 1);
+        if (!(cn >= 0.5)) break;
+        y++;
+        cy = cn;
+    }
+    const double top = (y + 1 < g.ny) ? y + (cy - 0.5) / (cy - cn) : (double)y;
+    out[0] = top - (y_top + 0.5);
+}
+
 // One thread: the c >= 1/2 segments of the (periodic) wall row, with their
 // crossings, base length L_s, height H_d (largest column height over the
 // segment) and theta_n.  out[4*i + 0..3] = L_s, H_d, theta_n (degrees), x_mid.

@@ -25,6 +25,10 @@ struct Ops {
     // wallc[nx], colh[nx] scratch, out[4*max_drops], *count
     cudaError_t (*contact)(const void* fA, const uint8_t* cls, int comp, double* wallc, double* colh,
                            double* out, int max_drops, int* count, const Geo& g, cudaStream_t s);
+    // film thickness above solid node (x, y_top) of the order-parameter sum
+    // selected by comps (FP64), into *out
+    cudaError_t (*film)(const void* fA, const uint8_t* cls, int x, int y_top, int comps, double* out, const Geo& g,
+                        cudaStream_t s);
     // batched step: persistent interior kernel (variant 0: 64-thread blocks,
     // 1: 128-thread blocks) over the tile list, then the near-wall loop
     cudaError_t (*batch_step)(const void* descs, const void* tiles, const void* walls, void* ctr, int parity,

@@ -101,6 +101,12 @@ struct OpsImpl {
         k_contact_scan<<<1, 32, 0, s>>>(wallc, colh, g.nx, out, max_drops, count);
         return cudaGetLastError();
     }
+    static cudaError_t film(const void* fA, const uint8_t* cls, int x, int y_top, int comps, double* out,
+                            const Geo& g, cudaStream_t s)
+    {
+        k_film<S><<<1, 32, 0, s>>>((const S*)fA, cls, x, y_top, comps, out, g);
+        return cudaGetLastError();
+    }
     // the two block shapes the batch tuner chooses between
     static constexpr int kMinB64 = std::is_same<R, float>::value ? 8 : 6;
     static cudaError_t batch_step(const void* descs, const void* tiles, const void* walls, void* ctr, int parity,
@@ -141,7 +147,7 @@ struct OpsImpl {
     }
     static const Ops& table()
     {
-        static const Ops t{sizeof(S), Store<S>::kPlanes, sizeof(CuT<S>), &interior, &wall, &init, &read, &contact, &batch_step,
+        static const Ops t{sizeof(S), Store<S>::kPlanes, sizeof(CuT<S>), &interior, &wall, &init, &read, &contact, &film, &batch_step,
                           &batch_blocks_per_sm, sizeof(LatDesc<R>), &fill_desc, &mass};
         return t;
     }

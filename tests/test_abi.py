@@ -72,6 +72,8 @@ def test_create_rejects_bad_arguments_without_touching_the_device(lib):
     assert lib.tlb_create_lattice(16, 16, 0, e, None, 0, None, ctypes.byref(h)) == T.EINVAL
     assert "workspace" in T.last_error()
     assert lib.tlb_step(None, 1) == T.EINVAL
+    hf = ctypes.c_double()
+    assert lib.tlb_film_thickness(None, 0, 0, 3, ctypes.byref(hf)) == T.EINVAL
 
 
 def test_python_params_mirror_the_header_struct():

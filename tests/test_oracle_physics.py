@@ -301,3 +301,26 @@ def test_solid_row_in_mask_equals_wall_edge():
     fa, fb = A.fields(), B.fields()
     for k in ("c1", "c2", "ux", "uy", "p", "mu1", "mu2"):
         assert np.abs(fa[k] - fb[k][1:]).max() <= 1e-14 * max(1.0, np.abs(fa[k]).max()), k
+
+
+def test_film_thickness_measurement():
+    """The film reading: crossing of c = 1/2 above the half-way wall."""
+    ny, nx, y_top = 40, 3, 9
+    c = np.zeros((ny, nx))
+    # a linear ramp 1 -> 0 between rows 20 and 21 crosses 1/2 at 20.5: h = 20.5 - 9.5
+    c[10:21, 1] = 1.0
+    c[20, 1] = 0.75
+    c[21, 1] = 0.25
+    assert oracle.film_thickness(c, 1, y_top) == pytest.approx(11.0, abs=1e-15)
+    # no liquid on the solid: zero
+    assert oracle.film_thickness(c, 0, y_top) == 0.0
+    # liquid up to the top row: bounded by it
+    c[10:, 2] = 1.0
+    assert oracle.film_thickness(c, 2, y_top) == pytest.approx(ny - 1 - (y_top + 0.5))
+    # a tanh film of thickness h0 (Eq. 50 profile across a flat interface)
+    y = np.arange(ny, dtype=float)
+    for h0 in (6.3, 12.8):
+        prof = 0.5 + 0.5 * np.tanh(2.0 * (h0 - (y - (y_top + 0.5))) / 4.0)
+        prof[: y_top + 1] = 0.0
+        col = np.repeat(prof[:, None], 1, axis=1)
+        assert abs(oracle.film_thickness(col, 0, y_top) - h0) < 0.02

@@ -117,6 +117,29 @@ def binary_drops_on_wall(nx=128, ny=64, R=16.0, sep=40.0, theta=(60.0, 90.0, 120
                     steps=steps)
 
 
+def puddles(g, nx=600, ny=150, R=60.0, rho=(10.0, 5.0, 1.0), sigma=0.1, theta=90.0, M0=0.01,
+            steps=200000) -> Workload:
+    """Two drops (fluid 1, density 10; fluid 2, density 5) on a wetting bottom
+    wall in fluid 3 (density 1) under gravity G = (0, -rho g) (Sec. III.A with
+    gravity): L x W = 600 x 150, R = 0.1 L centred on the wall at 0.25 L and
+    0.75 L, sigma_ij = 0.1, tau_i = tau_g = 0.8, M0 = 0.01, D = 4,
+    theta_13 = theta_23 = theta (theta_12 from Eq. 39), bounce-back top wall."""
+    x, y = grid(nx, ny)
+    c1 = profile(x, y, 0.25 * nx, -0.5, R, 4.0, period_x=nx)
+    c2 = profile(x, y, 0.75 * nx, -0.5, R, 4.0, period_x=nx)
+    th12 = theta12_from(sigma, sigma, sigma, theta, theta)
+    P = params(sigma=(sigma, sigma, sigma), theta=(th12, theta, theta), rho=rho, nu=(0.1, 0.1, 0.1),
+               M0=M0, D=4.0, tau=(0.8, 0.8), g=(0.0, -g))
+    return Workload(f"puddles_{nx}x{ny}_g{g:g}", nx, ny, (PERIODIC, PERIODIC, WETTING, NEUTRAL),
+                    np.zeros((ny, nx), np.uint8), P, c1, c2, _zeros(nx, ny), _zeros(nx, ny),
+                    steps=steps, meta=dict(g=g, R=R, rho=rho, sigma=sigma, theta=theta))
+
+
+def puddle_thickness(sigma, rho_liquid, g, theta_deg):
+    """Eq. 48: H = 2 sqrt(sigma / (rho_l g)) sin(theta_e / 2) (de Gennes' puddle)."""
+    return 2.0 * math.sqrt(sigma / (rho_liquid * g)) * math.sin(math.radians(theta_deg) / 2)
+
+
 def compound_drop_shear(nx=512, ny=256, R_core=30.0, R_shell=50.0, U0=0.01, steps=20000,
                         sigma=(2e-3, 1e-3, 1e-3), theta13=90.0, theta23=135.0) -> Workload:
     """Compound drop (core fluid 1, shell fluid 2) on a wetting wall in fluid 3,
@@ -163,6 +186,35 @@ def compound_drop_on_cylinder(nx=1024, ny=2048, R_cyl=120.0, R_core=60.0, R_shel
                     (PERIODIC, PERIODIC, PERIODIC, PERIODIC), mask, P, c1, c2,
                     _zeros(nx, ny), uy, steps=steps,
                     meta=dict(We=We, U=U, Re=xi * U / 0.02))
+
+
+def impact_e5(We=21.6, theta13=30.0, L=240, W=280, single=False, mrt=None) -> Workload:
+    """Compound drop impact on a cylinder at the paper's size (Sec. III.D):
+    L x W = 240 x 280 fully periodic; cylinder R = L/8 centred at (L/2, L/2);
+    drop centred at (L/2, 3L/4), core fluid 1 of radius L/16 in a shell of
+    fluid 2 of outer radius L/8 (xi = L/4); rho_1 = rho_2 = 10, rho_3 = 1;
+    U = 0.06 downward, Re = xi U / nu = 600; sigma_ij all equal, set by We =
+    rho_bar xi U^2 / sigma_bar (Eq. 55); theta_12 = 90, theta_13 = theta_23;
+    M_1 = M_2 = 0.1, tau_1 = tau_2 = 0.8.  single=True: c1 = 0 (the
+    single-drop comparison).  meta: xi, U, x and y_top of the cylinder top."""
+    x, y = grid(L, W)
+    xc, yc, Rc = L / 2, L / 2, L / 8
+    mask = (((x - xc) ** 2 + (y - yc) ** 2) <= Rc ** 2).astype(np.uint8)
+    R_out, R_in = L / 8, L / 16
+    c1 = np.zeros((W, L)) if single else profile(x, y, L / 2, 0.75 * L, R_in, 4.0, period_x=L, period_y=W)
+    c2 = profile(x, y, L / 2, 0.75 * L, R_out, 4.0, period_x=L, period_y=W) - c1
+    c1[mask == 1] = 0.0
+    c2[mask == 1] = 0.0
+    xi, U = L / 4, 0.06
+    nu = xi * U / 600.0
+    sig = 10.0 * xi * U * U / We
+    P = params(sigma=(sig, sig, sig), theta=(90.0, theta13, theta13), rho=(10.0, 10.0, 1.0),
+               nu=(nu, nu, nu), mobility=0.1, D=4.0, tau=(0.8, 0.8), mrt=mrt)
+    col = int(round(xc))
+    y_top = int(max(yy for yy in range(W) if mask[yy, col]))
+    return Workload(f"impact_e5_{L}x{W}_We{We:g}_th{theta13:g}" + ("_single" if single else ""), L, W,
+                    (PERIODIC, PERIODIC, PERIODIC, PERIODIC), mask, P, c1, c2, _zeros(L, W), -U * (c1 + c2),
+                    steps=int(10 * xi / U), meta=dict(xi=xi, U=U, x_top=col, y_top=y_top, We=We))
 
 
 def tiled_drops(nx=2048, ny=2048, seed=1710, steps=1000) -> Workload:
