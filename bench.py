@@ -335,6 +335,19 @@ def run_ours(args):
             variants[prec] = {"value": round(v_mlups, 2), "unit": "MLUPS",
                               "hbm_roofline_pct": round(100 * v_mlups * 1e6 * bytes_per_node(prec) / (hbm_gbs * 1e9), 2)}
             del V
+        # the MRT collision option on the same lattice (FP64 and FP32 storage)
+        for prec in ("fp64", "fp32"):
+            wm = W.tiled_drops(args.nx, args.ny)
+            wm.params.update(collision=1.0, mrt_s_f=1.2, mrt_s_g=1.2)
+            V = T.lattice_from_workload(wm, prec)
+            V.step(args.warmup)
+            V.sync()
+            n_mrt = max(10, args.steps // (4 if prec == "fp64" else 1))
+            vms = time_steps(V, n_mrt, torch, stream)
+            v_mlups = n_nodes * n_mrt / (vms / 1e3) / 1e6
+            variants[prec + "_mrt"] = {"value": round(v_mlups, 2), "unit": "MLUPS", "steps": n_mrt,
+                                       "collision": "MRT (s_f = s_g = 1.2)"}
+            del V
         result["variants"] = variants
         if args.impact_steps > 0:
             result["impact"] = impact(args, torch, T)
