@@ -5,9 +5,9 @@
 // order-parameter populations (plus the rest populations' lo parts) of the row
 // it enters, to sum c_1, c_2 (Eq. 13a), and two iterations later the same
 // populations again for the collision of that row.  Here one thread of the
-// block issues, kPrefetch iterations ahead, one cp.async.bulk copy per plane of
-// the row segment into a ring of shared-memory slots, completing on an
-// mbarrier per slot; the threads wait on the slot's phase and read the row
+// block's first warp issues, kPrefetch iterations ahead, one cp.async.bulk copy
+// per plane of the row segment (one lane per plane) into a ring of
+// shared-memory slots, completing on an mbarrier per slot; the threads wait on the slot's phase and read the row
 // from shared memory for both uses.  The loads leave the threads' critical
 // path and their registers, and the DRAM traffic of a row is in flight while
 // the rows before it are computed.
@@ -104,11 +104,12 @@ struct StagedRows {
 
     __device__ __forceinline__ int row_of(int j) const { return dir > 0 ? y0 - 2 + j : y1 + 1 - j; }
 
-    // producer: stage the row that iteration j will sum
+    // producer (warp 0): stage the row that iteration j will sum; lane 0
+    // arms the slot's barrier, then one lane per plane issues its copy
     __device__ __forceinline__ void issue(int j)
     {
-        if (threadIdx.x != 0 || j >= iters) return;
-        issued = j;
+        if (threadIdx.x >= 32 || j >= iters) return;
+        const int lane = threadIdx.x;
         unsigned char* slot = slots + (j % kSlots) * Ring::kSlotBytes;
         uint64_t* bar = bars + (j % kSlots);
         int y = row_of(j);
@@ -120,28 +121,28 @@ struct StagedRows {
         const int cs = a0 > 0 ? a0 : 0;
         const int ce = (a0 + NC < pitch) ? a0 + NC : pitch;
         const int ncol = ce - cs;
-        fence_proxy_async_smem();
-        if (!valid) {
-            mbar_arrive_expect_tx(bar, 0);  // complete the phase without data
-            return;
+        if (lane == 0) {
+            issued = j;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, valid ? (uint32_t)(ncol * (Ring::k16 ? 16 * 2 + 4 * 4 : 20 * 4)) : 0u);
         }
+        __syncwarp();
+        if (!valid || lane >= 20) return;
+        fence_proxy_async_smem();
         const long long rowoff = (long long)y * pitch + cs;
         if constexpr (Ring::k16) {
-            mbar_arrive_expect_tx(bar, (uint32_t)(ncol * (16 * 2 + 4 * 4)));
-            const unsigned short* h = reinterpret_cast<const unsigned short*>(f);
-            for (int m = 0; m < 16; m++) {
-                const int q = m < 8 ? m + 1 : m + 2;
-                bulk_g2s(slot + (m * NC + (cs - a0)) * 2, h + q * PL + rowoff, (uint32_t)(ncol * 2), bar);
+            if (lane < 16) {
+                const int q = lane < 8 ? lane + 1 : lane + 2;
+                bulk_g2s(slot + (lane * NC + (cs - a0)) * 2,
+                         reinterpret_cast<const unsigned short*>(f) + q * PL + rowoff, (uint32_t)(ncol * 2), bar);
+            } else {
+                const int j2 = lane - 16;
+                bulk_g2s(slot + 32 * NC + (j2 * NC + (cs - a0)) * 4, rest_region(f, PL) + j2 * PL + rowoff,
+                         (uint32_t)(ncol * 4), bar);
             }
-            const float* r = rest_region(f, PL);
-            for (int j2 = 0; j2 < 4; j2++)
-                bulk_g2s(slot + 32 * NC + (j2 * NC + (cs - a0)) * 4, r + j2 * PL + rowoff, (uint32_t)(ncol * 4), bar);
         } else {
-            mbar_arrive_expect_tx(bar, (uint32_t)(ncol * 20 * 4));
-            for (int p = 0; p < 20; p++) {
-                const int q = p < 18 ? p : 27 + (p - 18);
-                bulk_g2s(slot + (p * NC + (cs - a0)) * 4, f + q * PL + rowoff, (uint32_t)(ncol * 4), bar);
-            }
+            const int q = lane < 18 ? lane : 27 + (lane - 18);
+            bulk_g2s(slot + (lane * NC + (cs - a0)) * 4, f + q * PL + rowoff, (uint32_t)(ncol * 4), bar);
         }
     }
 
