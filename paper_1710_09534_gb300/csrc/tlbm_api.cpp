@@ -74,7 +74,7 @@ tlb::Layout layout_for(int nx, int ny, int precision)
     L.cls = take(L.plane);
     L.list = take((int64_t)nx * ny * 4);
     L.part = take((int64_t)kMassParts * 4 * 8);
-    L.diag = take(4 * 8 + 16);  // 4 FP64 results, then the interior kernel's status word
+    L.diag = take(4 * 8);
     // contact-line scratch: wall-row c and column heights (2 nx doubles),
     // up to kMaxDrops results (4 doubles each) and the drop count
     L.contact = take((2 * (int64_t)nx + 4 * kMaxDrops) * 8 + 16);
@@ -364,20 +364,8 @@ static int set_fields_impl(tlb_lattice* L, const double* c1, const double* c2, c
                            const double* uy, const double* p)
 {
     TLB_CUDA(L->ops->init(L->bufA(), L->cu(), L->dcls(), c1, c2, ux, uy, p, L->geo, L->prm, L->stream));
-    TLB_CUDA(cudaMemsetAsync(L->status(), 0, sizeof(int), L->stream));
     L->have_fields = true;
     return TLB_OK;
-}
-
-// The interior kernel's status word (non-zero: a staged-row wait ran out and
-// the state is not valid); synchronizes the stream.
-static int check_status(tlb_lattice* L)
-{
-    int st = 0;
-    TLB_CUDA(cudaMemcpyAsync(&st, L->status(), sizeof st, cudaMemcpyDeviceToHost, L->stream));
-    TLB_CUDA(cudaStreamSynchronize(L->stream));
-    if (st != 0) return fail(TLB_ECUDA, "a staged-row wait in the interior kernel ran out (status %d); the state is invalid", st);
-    return ok();
 }
 
 int tlb_set_fields(tlb_lattice* L, const double* c1, const double* c2, const double* ux, const double* uy,
@@ -426,7 +414,7 @@ int tlb_step(tlb_lattice* L, int64_t n)
             if (L->ev_used == kProfSlots && (rc = prof_fold(L))) return rc;
             TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used], L->stream));
         }
-        TLB_CUDA(L->ops->interior(L->bufA(), L->bufB(), L->cu(), L->dcls(), L->geo, L->prm, L->status(), L->stream));
+        TLB_CUDA(L->ops->interior(L->bufA(), L->bufB(), L->cu(), L->dcls(), L->geo, L->prm, L->stream));
         if (L->prof) TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used + 1], L->stream));
         TLB_CUDA(L->ops->wall(L->bufA(), L->bufB(), L->cu(), L->dcls(), L->dlist(), (int)L->nlist, L->geo,
                               L->prm, L->stream));
@@ -447,7 +435,7 @@ int tlb_sync(tlb_lattice* L, int64_t timeout_ms)
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         const cudaError_t e = cudaEventQuery(L->done);
-        if (e == cudaSuccess) return check_status(L);
+        if (e == cudaSuccess) return ok();
         if (e != cudaErrorNotReady) return fail(TLB_ECUDA, "stream error: %s", cudaGetErrorString(e));
         if (timeout_ms >= 0) {
             const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
@@ -514,7 +502,6 @@ int tlb_diagnostics(tlb_lattice* L, tlb_diag* out)
     out->mass[1] = h[1];
     out->mass[2] = h[2];
     out->nonfinite = (int64_t)h[3];
-    if ((rc = check_status(L))) return rc;
     if (out->nonfinite > 0) return fail(TLB_EUNSTABLE, "%lld fluid nodes hold non-finite values", (long long)out->nonfinite);
     return ok();
 }
@@ -657,7 +644,6 @@ int tlb_import_state(tlb_lattice* L, const void* host_buf, int64_t bytes)
     TLB_CUDA(cudaMemcpyAsync(L->cu(), (const char*)host_buf + a, (size_t)need - a, cudaMemcpyHostToDevice, L->stream));
     TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, a, L->stream));
     TLB_CUDA(cudaStreamSynchronize(L->stream));
-    TLB_CUDA(cudaMemsetAsync(L->status(), 0, sizeof(int), L->stream));
     L->have_fields = true;
     return ok();
 }

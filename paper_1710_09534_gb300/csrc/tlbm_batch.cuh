@@ -60,9 +60,8 @@ k_batch_interior(const LatDesc<R>* __restrict__ descs, const TileItem* __restric
             reinterpret_cast<R*>(&Ps)[threadIdx.x] = reinterpret_cast<const R*>(&d->P)[threadIdx.x];
         __syncthreads();
         const Geo g = d->g;
-        GlobalRows<S, R> src{(const S*)d->buf[parity], g.plane};
         interior_tile<S, R, BLOCK, PREFETCH, MRT>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1], (CuT<S>*)d->cu, d->cls,
-                                                  g, Ps, ti.bx, ti.by, d->rows, sh, src);
+                                             g, Ps, ti.bx, ti.by, d->rows, sh);
         __syncthreads();  // rings, parameters and item_s are reused by the next tile
     }
 }

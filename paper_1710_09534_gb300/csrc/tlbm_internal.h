@@ -46,7 +46,6 @@ struct tlb_lattice {
     void* bufB() { return ws + (cur == 0 ? lay.fB : lay.fA); }
     void* cu() { return ws + lay.cu; }
     const uint8_t* dcls() { return (const uint8_t*)(ws + lay.cls); }
-    int* status() { return (int*)(ws + lay.diag + 32); }
     const uint32_t* dlist() { return (const uint32_t*)(ws + lay.list); }
     int64_t n() const { return (int64_t)nx * ny; }
 };

@@ -335,36 +335,10 @@ struct TileRings {
 
 // One tile: strip bx (columns bx*(BLOCK-4) .. +BLOCK-5), segment by (rows
 // by*rows .. +rows-1, marching up for even by and down for odd by).
-// Where a tile reads the order-parameter populations it needs: the c sums of
-// the row being entered and the populations of the node being updated.
-// GlobalRows reads them from the distribution buffer in HBM (through L1/L2);
-// StagedRows (tlbm_staged.cuh) from rows the bulk-copy engine staged in
-// shared memory ahead of use.
-template <typename S, typename R>
-struct GlobalRows {
-    const S* __restrict__ f;
-    long long PL;
-    __device__ __forceinline__ void begin(int) {}
-    __device__ __forceinline__ void c_at(int, long long o, bool, R& a, R& b) { order_params<R>(f, PL, o, a, b); }
-    __device__ __forceinline__ bool aborted() const { return false; }
-    __device__ __forceinline__ void finish(int) {}
-    template <int K>
-    __device__ __forceinline__ void pop(int, long long o, R& f1k, R& f2k) const
-    {
-        f1k = ld_pop<R>(f, K, PL, o);
-        f2k = ld_pop<R>(f, 9 + K, PL, o);
-    }
-    __device__ __forceinline__ void lo(int, long long o, R& l1, R& l2) const
-    {
-        l1 = ld_lo<R>(f, 0, PL, o);
-        l2 = ld_lo<R>(f, 1, PL, o);
-    }
-};
-
-template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT, typename Src>
+template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT>
 __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
                                               const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
-                                              int bx, int by, int rows, TileRings<R, BLOCK>& sh, Src& src)
+                                              int bx, int by, int rows, TileRings<R, BLOCK>& sh)
 {
     R(&sc1)[5][BLOCK] = sh.c1;
     R(&sc2)[5][BLOCK] = sh.c2;
@@ -388,8 +362,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
     const int dir = (by & 1) ? -1 : 1;
     const int iters = (y1 - y0) + 4;
 
-    int it = 0;
-    for (; it < iters; it++) {
+    for (int it = 0; it < iters; it++) {
         const int yc = dir > 0 ? y0 - 2 + it : y1 + 1 - it;  // c row of this iteration
         const int ym = yc - dir;                              // mu row
         const int yu = yc - 2 * dir;                          // updated row
@@ -416,14 +389,12 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                 else in = false;
             }
             R a = R(0), b = R(0);
-            if (in) src.c_at(it, (long long)yw * g.pitch + xw, xw == xs, a, b);
+            if (in) order_params<R>(fA, PL, (long long)yw * g.pitch + xw, a, b);
             const int sl = (yc + 10) % 5;
             sc1[sl][t] = a;
             sc2[sl][t] = b;
         }
         __syncthreads();
-        if (src.aborted()) break;
-        src.begin(it);  // every thread is past the previous update: its rows may be recycled
         // 2) mu of row ym (Eq. 8 with Eq. 20b)
         if (it >= 2 && t >= 1 && t < BLOCK - 1) {
             R v1[9], v2[9];
@@ -484,9 +455,13 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         collide_all<S, R>(col, gv,
             [&](auto kc, R& f1k, R& f2k) {
                 constexpr int K = decltype(kc)::value;
-                src.template pop<K>(it, ou, f1k, f2k);
+                f1k = ld_pop<R>(fA, K, PL, ou);
+                f2k = ld_pop<R>(fA, 9 + K, PL, ou);
             },
-            [&](R& l1, R& l2) { src.lo(it, ou, l1, l2); },
+            [&](R& l1, R& l2) {
+                l1 = ld_lo<R>(fA, 0, PL, ou);
+                l2 = ld_lo<R>(fA, 1, PL, ou);
+            },
             [&](auto kc, R o1, R o2, R og) {
                 constexpr int K = decltype(kc)::value;
                 const long long d = (K == 0) ? ou : po.template dest<K>();
@@ -499,7 +474,6 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                 st_lo(fB, 1, PL, ou, l2);
             });
     }
-    src.finish(it);
 }
 
 template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT>
@@ -508,8 +482,7 @@ k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict
                 const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
 {
     __shared__ TileRings<R, BLOCK> sh;
-    GlobalRows<S, R> src{fA, g.plane};
-    interior_tile<S, R, BLOCK, PREFETCH, MRT>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh, src);
+    interior_tile<S, R, BLOCK, PREFETCH, MRT>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
 }
 
 // ---------------------------------------------------------------------------

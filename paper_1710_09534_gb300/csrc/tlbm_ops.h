@@ -12,9 +12,8 @@ struct Ops {
     int ndist;       // planes of `elem` bytes per distribution buffer
     size_t cu_elem;  // bytes per scalar of the c_i u planes
     // one time step A -> B = interior tiles (fused kernel) + near-wall list
-    // (status: device int set non-zero if a staged-row wait ran out)
     cudaError_t (*interior)(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
-                            const Prm<double>& P, int* status, cudaStream_t s);
+                            const Prm<double>& P, cudaStream_t s);
     cudaError_t (*wall)(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
                         int nlist, const Geo& g, const Prm<double>& P, cudaStream_t s);
     cudaError_t (*init)(void* fA, void* cu, const uint8_t* cls, const double* c1, const double* c2,
@@ -97,22 +96,6 @@ inline const Ops& ops_for(int precision, bool mrt)
 constexpr int kBlock64 = TLB_BLOCK64, kRows64 = TLB_ROWS64, kMinB64 = TLB_MINB64;
 constexpr int kBlock32 = TLB_BLOCK32, kRows32 = TLB_ROWS32, kMinB32 = TLB_MINB32;
 constexpr bool kPrefetch32 = TLB_PREFETCH32 != 0;
-// FP32 and 16-bit storage: the interior kernel stages rows with bulk copies,
-// kStagedPf rows ahead, at kStagedMinB* blocks per SM (shared memory bound).
-#ifndef TLB_STAGED
-#define TLB_STAGED 1
-#endif
-#ifndef TLB_STAGED_PF
-#define TLB_STAGED_PF 2
-#endif
-#ifndef TLB_STAGED_MINB32
-#define TLB_STAGED_MINB32 3
-#endif
-#ifndef TLB_STAGED_MINB16
-#define TLB_STAGED_MINB16 5
-#endif
-constexpr bool kStaged = TLB_STAGED != 0;
-constexpr int kStagedPf = TLB_STAGED_PF, kStagedMinB32 = TLB_STAGED_MINB32, kStagedMinB16 = TLB_STAGED_MINB16;
 
 
 }  // namespace tlb

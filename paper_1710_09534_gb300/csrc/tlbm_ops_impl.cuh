@@ -3,7 +3,6 @@
 #include "tlbm_batch.cuh"
 #include "tlbm_kernels.cuh"
 #include "tlbm_ops.h"
-#include "tlbm_staged.cuh"
 
 namespace tlb {
 
@@ -53,24 +52,13 @@ inline Prm<R> cast_prm(const Prm<double>& d)
 
 template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT>
 struct OpsImpl {
-    static constexpr int kStagedMinB = Store<S>::k16 ? kStagedMinB16 : kStagedMinB32;
     static cudaError_t interior(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
-                                const Prm<double>& Pd, int* status, cudaStream_t s)
+                                const Prm<double>& Pd, cudaStream_t s)
     {
         const Prm<R> P = cast_prm<R>(Pd);
         constexpr int TX = BLOCK - 4;
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + ROWS - 1) / ROWS);
-        if constexpr (Store<S>::kLo && kStaged) {
-            constexpr int bytes = StagedRing<S, BLOCK, kStagedPf>::kBytes;
-            auto k = k_step_interior_staged<S, R, BLOCK, ROWS, kStagedPf, kStagedMinB, MRT>;
-            static const cudaError_t attr =
-                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            if (attr != cudaSuccess) return attr;
-            k<<<grid, BLOCK, bytes, s>>>((const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P, status);
-        } else {
-            k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT><<<grid, BLOCK, 0, s>>>(
-                (const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P);
-        }
+        k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT><<<grid, BLOCK, 0, s>>>((const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P);
         return cudaGetLastError();
     }
     static cudaError_t wall(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
