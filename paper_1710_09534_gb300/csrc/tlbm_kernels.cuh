@@ -43,9 +43,9 @@ __device__ __forceinline__ R sum9(const R* v)
 //   double  27 FP64 planes (q = 0..8 f^1_k, 9..17 f^2_k, 18..26 g_k).
 //   float   27 FP32 planes, plus the rest populations f^1_0, f^2_0 kept as
 //           unevaluated float pairs hi + lo (hi in planes 0/9, lo in planes
-//           27/28), so that the per-node update can conserve sum_k f^i_k
-//           (Eq. 1a conserves c_i) to ~2^-48 instead of to one FP32 rounding
-//           per node and step.
+//           27/28), so that the per-node update conserves sum_k f^i_k
+//           (Eq. 1a conserves c_i) without ever rounding the O(1) rest value
+//           (see collide_all).
 //   __half, __nv_bfloat16
 //           the 25 other populations as 16-bit values after subtracting their
 //           equilibrium at rest (u = 0, mu = 0, p = 0), which is zero for every
@@ -164,41 +164,36 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = (a - (s - bb)) + (b - bb);
 }
 
-// Unevaluated pair hi + lo accumulated with TwoSum (compensated summation).
-struct FF {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(float x)
-    {
-        float e;
-        two_sum(hi, x, hi, e);
-        lo += e;
-    }
-};
-
-// (a.hi + a.lo) - (b.hi + b.lo) rounded to a normalised pair.
-__device__ __forceinline__ void ff_sub(const FF& a, const FF& b, float& hi, float& lo)
+// Rest pair (hi + lo) plus a small FP32 increment d, renormalised: TwoSum
+// keeps the rounding of hi + d, which joins lo.
+__device__ __forceinline__ void rest_add(float hi, float lo, float d, float& nhi, float& nlo)
 {
     float s, e;
-    two_sum(a.hi, -b.hi, s, e);
-    const float t = e + (a.lo - b.lo);
-    hi = s + t;
-    lo = t - (hi - s);
+    two_sum(hi, d, s, e);
+    const float t = e + lo;
+    nhi = s + t;
+    nlo = t - (nhi - s);
 }
 
 // All nine directions of one node.  load(kc, f1k, f2k) fetches the
 // pre-collision order-parameter populations of direction kc (for kc = 0 the
 // hi part), load_lo(f1lo, f2lo) the lo parts of the rest populations (FP32
-// storage), store(kc, o1, o2, og) streams the post-collision triple and
-// store_lo(o1lo, o2lo) the rest lo parts.  With FP32 storage the rest
-// population is the exact input sum minus the eight moving outputs, so the
-// stored sum_k f'^i_k equals the stored sum_k f^i_k to ~2^-48 (Eq. 1a
-// conserves c_i; sum_k f^eq_k = c_i, sum_k F_k = 0); FP64 uses the direct form.
+// and 16-bit storage), store(kc, o1, o2, og) streams the post-collision triple
+// and store_lo(o1lo, o2lo) the rest lo parts.  With paired rest populations
+// the new rest population is the old one plus sum_k (f_k - o'_k) over the
+// eight moving directions (o'_k as stored), so the stored sum_k f'^i_k equals
+// the stored sum_k f^i_k (Eq. 1a conserves c_i; sum_k f^eq_k = c_i,
+// sum_k F_k = 0) up to the FP32 rounding of those small differences and
+// their sum -- none where f_k and o'_k are within a factor 2 of each other
+// (Sterbenz), which covers near-equilibrium nodes, and exact for 16-bit
+// storage -- while the O(1) rest value itself is never rounded; FP64 uses the
+// direct form.
 template <typename S, typename R, typename Load, typename LoadLo, typename St, typename StLo>
 __device__ __forceinline__ void collide_all(const Collider<R>& col, const R gv[9], Load load, LoadLo load_lo,
                                             St store, StLo store_lo)
 {
     constexpr bool ff = Store<S>::kLo;
-    FF in1, in2, out1, out2;
+    R d1 = R(0), d2 = R(0);  // sum_k (f_k - o'_k) over the moving directions
     static_for<1, 9>([&](auto kc) {
         constexpr int K = decltype(kc)::value;
         R f1k, f2k, o1, o2, og;
@@ -207,10 +202,8 @@ __device__ __forceinline__ void collide_all(const Collider<R>& col, const R gv[9
         o1 = as_stored<S>(K, o1);
         o2 = as_stored<S>(9 + K, o2);
         if constexpr (ff) {
-            in1.add(f1k);
-            in2.add(f2k);
-            out1.add(o1);
-            out2.add(o2);
+            d1 += f1k - o1;
+            d2 += f2k - o2;
         }
         store(kc, o1, o2, og);
     });
@@ -222,13 +215,9 @@ __device__ __forceinline__ void collide_all(const Collider<R>& col, const R gv[9
         load_lo(l1, l2);
         // the collision sees the rest population as hi + lo
         col.template post<0>(f10 + l1, f20 + l2, gv[0], o1, o2, og);
-        in1.add(f10);
-        in1.add(l1);
-        in2.add(f20);
-        in2.add(l2);
         R h1, h2, lo1, lo2;
-        ff_sub(in1, out1, h1, lo1);
-        ff_sub(in2, out2, h2, lo2);
+        rest_add(f10, l1, d1, h1, lo1);
+        rest_add(f20, l2, d2, h2, lo2);
         store(k0, h1, h2, og);
         store_lo(lo1, lo2);
     } else {
@@ -263,21 +252,15 @@ __device__ __forceinline__ void collide_all(const MrtNode<R>& col, const R gv[9]
         o2[k] = as_stored<S>(9 + k, o2[k]);
     }
     if constexpr (ff) {
-        FF in1, in2, out1, out2;
+        R d1 = R(0), d2 = R(0);
 #pragma unroll
         for (int k = 1; k < 9; k++) {
-            in1.add(f1[k]);
-            in2.add(f2[k]);
-            out1.add(o1[k]);
-            out2.add(o2[k]);
+            d1 += f1[k] - o1[k];
+            d2 += f2[k] - o2[k];
         }
-        in1.add(h10);
-        in1.add(l1);
-        in2.add(h20);
-        in2.add(l2);
         R hh1, hh2, lo1, lo2;
-        ff_sub(in1, out1, hh1, lo1);
-        ff_sub(in2, out2, hh2, lo2);
+        rest_add(h10, l1, d1, hh1, lo1);
+        rest_add(h20, l2, d2, hh2, lo2);
         store(std::integral_constant<int, 0>{}, hh1, hh2, og[0]);
         store_lo(lo1, lo2);
     } else {
