@@ -50,9 +50,10 @@ KERNEL = {"fp64": "k_step_interior<double>", "fp32": "k_step_interior<float>",
 
 # FP64 arithmetic per node update of the fused interior kernel, as counted by
 # ncu (DADD + DMUL + DFMA instructions; flops with FMA = 2) on the 2048^2
-# lattice: see profiles/k_step_interior_fp64_tiled_drops_2048.md
-FP64_DP_INST_PER_NODE = 342
-FP64_FLOPS_PER_NODE = 496
+# lattice: see profiles/k_step_interior_fp64_tiled_drops_2048.md.  "uniform":
+# the update taken when all three fluids share density and viscosity (the
+# tiled-drops workload); "general": any densities and viscosities.
+FP64_DP = {"uniform": (289, 416), "general": (343, 497)}  # (DP instructions, flops) per node
 # FP64 vector unit: 152 SMs x 2 DP instructions/clk x 2.07 GHz (an FMA is 2 flops)
 FP64_DP_INST_PEAK = 152 * 2 * 2.07e9
 FP64_PEAK_TFLOPS = 2 * FP64_DP_INST_PEAK / 1e12
@@ -291,13 +292,17 @@ def run_ours(args):
     ach_gbs = interior_nodes * bytes_node / (k1_avg / 1e3) / 1e9
     hbm_frac = ach_gbs / hbm_gbs
     traffic = measured_traffic(args.precision, interior_nodes)
+    prm = w.params
+    path = "uniform" if (prm["rho1"] == prm["rho3"] == prm["rho2"] and prm["nu1"] == prm["nu3"] == prm["nu2"]) else "general"
     if args.precision == "fp64":
-        ach_tf = interior_nodes * FP64_FLOPS_PER_NODE / (k1_avg / 1e3) / 1e12
-        dp_issue = interior_nodes * FP64_DP_INST_PER_NODE / (k1_avg / 1e3) / FP64_DP_INST_PEAK
+        dp_inst, dp_flops = FP64_DP[path]
+        ach_tf = interior_nodes * dp_flops / (k1_avg / 1e3) / 1e12
+        dp_issue = interior_nodes * dp_inst / (k1_avg / 1e3) / FP64_DP_INST_PEAK
         roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(ach_tf / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 2 DP inst/clk x 2 flop x 2.07 GHz (FMA-chain probe measured 1.25-1.257 TFLOP/s)",
-                "kernel": "k_step_interior<double>",
+                "kernel": "k_step_interior<double>", "update": path,
+                "dp_inst_per_node": dp_inst, "flops_per_node": dp_flops,
                 "dp_issue_frac": round(dp_issue, 4),
                 "hbm_achieved_gbs": round(ach_gbs, 1), "hbm_peak_gbs": hbm_gbs, "hbm_frac": round(hbm_frac, 4)}
     else:
@@ -334,6 +339,19 @@ def run_ours(args):
             v_mlups = n_nodes * args.steps / (vms / 1e3) / 1e6
             variants[prec] = {"value": round(v_mlups, 2), "unit": "MLUPS",
                               "hbm_roofline_pct": round(100 * v_mlups * 1e6 * bytes_per_node(prec) / (hbm_gbs * 1e9), 2)}
+            del V
+        # the general (per-node density and viscosity) update: fluid 2 three times denser
+        for prec in ("fp64", "fp32"):
+            wd = W.tiled_drops(args.nx, args.ny)
+            wd.params.update(rho2=3.0)
+            V = T.lattice_from_workload(wd, prec)
+            V.step(args.warmup)
+            V.sync()
+            n_d = max(10, args.steps // (4 if prec == "fp64" else 1))
+            vms = time_steps(V, n_d, torch, stream)
+            variants[prec + "_density_contrast"] = {
+                "value": round(n_nodes * n_d / (vms / 1e3) / 1e6, 2), "unit": "MLUPS", "steps": n_d,
+                "update": "general (rho = 1, 3, 1)"}
             del V
         # the MRT collision option on the same lattice (FP64 and FP32 storage)
         for prec in ("fp64", "fp32"):

@@ -347,6 +347,19 @@ int tlb_set_params(tlb_lattice* L, const tlb_params* p)
     P.gx = p->gx;
     P.gy = p->gy;
     P.lid_u = p->lid_u;
+    // equal densities and viscosities: constants of the uniform-property update
+    P.uni = (p->rho1 == p->rho3 && p->rho2 == p->rho3 && p->nu1 == p->nu3 && p->nu2 == p->nu3) ? 1.0 : 0.0;
+    {
+        const double itg = 1.0 / (3.0 * p->nu3 + 0.5);
+        P.inv_rho3 = 1.0 / p->rho3;
+        P.inv_taug3 = itg;
+        P.omtg3 = 1.0 - itg;
+        P.kG3 = 1.0 - 0.5 * itg;
+        for (int c = 0; c < 2; c++) {
+            P.Rw3[c] = w[c] * p->rho3 * itg;
+            P.Kw3[c] = w[c] * P.kG3;
+        }
+    }
     P.mrt = mrt ? 1.0 : 0.0;
     P.mrt_s_f = mrt ? p->mrt_s_f : 1.0;
     P.mrt_s_g = mrt ? p->mrt_s_g : 1.0;

@@ -67,6 +67,11 @@ struct Prm {
     R mrt;            // 1: MRT collision (moment basis below), 0: BGK
     R mrt_s_f;        // MRT rate of the non-flux moments of f^i
     R mrt_s_g;        // MRT rate of the energy moments of g
+    // equal densities and equal viscosities (rho_i = rho_3, nu_i = nu_3): the
+    // constants the uniform-property update uses instead of per-node values
+    R uni;            // 1 when both hold
+    R inv_rho3, inv_taug3, omtg3, kG3;  // 1/rho, 1/tau_g, 1 - 1/tau_g, 1 - 1/(2 tau_g)
+    R Rw3[2], Kw3[2];                   // rho w / tau_g, w (1 - 1/(2 tau_g)) per class
 };
 
 // Site of (x, y), possibly outside the lattice; on an inside site sets the
@@ -169,7 +174,10 @@ __device__ __forceinline__ R density(const Prm<R>& P, R c1, R c2)
     return fma(c2, P.drho[1], fma(c1, P.drho[0], P.rho[2]));
 }
 
-template <typename R>
+// UNI (equal densities and viscosities): grad rho, u.grad rho and F_a vanish
+// identically and rho, tau_g are constants, so those terms are skipped (the
+// general form would add exact zeros).
+template <bool UNI = false, typename R>
 __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m, const R g[9], Hydro<R>& h)
 {
     const R mu3 = -fma(P.l3_l1, m.mu1, P.l3_l2 * m.mu2);
@@ -177,22 +185,32 @@ __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m,
     // F_s = sum_i mu_i grad c_i with grad c3 = -grad c1 - grad c2; G = rho g
     h.Ftx = fma(q1, m.g1x, fma(q2, m.g2x, m.rho * P.gx));
     h.Fty = fma(q1, m.g1y, fma(q2, m.g2y, m.rho * P.gy));
-    h.grx = fma(P.drho[0], m.g1x, P.drho[1] * m.g2x);
-    h.gry = fma(P.drho[0], m.g1y, P.drho[1] * m.g2y);
     const R g57 = g[5] - g[7], g86 = g[8] - g[6];
     const R mx = (g[1] - g[3]) + (g57 + g86);
     const R my = (g[2] - g[4]) + (g57 - g86);
-    const R inv_rho = rcp(m.rho);
-    h.ux = fma(R(0.5), h.Ftx, mx) * inv_rho;
-    h.uy = fma(R(0.5), h.Fty, my) * inv_rho;
-    h.usq = fma(h.ux, h.ux, h.uy * h.uy);
     const R sumg = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
-    // p = cs^2/(1 - w0) [sum_{k!=0} g_k + u.grad rho / 2 + rho s_0(u)], s_0 = -w0 u.u / (2 cs^2)
-    const R ug = fma(h.ux, h.grx, h.uy * h.gry);
-    h.p = R(0.6) * fma(R(-2.0 / 3.0) * m.rho, h.usq, fma(R(0.5), ug, sumg));
-    h.a = fma(P.aM[0], m.lm1, P.aM[1] * m.lm2);
-    const R nu = fma(m.c2, P.dnu[1], fma(m.c1, P.dnu[0], P.nu[2]));
-    h.inv_taug = rcp(fma(R(3), nu, R(0.5)));
+    if constexpr (UNI) {
+        h.grx = h.gry = R(0);
+        h.ux = fma(R(0.5), h.Ftx, mx) * P.inv_rho3;
+        h.uy = fma(R(0.5), h.Fty, my) * P.inv_rho3;
+        h.usq = fma(h.ux, h.ux, h.uy * h.uy);
+        h.p = R(0.6) * fma(R(-2.0 / 3.0) * m.rho, h.usq, sumg);
+        h.a = R(0);
+        h.inv_taug = P.inv_taug3;
+    } else {
+        h.grx = fma(P.drho[0], m.g1x, P.drho[1] * m.g2x);
+        h.gry = fma(P.drho[0], m.g1y, P.drho[1] * m.g2y);
+        const R inv_rho = rcp(m.rho);
+        h.ux = fma(R(0.5), h.Ftx, mx) * inv_rho;
+        h.uy = fma(R(0.5), h.Fty, my) * inv_rho;
+        h.usq = fma(h.ux, h.ux, h.uy * h.uy);
+        // p = cs^2/(1 - w0) [sum_{k!=0} g_k + u.grad rho / 2 + rho s_0(u)], s_0 = -w0 u.u / (2 cs^2)
+        const R ug = fma(h.ux, h.grx, h.uy * h.gry);
+        h.p = R(0.6) * fma(R(-2.0 / 3.0) * m.rho, h.usq, fma(R(0.5), ug, sumg));
+        h.a = fma(P.aM[0], m.lm1, P.aM[1] * m.lm2);
+        const R nu = fma(m.c2, P.dnu[1], fma(m.c1, P.dnu[0], P.nu[2]));
+        h.inv_taug = rcp(fma(R(3), nu, R(0.5)));
+    }
 }
 
 // Per-node precomputation of the BGK update (Eqs. 1a, 1b, 2a, 2b, 4, 11a,
@@ -202,7 +220,7 @@ __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m,
 //   g^eq_k / tau_g = w (3p + rho q_k) / tau_g,  q_k = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u
 //   G_k = w (1 - 1/(2 tau_g)) [q_k (e - u).H + (e - u).T] + 3 w e.F_a,
 //   H = grad rho + 3 (F_s + G), T = 3 (F_s + G)   (s_k = w q_k)
-template <typename R>
+template <typename R, bool UNI = false>
 struct Collider {
     R eu[4];            // e.u for +x, +y, (1,1), (1,-1)
     R A1[2], A2[2];     // f^eq / tau constant parts per class, with the source folded in below
@@ -245,33 +263,46 @@ struct Collider {
         F2[3] = P.sw[1][1] * (d2x - d2y);
         // hydrodynamics
         const R itg = h.inv_taug;
-        omtg = R(1) - itg;
-        const R kG = fma(R(-0.5), itg, R(1));
         t0 = R(-1.5) * h.usq;
         const R Tx = R(3) * h.Ftx, Ty = R(3) * h.Fty;
-        const R Hx = h.grx + Tx, Hy = h.gry + Ty;
-        H[0] = Hx;
-        H[1] = Hy;
-        H[2] = Hx + Hy;
-        H[3] = Hx - Hy;
         T[0] = Tx;
         T[1] = Ty;
         T[2] = Tx + Ty;
         T[3] = Tx - Ty;
-        uH = fma(h.ux, Hx, h.uy * Hy);
         uT = fma(h.ux, Tx, h.uy * Ty);
-        const R za = R(3.0 / 9.0) * h.a, zd = R(3.0 / 36.0) * h.a;  // 3 w_c a, F_a = u a
-        Z[0] = za * eu[0];
-        Z[1] = za * eu[1];
-        Z[2] = zd * eu[2];
-        Z[3] = zd * eu[3];
-        const R p3 = R(3) * h.p * itg, ri = m.rho * itg;
+        const R p3 = R(3) * h.p * itg;
         Pw[0] = R(1.0 / 9.0) * p3;
         Pw[1] = R(1.0 / 36.0) * p3;
-        Rw[0] = R(1.0 / 9.0) * ri;
-        Rw[1] = R(1.0 / 36.0) * ri;
-        Kw[0] = R(1.0 / 9.0) * kG;
-        Kw[1] = R(1.0 / 36.0) * kG;
+        R kG;
+        if constexpr (UNI) {
+            // H = T (grad rho = 0), F_a = 0; tau_g and rho are constants
+            omtg = P.omtg3;
+            kG = P.kG3;
+            Rw[0] = P.Rw3[0];
+            Rw[1] = P.Rw3[1];
+            Kw[0] = P.Kw3[0];
+            Kw[1] = P.Kw3[1];
+            uH = uT;
+        } else {
+            omtg = R(1) - itg;
+            kG = fma(R(-0.5), itg, R(1));
+            const R Hx = h.grx + Tx, Hy = h.gry + Ty;
+            H[0] = Hx;
+            H[1] = Hy;
+            H[2] = Hx + Hy;
+            H[3] = Hx - Hy;
+            uH = fma(h.ux, Hx, h.uy * Hy);
+            const R za = R(3.0 / 9.0) * h.a, zd = R(3.0 / 36.0) * h.a;  // 3 w_c a, F_a = u a
+            Z[0] = za * eu[0];
+            Z[1] = za * eu[1];
+            Z[2] = zd * eu[2];
+            Z[3] = zd * eu[3];
+            const R ri = m.rho * itg;
+            Rw[0] = R(1.0 / 9.0) * ri;
+            Rw[1] = R(1.0 / 36.0) * ri;
+            Kw[0] = R(1.0 / 9.0) * kG;
+            Kw[1] = R(1.0 / 36.0) * kG;
+        }
         // k = 0: g^eq_0 = 3p (w0 - 1) + rho w0 t0; G_0 = -w0 kG (t0 u.H + u.T)
         const R w0 = R(4.0 / 9.0);
         const R geq0 = fma(m.rho * w0, t0, R(3) * (w0 - R(1)) * h.p);
@@ -292,10 +323,15 @@ struct Collider {
             const R q = fma(e, fma(R(4.5), e, R(3)), t0);
             o1 = fma(omt1, f1k, fma(B1[W], e, fma(s, F1[C], A1[W])));
             o2 = fma(omt2, f2k, fma(B2[W], e, fma(s, F2[C], A2[W])));
-            const R X = fma(s, H[C], -uH);
             const R Y = fma(s, T[C], -uT);
-            const R Gk = fma(Kw[W], fma(q, X, Y), s * Z[C]);
-            og = fma(omtg, gk, fma(Rw[W], q, Pw[W]) + Gk);
+            if constexpr (UNI) {
+                // X = Y: G_k = w kG (q + 1) (e - u).T
+                og = fma(omtg, gk, fma(Kw[W], fma(q, Y, Y), fma(Rw[W], q, Pw[W])));
+            } else {
+                const R X = fma(s, H[C], -uH);
+                const R Gk = fma(Kw[W], fma(q, X, Y), s * Z[C]);
+                og = fma(omtg, gk, fma(Rw[W], q, Pw[W]) + Gk);
+            }
         }
     }
 };

@@ -188,8 +188,8 @@ __device__ __forceinline__ void rest_add(float hi, float lo, float d, float& nhi
 // (Sterbenz), which covers near-equilibrium nodes, and exact for 16-bit
 // storage -- while the O(1) rest value itself is never rounded; FP64 uses the
 // direct form.
-template <typename S, typename R, typename Load, typename LoadLo, typename St, typename StLo>
-__device__ __forceinline__ void collide_all(const Collider<R>& col, const R gv[9], Load load, LoadLo load_lo,
+template <typename S, typename R, bool UNI, typename Load, typename LoadLo, typename St, typename StLo>
+__device__ __forceinline__ void collide_all(const Collider<R, UNI>& col, const R gv[9], Load load, LoadLo load_lo,
                                             St store, StLo store_lo)
 {
     constexpr bool ff = Store<S>::kLo;
@@ -272,9 +272,10 @@ __device__ __forceinline__ void collide_all(const MrtNode<R>& col, const R gv[9]
     });
 }
 
-// Per-node collision data of the BGK (MRT = false) or MRT update.
-template <bool MRT, typename R>
-using CollideOf = typename std::conditional<MRT, MrtNode<R>, Collider<R>>::type;
+// Per-node collision data of the BGK (MRT = false) or MRT update; UNI: the
+// uniform-property form of the BGK update.
+template <bool MRT, typename R, bool UNI = false>
+using CollideOf = typename std::conditional<MRT, MrtNode<R>, Collider<R, UNI>>::type;
 
 // Destinations of the push from an interior node (x, y): the neighbouring
 // columns and rows, wrapped on a periodic axis (interior nodes never reach a
@@ -318,7 +319,7 @@ struct TileRings {
 
 // One tile: strip bx (columns bx*(BLOCK-4) .. +BLOCK-5), segment by (rows
 // by*rows .. +rows-1, marching up for even by and down for odd by).
-template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT>
+template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT, bool UNI = false>
 __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
                                               const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
                                               int bx, int by, int rows, TileRings<R, BLOCK>& sh)
@@ -416,7 +417,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
             grad9(v2, m.g2x, m.g2y);
             m.lm1 = lap9(w1);
             m.lm2 = lap9(w2);
-            m.rho = density(P, m.c1, m.c2);
+            m.rho = UNI ? P.rho[2] : density(P, m.c1, m.c2);
         }
         if (!PREFETCH) {
 #pragma unroll
@@ -425,14 +426,14 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
             for (int q = 0; q < 4; q++) cp[q] = R(cu[q * PL + ou]);
         }
         Hydro<R> h;
-        hydro_from_g(P, m, gv, h);
+        hydro_from_g<UNI>(P, m, gv, h);
         // Eq. 19: d/dt (c_i u) against the stored product of the previous step
         const R c1ux = m.c1 * h.ux, c1uy = m.c1 * h.uy, c2ux = m.c2 * h.ux, c2uy = m.c2 * h.uy;
         cu[0 * PL + ou] = CuT<S>(c1ux);
         cu[1 * PL + ou] = CuT<S>(c1uy);
         cu[2 * PL + ou] = CuT<S>(c2ux);
         cu[3 * PL + ou] = CuT<S>(c2uy);
-        CollideOf<MRT, R> col;
+        CollideOf<MRT, R, UNI> col;
         col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
         const PushOffsets po(g, xs, yu);
         collide_all<S, R>(col, gv,
@@ -459,13 +460,13 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
     }
 }
 
-template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT>
+template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT, bool UNI>
 __global__ void __launch_bounds__(BLOCK, MINB)
 k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
                 const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
 {
     __shared__ TileRings<R, BLOCK> sh;
-    interior_tile<S, R, BLOCK, PREFETCH, MRT>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
+    interior_tile<S, R, BLOCK, PREFETCH, MRT, UNI>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
 }
 
 // ---------------------------------------------------------------------------

@@ -47,6 +47,15 @@ inline Prm<R> cast_prm(const Prm<double>& d)
     r.mrt = R(d.mrt);
     r.mrt_s_f = R(d.mrt_s_f);
     r.mrt_s_g = R(d.mrt_s_g);
+    r.uni = R(d.uni);
+    r.inv_rho3 = R(d.inv_rho3);
+    r.inv_taug3 = R(d.inv_taug3);
+    r.omtg3 = R(d.omtg3);
+    r.kG3 = R(d.kG3);
+    for (int c = 0; c < 2; c++) {
+        r.Rw3[c] = R(d.Rw3[c]);
+        r.Kw3[c] = R(d.Kw3[c]);
+    }
     return r;
 }
 
@@ -58,7 +67,13 @@ struct OpsImpl {
         const Prm<R> P = cast_prm<R>(Pd);
         constexpr int TX = BLOCK - 4;
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + ROWS - 1) / ROWS);
-        k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT><<<grid, BLOCK, 0, s>>>((const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P);
+        // equal densities and viscosities: the uniform-property update
+        if (Pd.uni != 0.0)
+            k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT, true><<<grid, BLOCK, 0, s>>>(
+                (const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P);
+        else
+            k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT, false><<<grid, BLOCK, 0, s>>>(
+                (const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P);
         return cudaGetLastError();
     }
     static cudaError_t wall(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
