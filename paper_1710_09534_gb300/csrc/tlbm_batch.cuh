@@ -60,8 +60,14 @@ k_batch_interior(const LatDesc<R>* __restrict__ descs, const TileItem* __restric
             reinterpret_cast<R*>(&Ps)[threadIdx.x] = reinterpret_cast<const R*>(&d->P)[threadIdx.x];
         __syncthreads();
         const Geo g = d->g;
-        interior_tile<S, R, BLOCK, PREFETCH, MRT>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1], (CuT<S>*)d->cu, d->cls,
-                                             g, Ps, ti.bx, ti.by, d->rows, sh);
+        // members with equal densities and viscosities take the uniform-property
+        // update, as they do when stepped alone (the branch is uniform per tile)
+        if (Ps.uni != R(0))
+            interior_tile<S, R, BLOCK, PREFETCH, MRT, true>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1],
+                                                            (CuT<S>*)d->cu, d->cls, g, Ps, ti.bx, ti.by, d->rows, sh);
+        else
+            interior_tile<S, R, BLOCK, PREFETCH, MRT, false>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1],
+                                                             (CuT<S>*)d->cu, d->cls, g, Ps, ti.bx, ti.by, d->rows, sh);
         __syncthreads();  // rings, parameters and item_s are reused by the next tile
     }
 }
