@@ -53,7 +53,9 @@ KERNEL = {"fp64": "k_step_interior<double>", "fp32": "k_step_interior<float>",
 # lattice: see profiles/k_step_interior_fp64_tiled_drops_2048.md.  "uniform":
 # the update taken when all three fluids share density and viscosity (the
 # tiled-drops workload); "general": any densities and viscosities.
-FP64_DP = {"uniform": (289, 416), "general": (343, 497)}  # (DP instructions, flops) per node
+# (DADD + DMUL + DFMA instructions, flops with an FMA as 2) per interior node, from
+# the ncu captures of k_step_interior<double> (profiles/k_step_interior_fp64_*.md)
+FP64_DP = {"uniform": (264, 394), "general": (343, 497)}
 # FP64 vector unit: 152 SMs x 2 DP instructions/clk x 2.07 GHz (an FMA is 2 flops)
 FP64_DP_INST_PEAK = 152 * 2 * 2.07e9
 FP64_PEAK_TFLOPS = 2 * FP64_DP_INST_PEAK / 1e12
@@ -82,11 +84,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--inplace", action="store_true",
+                    help="step the main lattice with in-place (AA-pattern) streaming; the interior time then "
+                         "includes the order-parameter pass")
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--variants", default="fp32,fp16,bf16", help="comma list of extra precisions to time")
+    ap.add_argument("--variants", default="fp32,fp16,bf16",
+                    help="comma list of extra precisions to time; 'none' also skips the density-contrast, MRT and in-place variants")
     ap.add_argument("--impact-steps", type=int, default=200,
                     help="steps timed on the 1024x2048 cylinder-impact workload per precision (0: skip)")
     ap.add_argument("--batch-count", type=int, default=256, help="lattices in the batched workload (0: skip)")
@@ -264,7 +270,7 @@ def run_ours(args):
     import workloads as W
     stream = torch.cuda.current_stream()
     w = W.tiled_drops(args.nx, args.ny)
-    L = T.lattice_from_workload(w, args.precision)
+    L = T.lattice_from_workload(w, args.precision, inplace=args.inplace)
     n_nodes = w.nx * w.ny
     L.step(args.warmup)
     L.sync()
@@ -316,6 +322,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "precision": args.precision,
+                   "streaming": "in-place (AA pattern)" if args.inplace else "two buffers",
                    "storage": {"fp64": "f64", "fp32": "f32", "fp16": "f16 (shifted, x2^12) + f32 rest pairs",
                                "bf16": "bf16 (shifted) + f32 rest pairs"}[args.precision],
                    "l2": f"state {bytes_node * n_nodes / 1e9:.2f} GB moved per step > 129 MB L2 (no flush needed)",
@@ -324,13 +331,18 @@ def run_ours(args):
         "hbm_roofline_pct": round(100 * mlups / ws * 1e6 * bytes_node / (hbm_gbs * 1e9), 2),
         "roofline": roof,
         "kernel_ms": {"interior_avg": round(k1_avg, 4), "wall_avg": round(k2_ms / max(k2_n, 1), 4)},
-        "gpu_launches": int(k1_n + k2_n),
+        # two buffers: interior + near-wall kernel per step; in place: the
+        # order-parameter pass, the interior, the lid row (if any) and the
+        # near-wall kernel, plus the streaming swap after an odd step count
+        "gpu_launches": int(k1_n + k2_n) if not args.inplace else
+        int(args.steps * (3 + (w.edges[3] == 3)) + args.steps % 2),
         "clocks": clk,
     }
     if rank == 0 and not args.no_e2e:
         result["e2e"] = e2e(L, w, args, torch, T)
     if rank == 0:
         variants = {}
+        extras = args.variants != "none"  # "none": no variant of any kind (short profiling runs)
         for prec in [v for v in args.variants.split(",") if v and v not in ("none", args.precision)]:
             V = T.lattice_from_workload(w, prec)
             V.step(args.warmup)
@@ -341,7 +353,7 @@ def run_ours(args):
                               "hbm_roofline_pct": round(100 * v_mlups * 1e6 * bytes_per_node(prec) / (hbm_gbs * 1e9), 2)}
             del V
         # the general (per-node density and viscosity) update: fluid 2 three times denser
-        for prec in ("fp64", "fp32"):
+        for prec in ("fp64", "fp32") if extras else ():
             wd = W.tiled_drops(args.nx, args.ny)
             wd.params.update(rho2=3.0)
             V = T.lattice_from_workload(wd, prec)
@@ -354,7 +366,7 @@ def run_ours(args):
                 "update": "general (rho = 1, 3, 1)"}
             del V
         # the MRT collision option on the same lattice (FP64 and FP32 storage)
-        for prec in ("fp64", "fp32"):
+        for prec in ("fp64", "fp32") if extras else ():
             wm = W.tiled_drops(args.nx, args.ny)
             wm.params.update(collision=1.0, mrt_s_f=1.2, mrt_s_g=1.2)
             V = T.lattice_from_workload(wm, prec)
@@ -365,6 +377,19 @@ def run_ours(args):
             v_mlups = n_nodes * n_mrt / (vms / 1e3) / 1e6
             variants[prec + "_mrt"] = {"value": round(v_mlups, 2), "unit": "MLUPS", "steps": n_mrt,
                                        "collision": "MRT (s_f = s_g = 1.2)"}
+            del V
+        # in-place (AA-pattern) streaming: one distribution buffer plus the
+        # order-parameter planes, the extra order-parameter pass in every step
+        for prec in ("fp64", "fp32", "fp16") if extras else ():
+            V = T.lattice_from_workload(w, prec, inplace=True)
+            V.step(args.warmup)
+            V.sync()
+            n_ip = max(10, args.steps // (4 if prec == "fp64" else 1)) // 2 * 2
+            vms = time_steps(V, n_ip, torch, stream)
+            variants[prec + "_inplace"] = {
+                "value": round(n_nodes * n_ip / (vms / 1e3) / 1e6, 2), "unit": "MLUPS", "steps": n_ip,
+                "workspace_bytes": int(V.workspace.numel()),
+                "two_buffer_workspace_bytes": int(T.load_library().tlb_workspace_bytes(w.nx, w.ny, T.PRECISIONS[prec]))}
             del V
         result["variants"] = variants
         if args.impact_steps > 0:

@@ -60,6 +60,26 @@ typedef struct tlb_batch tlb_batch;
  * pairs hi + lo. */
 enum { TLB_FP64 = 0, TLB_FP32 = 1, TLB_FP16 = 2, TLB_BF16 = 3 };
 
+/* In-place streaming, OR-ed into the precision of tlb_workspace_bytes and
+ * tlb_create_lattice (beyond the paper, which does not discuss storage): the
+ * lattice keeps ONE distribution buffer instead of two and streams in place
+ * with the AA pattern -- an even step reads each node's own slots k and
+ * writes f'_k into its own slot k-bar; an odd step reads f_k from slot k-bar
+ * of x - e_k and writes f'_k into slot k of x + e_k (the half-way
+ * bounce-back of Eq. 44 becomes own-slot reads and writes on wall links).
+ * Because the chemical potentials need the order parameters of neighbours
+ * (Eqs. 8, 20), a first pass per step writes c_1, c_2 of every node to two
+ * planes of the arithmetic type, which the update then reads.  Workspace:
+ * 0.57 (FP64, FP32) and 0.61 (FP16, BF16) of the two-buffer size at
+ * 2048x2048; each step also moves the order-parameter pass.  The results equal
+ * the two-buffer update's up to rounding order.  Every call sees the usual
+ * layout (a call that ends on an even step streams its result in place), so
+ * all reads, diagnostics and state export work as for two buffers; such a
+ * lattice cannot join a batch (TLB_EINVAL from tlb_batch_add).  tlb_set_fields
+ * stages the host arrays through the order-parameter planes in bands of rows
+ * (one set-up launch per band). */
+enum { TLB_INPLACE = 0x100 };
+
 enum { TLB_EDGE_PERIODIC = 0, TLB_EDGE_WETTING = 1, TLB_EDGE_NEUTRAL = 2, TLB_EDGE_LID = 3 };
 
 /* Solid mask values for tlb_set_geometry. */
@@ -123,11 +143,14 @@ typedef struct {
 } tlb_diag;
 
 /* Bytes of device workspace one lattice needs (the state of Eqs. 1a/1b
- * double-buffered, the c_i u planes of Eq. 19, node classes and the near-wall
- * list).  Returns a negative TLB_E* code for invalid sizes or precision. */
+ * double-buffered -- one buffer plus the order-parameter planes with
+ * TLB_INPLACE -- the c_i u planes of Eq. 19, node classes and the near-wall
+ * list).  precision: TLB_FP64 .. TLB_BF16, optionally | TLB_INPLACE.  Returns a
+ * negative TLB_E* code for invalid sizes or precision. */
 int64_t tlb_workspace_bytes(int nx, int ny, int precision);
 
-/* Create a lattice of nx*ny nodes (nx, ny >= 3 and <= 32768).  dev_workspace:
+/* Create a lattice of nx*ny nodes (nx, ny >= 3 and <= 32768) with the
+ * storage precision (| TLB_INPLACE for in-place streaming).  dev_workspace:
  * caller-owned device memory of at least tlb_workspace_bytes, 256-byte aligned.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).  *out receives
  * the handle.  The lattice starts all-fluid; parameters and fields must be set
@@ -168,7 +191,10 @@ int tlb_set_fields_device(tlb_lattice *lat, const double *c1, const double *c2,
                           const double *ux, const double *uy, const double *p);
 
 /* Advance n >= 0 time steps, asynchronously on the stream: per step one fused
- * interior kernel and one near-wall kernel.  TLB_ESTATE before set_fields. */
+ * interior kernel and one near-wall kernel (in-place lattices: the
+ * order-parameter pass, the interior kernel, the lid row if any, the
+ * near-wall kernel, and after a last even step the in-place streaming).
+ * TLB_ESTATE before set_fields. */
 int tlb_step(tlb_lattice *lat, int64_t n);
 
 /* Wait for the stream with a deadline (timeout_ms < 0: no deadline).

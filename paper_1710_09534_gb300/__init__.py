@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtlbm.so")
 
 FP64, FP32, FP16, BF16 = 0, 1, 2, 3
+INPLACE = 0x100  # OR-ed into the precision: one distribution buffer, in-place streaming
 EDGE_PERIODIC, EDGE_WETTING, EDGE_NEUTRAL, EDGE_LID = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
 FIELDS = ("c1", "c2", "c3", "rho", "ux", "uy", "p", "mu1", "mu2", "mu3")
@@ -137,22 +138,25 @@ class Lattice:
     Arrays are [ny, nx] (x fastest).
     """
 
-    def __init__(self, nx: int, ny: int, precision="fp64", edges=(0, 0, 1, 2), stream=None, device=None):
+    def __init__(self, nx: int, ny: int, precision="fp64", edges=(0, 0, 1, 2), stream=None, device=None,
+                 inplace=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("tlbm needs a CUDA device; there is no CPU fallback")
         self.lib = load_library()
         self.nx, self.ny = int(nx), int(ny)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.inplace = bool(inplace)
+        flags = self.precision | (INPLACE if self.inplace else 0)
         self.edges = tuple(int(e) for e in edges)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            nbytes = _check(self.lib.tlb_workspace_bytes(self.nx, self.ny, self.precision))
+            nbytes = _check(self.lib.tlb_workspace_bytes(self.nx, self.ny, flags))
             self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
             h = ctypes.c_void_p()
             e = (ctypes.c_int32 * 4)(*self.edges)
-            _check(self.lib.tlb_create_lattice(self.nx, self.ny, self.precision, e,
+            _check(self.lib.tlb_create_lattice(self.nx, self.ny, flags, e,
                                                ctypes.c_void_p(self.workspace.data_ptr()),
                                                int(nbytes), ctypes.c_void_p(self.stream.cuda_stream),
                                                ctypes.byref(h)))
@@ -284,9 +288,9 @@ def theta12_from(s12, s13, s23, th13, th23) -> float:
     return out.value
 
 
-def lattice_from_workload(w, precision="fp64", stream=None) -> Lattice:
+def lattice_from_workload(w, precision="fp64", stream=None, inplace=False) -> Lattice:
     """Create and initialise a Lattice from a ``workloads.Workload``."""
-    L = Lattice(w.nx, w.ny, precision, w.edges, stream=stream)
+    L = Lattice(w.nx, w.ny, precision, w.edges, stream=stream, inplace=inplace)
     L.set_geometry(w.mask)
     L.set_params(w.params)
     L.set_fields(w.c1, w.c2, w.ux, w.uy, w.p)

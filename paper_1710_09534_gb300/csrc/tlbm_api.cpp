@@ -52,12 +52,22 @@ constexpr int kMaxDrops = 256;   // contact-line results kept per call
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 
-bool precision_ok(int precision) { return precision >= TLB_FP64 && precision <= TLB_BF16; }
+// precision argument: TLB_FP64 .. TLB_BF16, optionally | TLB_INPLACE
+bool precision_ok(int precision)
+{
+    const int base = precision & ~TLB_INPLACE;
+    return base >= TLB_FP64 && base <= TLB_BF16;
+}
 
+// Rows of set-up input one pass of the in-place tlb_set_fields stages in the
+// order-parameter planes: c1, c2 with 3 halo rows on each side, ux, uy, p.
+int band_rows(int64_t stage_doubles, int nx) { return (int)((stage_doubles / nx - 12) / 5); }
 
-tlb::Layout layout_for(int nx, int ny, int precision)
+tlb::Layout layout_for(int nx, int ny, int precision_flags)
 {
     tlb::Layout L;
+    const int precision = precision_flags & ~TLB_INPLACE;
+    L.inplace = (precision_flags & TLB_INPLACE) != 0;
     L.pitch = (int)align_up(nx, 32);
     L.plane = (int64_t)L.pitch * ny;
     const int64_t es = (int64_t)tlb::elem_for(precision);
@@ -69,8 +79,14 @@ tlb::Layout layout_for(int nx, int ny, int precision)
     };
     const int nd = tlb::ndist_for(precision);
     L.fA = take(nd * L.plane * es);
-    L.fB = take(nd * L.plane * es);
+    L.fB = L.inplace ? L.fA : take(nd * L.plane * es);
     L.cu = take(4 * L.plane * (int64_t)tlb::cu_elem_for(precision));
+    if (L.inplace) {
+        // c_1, c_2 planes of the arithmetic type; at least one staged set-up row
+        const int64_t relem = precision == TLB_FP64 ? 8 : 4;
+        L.cpl_bytes = std::max<int64_t>(2 * L.plane * relem, 17 * (int64_t)nx * 8);
+        L.cpl = take(L.cpl_bytes);
+    }
     L.cls = take(L.plane);
     L.list = take((int64_t)nx * ny * 4);
     L.part = take((int64_t)kMassParts * 4 * 8);
@@ -216,12 +232,12 @@ int tlb_create_lattice(int nx, int ny, int precision, const int32_t edges[4], vo
     auto* L = new tlb_lattice;
     L->nx = nx;
     L->ny = ny;
-    L->precision = precision;
+    L->precision = precision & ~TLB_INPLACE;
     for (int e = 0; e < 4; e++) L->edge[e] = edges[e];
     L->stream = (cudaStream_t)cuda_stream;
     L->ws = (char*)dev_workspace;
     L->lay = lay;
-    L->ops = &tlb::ops_for(precision, false);
+    L->ops = &tlb::ops_for(L->precision, false);
     L->geo.nx = nx;
     L->geo.ny = ny;
     L->geo.pitch = lay.pitch;
@@ -381,6 +397,58 @@ static int set_fields_impl(tlb_lattice* L, const double* c1, const double* c2, c
     return TLB_OK;
 }
 
+// In-place lattices have no spare buffer: the host inputs go through the
+// order-parameter planes in bands of rows (c1, c2 with the 3 halo rows the
+// set-up window needs on each side, wrapped on a periodic y axis; ux, uy, p
+// of the band itself), one set-up launch per band.
+static int set_fields_banded(tlb_lattice* L, const double* c1, const double* c2, const double* ux,
+                             const double* uy, const double* p)
+{
+    const int nx = L->nx, ny = L->ny;
+    const int64_t stage_doubles = L->lay.cpl_bytes / 8;
+    const int b = std::min(ny, band_rows(stage_doubles, nx));
+    if (b < 1) return fail(TLB_ECUDA, "order-parameter planes too small to stage a row");
+    double* st = (double*)L->cpl();
+    const size_t row = (size_t)nx * 8;
+    const bool wrap = L->edge[2] == TLB_EDGE_PERIODIC;
+    for (int y0 = 0; y0 < ny; y0 += b) {
+        const int y1 = std::min(ny, y0 + b), rows = (y1 - y0) + 6, y_b = y0 - 3;
+        double* sc1 = st;
+        double* sc2 = st + (size_t)rows * nx;
+        double* su = sc2 + (size_t)rows * nx;
+        double* sv = su + (size_t)(y1 - y0) * nx;
+        double* sp = sv + (size_t)(y1 - y0) * nx;
+        // runs of band rows that are consecutive lattice rows (a wrap splits them)
+        for (int r = 0; r < rows;) {
+            int y = y_b + r, n = rows - r;
+            if (y < 0) {
+                n = std::min(n, -y);
+                y += ny;
+            } else if (y >= ny) {
+                y -= ny;
+            } else {
+                n = std::min(n, ny - y);
+            }
+            n = std::min(n, ny - y);
+            if (wrap || (y_b + r >= 0 && y_b + r < ny)) {  // rows beyond a wall or lid edge are never read
+                TLB_CUDA(cudaMemcpyAsync(sc1 + (size_t)r * nx, c1 + (size_t)y * nx, (size_t)n * row,
+                                         cudaMemcpyHostToDevice, L->stream));
+                TLB_CUDA(cudaMemcpyAsync(sc2 + (size_t)r * nx, c2 + (size_t)y * nx, (size_t)n * row,
+                                         cudaMemcpyHostToDevice, L->stream));
+            }
+            r += n;
+        }
+        const size_t band = (size_t)(y1 - y0) * row;
+        TLB_CUDA(cudaMemcpyAsync(su, ux + (size_t)y0 * nx, band, cudaMemcpyHostToDevice, L->stream));
+        TLB_CUDA(cudaMemcpyAsync(sv, uy + (size_t)y0 * nx, band, cudaMemcpyHostToDevice, L->stream));
+        if (p) TLB_CUDA(cudaMemcpyAsync(sp, p + (size_t)y0 * nx, band, cudaMemcpyHostToDevice, L->stream));
+        TLB_CUDA(L->ops->init_rows(L->bufA(), L->cu(), L->dcls(), sc1, sc2, su, sv, p ? sp : nullptr, L->geo, L->prm,
+                                   y0, y1, y_b, rows, L->stream));
+    }
+    L->have_fields = true;
+    return TLB_OK;
+}
+
 int tlb_set_fields(tlb_lattice* L, const double* c1, const double* c2, const double* ux, const double* uy,
                    const double* p)
 {
@@ -388,6 +456,12 @@ int tlb_set_fields(tlb_lattice* L, const double* c1, const double* c2, const dou
     if (rc) return rc;
     if (!L->have_params) return fail(TLB_ESTATE, "set_params first");
     if (!c1 || !c2 || !ux || !uy) return fail(TLB_EINVAL, "c1, c2, ux, uy are required");
+    if (L->lay.inplace) {
+        rc = set_fields_banded(L, c1, c2, ux, uy, p);
+        if (rc) return rc;
+        TLB_CUDA(cudaStreamSynchronize(L->stream));
+        return ok();
+    }
     // stage the inputs in the spare distribution buffer, build the state,
     // then clear the spare buffer (solid nodes and lid slots must read zero)
     const size_t N = (size_t)L->n();
@@ -411,7 +485,37 @@ int tlb_set_fields_device(tlb_lattice* L, const double* c1, const double* c2, co
     if (!c1 || !c2 || !ux || !uy) return fail(TLB_EINVAL, "c1, c2, ux, uy are required");
     rc = set_fields_impl(L, c1, c2, ux, uy, p);
     if (rc) return rc;
-    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(L->ops->ndist * L->lay.plane * L->ops->elem), L->stream));
+    if (!L->lay.inplace)
+        TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, (size_t)(L->ops->ndist * L->lay.plane * L->ops->elem), L->stream));
+    return ok();
+}
+
+// In-place lattices: steps in even/odd pairs (an odd step leaves the usual
+// layout), a last even step followed by the in-place streaming swap.
+static int step_inplace(tlb_lattice* L, int64_t n)
+{
+    int rc;
+    const bool lid = L->edge[3] == TLB_EDGE_LID;
+    for (int64_t s = 0; s < n; s++) {
+        const int odd = (int)(s & 1);
+        if (L->prof) {
+            if (L->ev_used == kProfSlots && (rc = prof_fold(L))) return rc;
+            TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used], L->stream));
+        }
+        TLB_CUDA(L->ops->csum_ip(L->bufA(), L->cpl(), L->dcls(), L->geo, odd, L->stream));
+        TLB_CUDA(L->ops->interior_ip(L->bufA(), L->cu(), L->cpl(), L->dcls(), L->geo, L->prm, odd, L->stream));
+        if (L->prof) TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used + 1], L->stream));
+        if (lid)
+            TLB_CUDA(L->ops->wall_ip(L->bufA(), L->cu(), L->cpl(), L->dcls(), L->dlist(), (int)L->nlist, L->geo,
+                                     L->prm, odd, 1, L->stream));
+        TLB_CUDA(L->ops->wall_ip(L->bufA(), L->cu(), L->cpl(), L->dcls(), L->dlist(), (int)L->nlist, L->geo, L->prm,
+                                 odd, 0, L->stream));
+        if (!odd && s == n - 1) TLB_CUDA(L->ops->swap_ip(L->bufA(), L->dcls(), L->geo, L->stream));
+        if (L->prof) {
+            TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used + 2], L->stream));
+            L->ev_used++;
+        }
+    }
     return ok();
 }
 
@@ -422,6 +526,7 @@ int tlb_step(tlb_lattice* L, int64_t n)
     if (n < 0) return fail(TLB_EINVAL, "negative step count");
     if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "set_params and set_fields before step");
     if (L->batch) return fail(TLB_ESTATE, "lattice belongs to a batch: step the batch");
+    if (L->lay.inplace) return step_inplace(L, n);
     for (int64_t s = 0; s < n; s++) {
         if (L->prof) {
             if (L->ev_used == kProfSlots && (rc = prof_fold(L))) return rc;
@@ -475,11 +580,13 @@ int tlb_read_fields(tlb_lattice* L, uint32_t mask, double* host_out)
     if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "no state yet");
     if (!host_out || (mask & ~(uint32_t)TLB_F_ALL) || !mask) return fail(TLB_EINVAL, "bad output or field mask");
     // stage in the spare distribution buffer, as many FP64 planes per pass as
-    // it holds (8 or more: it has >= 70 bytes per node in every precision)
+    // it holds (8 or more: it has >= 70 bytes per node in every precision);
+    // in-place lattices stage in the order-parameter planes (1 or 2 per pass)
     const size_t N = (size_t)L->n();
-    const size_t spare = (size_t)(L->ops->ndist * L->lay.plane * L->ops->elem);
+    const size_t spare = L->lay.inplace ? (size_t)L->lay.cpl_bytes
+                                        : (size_t)(L->ops->ndist * L->lay.plane * L->ops->elem);
     const int per_pass = (int)std::min<size_t>(10, spare / (N * 8));
-    double* stage = (double*)L->bufB();
+    double* stage = (double*)(L->lay.inplace ? L->cpl() : L->bufB());
     size_t done = 0;
     for (int q = 0; q < 10;) {
         uint32_t sub = 0;
@@ -494,7 +601,7 @@ int tlb_read_fields(tlb_lattice* L, uint32_t mask, double* host_out)
         TLB_CUDA(cudaMemcpyAsync(host_out + done * N, stage, (size_t)cnt * N * 8, cudaMemcpyDeviceToHost, L->stream));
         done += (size_t)cnt;
     }
-    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, spare, L->stream));
+    if (!L->lay.inplace) TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, spare, L->stream));
     TLB_CUDA(cudaStreamSynchronize(L->stream));
     return ok();
 }
@@ -655,7 +762,7 @@ int tlb_import_state(tlb_lattice* L, const void* host_buf, int64_t bytes)
     const size_t a = (size_t)L->ops->ndist * L->lay.plane * L->ops->elem;
     TLB_CUDA(cudaMemcpyAsync(L->bufA(), host_buf, a, cudaMemcpyHostToDevice, L->stream));
     TLB_CUDA(cudaMemcpyAsync(L->cu(), (const char*)host_buf + a, (size_t)need - a, cudaMemcpyHostToDevice, L->stream));
-    TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, a, L->stream));
+    if (!L->lay.inplace) TLB_CUDA(cudaMemsetAsync(L->bufB(), 0, a, L->stream));
     TLB_CUDA(cudaStreamSynchronize(L->stream));
     L->have_fields = true;
     return ok();

@@ -278,6 +278,7 @@ int tlb_batch_add(tlb_batch* B, tlb_lattice* L)
     if (!L) return err(TLB_EINVAL, "null lattice");
     if (L->batch) return err(TLB_EINVAL, "lattice already belongs to a batch");
     if (L->precision != B->precision) return err(TLB_EINVAL, "lattice precision differs from the batch's");
+    if (L->lay.inplace) return err(TLB_EINVAL, "in-place lattices are stepped alone, not in a batch");
     if (L->device != B->device) return err(TLB_EINVAL, "lattice lives on another device");
     if ((int)B->members.size() >= B->max_lattices) return err(TLB_ENOMEM, "batch is full (%d lattices)", B->max_lattices);
     // work queued on the lattice's own stream must be done before the batch stream touches it

@@ -13,6 +13,8 @@ struct Layout {
     int pitch = 0;
     int64_t plane = 0;  // elements
     int64_t fA = 0, fB = 0, cu = 0, cls = 0, list = 0, part = 0, diag = 0, contact = 0, total = 0;
+    bool inplace = false;  // one distribution buffer (fB unused) and the order-parameter planes cpl
+    int64_t cpl = 0, cpl_bytes = 0;
 };
 
 }  // namespace tlb
@@ -43,7 +45,8 @@ struct tlb_lattice {
     int64_t prof_n[2] = {0, 0};
 
     void* bufA() { return ws + (cur == 0 ? lay.fA : lay.fB); }
-    void* bufB() { return ws + (cur == 0 ? lay.fB : lay.fA); }
+    void* bufB() { return lay.inplace ? nullptr : ws + (cur == 0 ? lay.fB : lay.fA); }
+    void* cpl() { return ws + lay.cpl; }
     void* cu() { return ws + lay.cu; }
     const uint8_t* dcls() { return (const uint8_t*)(ws + lay.cls); }
     const uint32_t* dlist() { return (const uint32_t*)(ws + lay.list); }

@@ -88,25 +88,34 @@ __device__ __forceinline__ float* rest_region(S* f, long long PL)
     return reinterpret_cast<float*>(f + 27 * PL);
 }
 
+// Load through the read-only path (NC: the buffer is not written during the
+// kernel) or a plain coherent load (the in-place update writes what it reads).
+template <bool NC, typename T>
+__device__ __forceinline__ T ld_any(const T* p)
+{
+    if constexpr (NC) return __ldg(p);
+    else return *p;
+}
+
 // Population q (0..26) of node offset o, as the arithmetic type R (for the
 // rest populations of the paired formats: the hi part).
-template <typename R, typename S>
+template <typename R, bool NC = true, typename S>
 __device__ __forceinline__ R ld_pop(const S* __restrict__ f, int q, long long PL, long long o)
 {
     if constexpr (Store<S>::k16) {
-        if (q == 0 || q == 9) return R(__ldg(rest_region(f, PL) + (q == 9 ? PL : 0) + o));
+        if (q == 0 || q == 9) return R(ld_any<NC>(rest_region(f, PL) + (q == 9 ? PL : 0) + o));
         constexpr float inv = 1.0f / float(1 << Store<S>::kScaleExp);
-        return R(dec16(S{}, __ldg(reinterpret_cast<const unsigned short*>(f) + q * PL + o)) * inv);
+        return R(dec16(S{}, ld_any<NC>(reinterpret_cast<const unsigned short*>(f) + q * PL + o)) * inv);
     } else {
-        return R(__ldg(f + q * PL + o));
+        return R(ld_any<NC>(f + q * PL + o));
     }
 }
 // lo part of rest population i (0: f^1_0, 1: f^2_0); zero for FP64
-template <typename R, typename S>
+template <typename R, bool NC = true, typename S>
 __device__ __forceinline__ R ld_lo(const S* __restrict__ f, int i, long long PL, long long o)
 {
-    if constexpr (Store<S>::k16) return R(__ldg(rest_region(f, PL) + (2 + i) * PL + o));
-    else if constexpr (Store<S>::kLo) return R(__ldg(f + (27 + i) * PL + o));
+    if constexpr (Store<S>::k16) return R(ld_any<NC>(rest_region(f, PL) + (2 + i) * PL + o));
+    else if constexpr (Store<S>::kLo) return R(ld_any<NC>(f + (27 + i) * PL + o));
     else return R(0);
 }
 // The value population q takes once stored (16-bit formats round; others keep it)
@@ -270,6 +279,63 @@ __device__ __forceinline__ void collide_all(const MrtNode<R>& col, const R gv[9]
         constexpr int K = decltype(kc)::value;
         store(kc, o1[K], o2[K], og[K]);
     });
+}
+
+// In-place form of the BGK collide_all: the post-collision populations of
+// direction k land in the location the input of direction k-bar came from
+// (and vice versa), so the directions go in opposite pairs, both inputs read
+// before either output is written.  Otherwise the same update.
+template <typename S, typename R, bool UNI, typename Load, typename LoadLo, typename St, typename StLo>
+__device__ __forceinline__ void collide_all_inplace(const Collider<R, UNI>& col, const R gv[9], Load load,
+                                                    LoadLo load_lo, St store, StLo store_lo)
+{
+    constexpr bool ff = Store<S>::kLo;
+    R d1 = R(0), d2 = R(0);
+    static_for<0, 4>([&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        constexpr int K = P == 0 ? 1 : (P == 1 ? 2 : (P == 2 ? 5 : 6));
+        constexpr int KB = opp(K);
+        std::integral_constant<int, K> kc;
+        std::integral_constant<int, KB> kbc;
+        R a1, a2, b1, b2, oa1, oa2, oag, ob1, ob2, obg;
+        load(kc, a1, a2);
+        load(kbc, b1, b2);
+        col.template post<K>(a1, a2, gv[K], oa1, oa2, oag);
+        col.template post<KB>(b1, b2, gv[KB], ob1, ob2, obg);
+        oa1 = as_stored<S>(K, oa1);
+        oa2 = as_stored<S>(9 + K, oa2);
+        ob1 = as_stored<S>(KB, ob1);
+        ob2 = as_stored<S>(9 + KB, ob2);
+        if constexpr (ff) {
+            d1 += (a1 - oa1) + (b1 - ob1);
+            d2 += (a2 - oa2) + (b2 - ob2);
+        }
+        store(kc, oa1, oa2, oag);
+        store(kbc, ob1, ob2, obg);
+    });
+    std::integral_constant<int, 0> k0;
+    R f10, f20, o1, o2, og;
+    load(k0, f10, f20);
+    if constexpr (ff) {
+        R l1, l2;
+        load_lo(l1, l2);
+        col.template post<0>(f10 + l1, f20 + l2, gv[0], o1, o2, og);
+        R h1, h2, lo1, lo2;
+        rest_add(f10, l1, d1, h1, lo1);
+        rest_add(f20, l2, d2, h2, lo2);
+        store(k0, h1, h2, og);
+        store_lo(lo1, lo2);
+    } else {
+        col.template post<0>(f10, f20, gv[0], o1, o2, og);
+        store(k0, o1, o2, og);
+    }
+}
+// MRT already reads all nine populations before writing any.
+template <typename S, typename R, typename Load, typename LoadLo, typename St, typename StLo>
+__device__ __forceinline__ void collide_all_inplace(const MrtNode<R>& col, const R gv[9], Load load, LoadLo load_lo,
+                                                    St store, StLo store_lo)
+{
+    collide_all<S, R>(col, gv, load, load_lo, store, store_lo);
 }
 
 // Per-node collision data of the BGK (MRT = false) or MRT update; UNI: the
@@ -579,16 +645,34 @@ struct DistFetch {
     }
 };
 
+// c_1, c_2 from dense FP64 row arrays holding rows y_b .. y_b + rows - 1 of
+// the lattice (y_b may be negative; rows outside 0 .. ny-1 hold the wrapped
+// rows of a periodic y axis); the whole lattice is y_b = 0, rows = ny.
 template <typename R>
 struct FieldFetch {
     const double* c1;
     const double* c2;
-    int nx, pitch;
+    int nx, pitch, ny, y_b, rows;
     __device__ __forceinline__ void operator()(long long off, R& a, R& b) const
     {
         const long long y = off / pitch, x = off - y * pitch;
-        a = R(c1[y * nx + x]);
-        b = R(c2[y * nx + x]);
+        long long r = y - y_b;
+        if (r < 0) r += ny;
+        if (r >= rows) r -= ny;
+        a = R(c1[r * nx + x]);
+        b = R(c2[r * nx + x]);
+    }
+};
+
+// c_1, c_2 from the two order-parameter planes of the in-place update
+template <typename R>
+struct PlaneFetch {
+    const R* c;  // c_1 plane, then c_2 plane (pitched)
+    long long PL;
+    __device__ __forceinline__ void operator()(long long off, R& a, R& b) const
+    {
+        a = c[off];
+        b = c[PL + off];
     }
 };
 
@@ -751,21 +835,25 @@ k_step_wall(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ c
 }
 
 // ---------------------------------------------------------------------------
-// Set-up: f = f^eq(c, mu(c), u), g = g^eq(p, rho(c), u), cu = c u.
-// Inputs are dense [ny][nx] FP64 device arrays.
+// Set-up: f = f^eq(c, mu(c), u), g = g^eq(p, rho(c), u), cu = c u, for rows
+// y0 .. y0 + gridDim.y - 1.  ux, uy, p are dense FP64 rows from y0 on; c1, c2
+// dense FP64 rows y_b .. y_b + rows - 1 (wrapped), which must cover the
+// radius-2 window of every updated row (radius 3 around a lid row, whose
+// window is centred on the row below).  The whole lattice: y0 = y_b = 0,
+// rows = ny.
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
 __global__ void k_init(S* __restrict__ fA, CuT<S>* __restrict__ cu, const uint8_t* __restrict__ cls,
                        const double* __restrict__ c1, const double* __restrict__ c2,
                        const double* __restrict__ ux, const double* __restrict__ uy,
-                       const double* __restrict__ p, Geo g, Prm<R> P)
+                       const double* __restrict__ p, Geo g, Prm<R> P, int y0, int y_b, int rows)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+    const int y = y0 + blockIdx.y;
     if (x >= g.nx) return;
     const long long PL = g.plane;
     const long long o = (long long)y * g.pitch + x;
-    const long long n = (long long)y * g.nx + x;
+    const long long n = (long long)blockIdx.y * g.nx + x;  // ux, uy, p hold rows y0 ..
     const int kind = cls[o] & CLS_KIND_MASK;
     st_lo(fA, 0, PL, o, R(0));
     st_lo(fA, 1, PL, o, R(0));
@@ -774,7 +862,7 @@ __global__ void k_init(S* __restrict__ fA, CuT<S>* __restrict__ cu, const uint8_
         for (int q = 0; q < 4; q++) cu[q * PL + o] = CuT<S>(0);
         return;
     }
-    FieldFetch<R> fetch{c1, c2, g.nx, g.pitch};
+    FieldFetch<R> fetch{c1, c2, g.nx, g.pitch, g.ny, y_b, rows};
     Macro<R> m;
     window_macros(g, cls, P, x, kind == ST_LID ? y - 1 : y, fetch, m);
     const R u = R(ux[n]), v = R(uy[n]);

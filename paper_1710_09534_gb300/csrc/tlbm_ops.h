@@ -41,6 +41,22 @@ struct Ops {
     // FP64 mass totals into out[4] via nparts block partials in part[4*nparts]
     cudaError_t (*mass)(const void* fA, const uint8_t* cls, double* part, int nparts, double* out,
                         const Geo& g, cudaStream_t s);
+    // set-up of rows y0 .. y1-1 from dense FP64 rows (see k_init)
+    cudaError_t (*init_rows)(void* fA, void* cu, const uint8_t* cls, const double* c1, const double* c2,
+                             const double* ux, const double* uy, const double* p, const Geo& g,
+                             const Prm<double>& P, int y0, int y1, int y_b, int rows, cudaStream_t s);
+    // In-place (AA-pattern) step of parity odd = 0/1 on the one buffer f:
+    // csum_ip writes c_1, c_2 into the planes cpl (2 planes of relem bytes),
+    // interior_ip the fused interior update, wall_ip the lid nodes (lid = 1)
+    // or the other near-wall nodes (lid = 0); swap_ip streams the layout an
+    // even step leaves into the usual one.
+    size_t relem;
+    cudaError_t (*csum_ip)(const void* f, void* cpl, const uint8_t* cls, const Geo& g, int odd, cudaStream_t s);
+    cudaError_t (*interior_ip)(void* f, void* cu, const void* cpl, const uint8_t* cls, const Geo& g,
+                               const Prm<double>& P, int odd, cudaStream_t s);
+    cudaError_t (*wall_ip)(void* f, void* cu, const void* cpl, const uint8_t* cls, const uint32_t* list, int nlist,
+                           const Geo& g, const Prm<double>& P, int odd, int lid, cudaStream_t s);
+    cudaError_t (*swap_ip)(void* f, const uint8_t* cls, const Geo& g, cudaStream_t s);
 };
 
 // Storage precisions (the TLB_FP64 .. TLB_BF16 values of the C ABI):

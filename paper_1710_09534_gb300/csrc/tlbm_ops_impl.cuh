@@ -1,6 +1,7 @@
 // Launchers of one precision; included by tlbm_f64.cu and tlbm_f32.cu.
 #pragma once
 #include "tlbm_batch.cuh"
+#include "tlbm_inplace.cuh"
 #include "tlbm_kernels.cuh"
 #include "tlbm_ops.h"
 
@@ -91,7 +92,7 @@ struct OpsImpl {
     {
         const Prm<R> P = cast_prm<R>(Pd);
         dim3 grid((g.nx + 127) / 128, g.ny);
-        k_init<S, R><<<grid, 128, 0, s>>>((S*)fA, (CuT<S>*)cu, cls, c1, c2, ux, uy, p, g, P);
+        k_init<S, R><<<grid, 128, 0, s>>>((S*)fA, (CuT<S>*)cu, cls, c1, c2, ux, uy, p, g, P, 0, 0, g.ny);
         return cudaGetLastError();
     }
     static cudaError_t read(const void* fA, const uint8_t* cls, double* out, uint32_t mask, const Geo& g,
@@ -160,10 +161,73 @@ struct OpsImpl {
         d->P = cast_prm<R>(P);
         d->rows = rows;
     }
+    static cudaError_t init_rows(void* fA, void* cu, const uint8_t* cls, const double* c1, const double* c2,
+                                 const double* ux, const double* uy, const double* p, const Geo& g,
+                                 const Prm<double>& Pd, int y0, int y1, int y_b, int rows, cudaStream_t s)
+    {
+        const Prm<R> P = cast_prm<R>(Pd);
+        if (y1 <= y0) return cudaSuccess;
+        dim3 grid((g.nx + 127) / 128, y1 - y0);
+        k_init<S, R><<<grid, 128, 0, s>>>((S*)fA, (CuT<S>*)cu, cls, c1, c2, ux, uy, p, g, P, y0, y_b, rows);
+        return cudaGetLastError();
+    }
+    static cudaError_t csum_ip(const void* f, void* cpl, const uint8_t* cls, const Geo& g, int odd, cudaStream_t s)
+    {
+        dim3 grid((g.pitch + 127) / 128, g.ny);
+        if (odd) k_csum<S, R, true><<<grid, 128, 0, s>>>((const S*)f, (R*)cpl, cls, g);
+        else k_csum<S, R, false><<<grid, 128, 0, s>>>((const S*)f, (R*)cpl, cls, g);
+        return cudaGetLastError();
+    }
+    // resident blocks of the in-place interior kernel: its FP32 form holds all
+    // 18 order-parameter populations at once, which needs 128 registers
+    static constexpr int kMinBIp = std::is_same<R, float>::value ? 4 : MINB;
+    template <bool UNI, bool ODD>
+    static void launch_interior_ip(void* f, void* cu, const void* cpl, const uint8_t* cls, const Geo& g,
+                                   const Prm<R>& P, cudaStream_t s)
+    {
+        constexpr int TX = BLOCK - 4;
+        dim3 grid((g.nx + TX - 1) / TX, (g.ny + ROWS - 1) / ROWS);
+        k_step_interior_ip<S, R, BLOCK, ROWS, PREFETCH, kMinBIp, MRT, UNI, ODD><<<grid, BLOCK, 0, s>>>(
+            (S*)f, (CuT<S>*)cu, (const R*)cpl, cls, g, P);
+    }
+    static cudaError_t interior_ip(void* f, void* cu, const void* cpl, const uint8_t* cls, const Geo& g,
+                                   const Prm<double>& Pd, int odd, cudaStream_t s)
+    {
+        const Prm<R> P = cast_prm<R>(Pd);
+        if (Pd.uni != 0.0) {
+            if (odd) launch_interior_ip<true, true>(f, cu, cpl, cls, g, P, s);
+            else launch_interior_ip<true, false>(f, cu, cpl, cls, g, P, s);
+        } else {
+            if (odd) launch_interior_ip<false, true>(f, cu, cpl, cls, g, P, s);
+            else launch_interior_ip<false, false>(f, cu, cpl, cls, g, P, s);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t wall_ip(void* f, void* cu, const void* cpl, const uint8_t* cls, const uint32_t* list,
+                               int nlist, const Geo& g, const Prm<double>& Pd, int odd, int lid, cudaStream_t s)
+    {
+        const Prm<R> P = cast_prm<R>(Pd);
+        if (nlist <= 0) return cudaSuccess;
+        const int blocks = (nlist + 127) / 128;
+        if (odd)
+            k_step_wall_ip<S, R, MRT, true><<<blocks, 128, 0, s>>>((S*)f, (CuT<S>*)cu, (const R*)cpl, cls, list, nlist,
+                                                                  g, P, lid);
+        else
+            k_step_wall_ip<S, R, MRT, false><<<blocks, 128, 0, s>>>((S*)f, (CuT<S>*)cu, (const R*)cpl, cls, list,
+                                                                   nlist, g, P, lid);
+        return cudaGetLastError();
+    }
+    static cudaError_t swap_ip(void* f, const uint8_t* cls, const Geo& g, cudaStream_t s)
+    {
+        dim3 grid((g.nx + 127) / 128, g.ny);
+        k_swap<S><<<grid, 128, 0, s>>>((S*)f, cls, g);
+        return cudaGetLastError();
+    }
     static const Ops& table()
     {
         static const Ops t{sizeof(S), Store<S>::kPlanes, sizeof(CuT<S>), &interior, &wall, &init, &read, &contact, &film, &batch_step,
-                          &batch_blocks_per_sm, sizeof(LatDesc<R>), &fill_desc, &mass};
+                          &batch_blocks_per_sm, sizeof(LatDesc<R>), &fill_desc, &mass, &init_rows, sizeof(R),
+                          &csum_ip, &interior_ip, &wall_ip, &swap_ip};
         return t;
     }
 };

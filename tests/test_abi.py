@@ -49,6 +49,19 @@ def test_workspace_size_validation(lib):
     assert b64 > b32
 
 
+def test_inplace_workspace_is_smaller(lib):
+    """One distribution buffer plus two order-parameter planes instead of two
+    buffers: 0.57 (FP64, FP32) and 0.61 (16-bit) of the two-buffer workspace
+    at 2048x2048; an unknown precision with the flag is still rejected."""
+    import paper_1710_09534_gb300 as T
+    for p, ratio in ((T.FP64, 0.58), (T.FP32, 0.58), (T.FP16, 0.62), (T.BF16, 0.62)):
+        two = lib.tlb_workspace_bytes(2048, 2048, p)
+        one = lib.tlb_workspace_bytes(2048, 2048, p | T.INPLACE)
+        assert 0 < one < ratio * two, (p, one, two)
+    assert lib.tlb_workspace_bytes(64, 64, 4 | T.INPLACE) == T.EINVAL
+    assert lib.tlb_workspace_bytes(2, 64, T.FP32 | T.INPLACE) == T.EINVAL
+
+
 def test_theta12_helper_applies_eq39(lib):
     import paper_1710_09534_gb300 as T
     th = T.theta12_from(1e-3, 1e-3, 1e-3, 90.0, 120.0)
