@@ -45,6 +45,8 @@ k_batch_interior(const LatDesc<R>* __restrict__ descs, const TileItem* __restric
                  BatchCounters* __restrict__ ctr, int parity)
 {
     __shared__ TileRings<R, BLOCK> sh;
+    constexpr bool kStash = kStashPops && std::is_same<R, float>::value && !MRT;
+    __shared__ PopStash<R, kStash ? BLOCK : 1> stash;
     __shared__ Prm<R> Ps;
     __shared__ int item_s;
     static_assert(sizeof(Prm<R>) % sizeof(R) == 0 && sizeof(Prm<R>) / sizeof(R) <= BLOCK, "params fit one pass");
@@ -62,12 +64,15 @@ k_batch_interior(const LatDesc<R>* __restrict__ descs, const TileItem* __restric
         const Geo g = d->g;
         // members with equal densities and viscosities take the uniform-property
         // update, as they do when stepped alone (the branch is uniform per tile)
+        auto* st = reinterpret_cast<PopStash<R, BLOCK>*>(&stash);  // used only when kStash
         if (Ps.uni != R(0))
-            interior_tile<S, R, BLOCK, PREFETCH, MRT, true>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1],
-                                                            (CuT<S>*)d->cu, d->cls, g, Ps, ti.bx, ti.by, d->rows, sh);
+            interior_tile<S, R, BLOCK, PREFETCH, MRT, true, kStash>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1],
+                                                                    (CuT<S>*)d->cu, d->cls, g, Ps, ti.bx, ti.by,
+                                                                    d->rows, sh, st);
         else
-            interior_tile<S, R, BLOCK, PREFETCH, MRT, false>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1],
-                                                             (CuT<S>*)d->cu, d->cls, g, Ps, ti.bx, ti.by, d->rows, sh);
+            interior_tile<S, R, BLOCK, PREFETCH, MRT, false, kStash>((const S*)d->buf[parity], (S*)d->buf[parity ^ 1],
+                                                                     (CuT<S>*)d->cu, d->cls, g, Ps, ti.bx, ti.by,
+                                                                     d->rows, sh, st);
         __syncthreads();  // rings, parameters and item_s are reused by the next tile
     }
 }

@@ -383,12 +383,28 @@ struct TileRings {
     R m1[3][BLOCK], m2[3][BLOCK];  // mu rings (row r in slot (r + 9) % 3)
 };
 
+// Per-thread copy of the 18 order-parameter populations (and the two rest lo
+// parts) that phase 1 reads for the c sums of a row, kept until the same
+// thread updates that row two iterations later (row r in slot (r + 9) % 3).
+template <typename R, int BLOCK>
+struct PopStash {
+    R v[3][20][BLOCK];
+};
+// Used by the FP32-arithmetic BGK interior kernels (single lattices and
+// batches): 5% faster FP32 and 2% faster FP16 on the 2048^2 lattice than
+// re-reading the populations through the cache.
+#ifndef TLB_STASH32
+#define TLB_STASH32 1
+#endif
+constexpr bool kStashPops = TLB_STASH32 != 0;
+
 // One tile: strip bx (columns bx*(BLOCK-4) .. +BLOCK-5), segment by (rows
 // by*rows .. +rows-1, marching up for even by and down for odd by).
-template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT, bool UNI = false>
+template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT, bool UNI = false, bool STASH = false>
 __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
                                               const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
-                                              int bx, int by, int rows, TileRings<R, BLOCK>& sh)
+                                              int bx, int by, int rows, TileRings<R, BLOCK>& sh,
+                                              PopStash<R, BLOCK>* stash = nullptr)
 {
     R(&sc1)[5][BLOCK] = sh.c1;
     R(&sc2)[5][BLOCK] = sh.c2;
@@ -439,7 +455,26 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                 else in = false;
             }
             R a = R(0), b = R(0);
-            if (in) order_params<R>(fA, PL, (long long)yw * g.pitch + xw, a, b);
+            if (in) {
+                const long long oc = (long long)yw * g.pitch + xw;
+                if constexpr (STASH) {
+                    R v[18];
+#pragma unroll
+                    for (int k = 0; k < 18; k++) v[k] = ld_pop<R>(fA, k, PL, oc);
+                    const R l1 = ld_lo<R>(fA, 0, PL, oc), l2 = ld_lo<R>(fA, 1, PL, oc);
+                    R(&st)[20][BLOCK] = stash->v[(yc + 9) % 3];
+#pragma unroll
+                    for (int k = 0; k < 18; k++) st[k][t] = v[k];
+                    st[18][t] = l1;
+                    st[19][t] = l2;
+                    v[0] += l1;
+                    v[9] += l2;
+                    a = sum9(v);
+                    b = sum9(v + 9);
+                } else {
+                    order_params<R>(fA, PL, oc, a, b);
+                }
+            }
             const int sl = (yc + 10) % 5;
             sc1[sl][t] = a;
             sc2[sl][t] = b;
@@ -502,15 +537,26 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         CollideOf<MRT, R, UNI> col;
         col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
         const PushOffsets po(g, xs, yu);
+        const int su = (yu + 9) % 3;
         collide_all<S, R>(col, gv,
             [&](auto kc, R& f1k, R& f2k) {
                 constexpr int K = decltype(kc)::value;
-                f1k = ld_pop<R>(fA, K, PL, ou);
-                f2k = ld_pop<R>(fA, 9 + K, PL, ou);
+                if constexpr (STASH) {
+                    f1k = stash->v[su][K][t];
+                    f2k = stash->v[su][9 + K][t];
+                } else {
+                    f1k = ld_pop<R>(fA, K, PL, ou);
+                    f2k = ld_pop<R>(fA, 9 + K, PL, ou);
+                }
             },
             [&](R& l1, R& l2) {
-                l1 = ld_lo<R>(fA, 0, PL, ou);
-                l2 = ld_lo<R>(fA, 1, PL, ou);
+                if constexpr (STASH) {
+                    l1 = stash->v[su][18][t];
+                    l2 = stash->v[su][19][t];
+                } else {
+                    l1 = ld_lo<R>(fA, 0, PL, ou);
+                    l2 = ld_lo<R>(fA, 1, PL, ou);
+                }
             },
             [&](auto kc, R o1, R o2, R og) {
                 constexpr int K = decltype(kc)::value;
@@ -532,7 +578,13 @@ k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict
                 const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
 {
     __shared__ TileRings<R, BLOCK> sh;
-    interior_tile<S, R, BLOCK, PREFETCH, MRT, UNI>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
+    if constexpr (kStashPops && std::is_same<R, float>::value && !MRT) {
+        __shared__ PopStash<R, BLOCK> stash;
+        interior_tile<S, R, BLOCK, PREFETCH, MRT, UNI, true>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh,
+                                                            &stash);
+    } else {
+        interior_tile<S, R, BLOCK, PREFETCH, MRT, UNI>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
+    }
 }
 
 // ---------------------------------------------------------------------------
