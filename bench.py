@@ -214,15 +214,27 @@ def oracle_run(w, steps, warmup=0):
     return w.nx * w.ny * steps / dt / 1e6, dt, oracle.threads()
 
 
-def cpu_baseline(w, budget_s=12.0):
-    """The oracle on a bounded sample (~budget_s seconds of host work)."""
+def cpu_baseline(w, budget_s=12.0, single_s=5.0):
+    """The oracle on a bounded sample (~budget_s seconds of host work on all
+    cores), and the same sample on one core (~single_s seconds) beside it."""
+    import oracle
     s = sample_workload(w)
     _, t1, _ = oracle_run(s, 2)
     steps = max(1, min(5000, int(budget_s / max(t1 / 2, 1e-3))))
     mlups, dt, thr = oracle_run(s, steps)
-    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
-            "sample": f"{s.nx}x{s.ny} bottom strip of the {w.nx}x{w.ny} lattice, {steps} steps, "
-                      f"{dt:.1f} s, FP64 C oracle with OpenMP over nodes"}
+    out = {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
+           "sample": f"{s.nx}x{s.ny} bottom strip of the {w.nx}x{w.ny} lattice, {steps} steps, "
+                     f"{dt:.1f} s, FP64 C oracle with OpenMP over nodes"}
+    oracle.set_threads(1)
+    try:
+        _, t1, _ = oracle_run(s, 1)
+        steps1 = max(1, int(single_s / max(t1, 1e-3)))
+        m1, dt1, _ = oracle_run(s, steps1)
+    finally:
+        oracle.set_threads(thr)
+    out["single_core"] = {"value": round(m1, 3), "unit": "MLUPS", "cores": 1,
+                          "sample": f"the same strip, {steps1} steps, {dt1:.1f} s"}
+    return out
 
 
 def run_reference(args):

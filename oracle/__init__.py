@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).argtypes = [ctypes.c_int]
             getattr(L, name).restype = ctypes.c_int
         L.orc_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_mrt_matrix.argtypes = [dp]
         L.orc_mrt_inverse.argtypes = [dp]
         L.orc_mrt_relax.argtypes = [dp, dp, dp, dp, dp]
@@ -240,6 +241,11 @@ def src_g(k, taug, ux, uy, grx, gry, Ftx, Fty, Fax, Fay):
 def threads() -> int:
     """OpenMP threads the oracle's passes run on."""
     return lib().orc_threads()
+
+
+def set_threads(n: int) -> None:
+    """Run the oracle's passes on n OpenMP threads (results do not depend on n)."""
+    lib().orc_set_threads(int(n))
 
 
 def mrt_matrices():

@@ -222,6 +222,17 @@ int orc_threads(void)
 #endif
 }
 
+/* Set the number of OpenMP threads of the passes (no effect without OpenMP);
+ * results do not depend on it (each pass writes per-node outputs only). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ---- MRT option (reading R8) ---------------------------------------------- */
 /* Moment matrix: rows are 1, e = -4 + 3|e_k|^2, eps = 4 - 21/2 |e_k|^2 + 9/2 |e_k|^4,
  * j_x = e_kx, q_x = (-5 + 3|e_k|^2) e_kx, j_y, q_y, p_xx = e_kx^2 - e_ky^2, p_xy = e_kx e_ky. */
