@@ -95,6 +95,8 @@ def parse():
                     help="comma list of extra precisions to time; 'none' also skips the density-contrast, MRT and in-place variants")
     ap.add_argument("--impact-steps", type=int, default=200,
                     help="steps timed on the 1024x2048 cylinder-impact workload per precision (0: skip)")
+    ap.add_argument("--shear-steps", type=int, default=20000,
+                    help="steps of the 512x256 sheared compound drop, FP64 and FP32 (0: skip)")
     ap.add_argument("--batch-count", type=int, default=256, help="lattices in the batched workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--serve-count", type=int, default=40, help="requests in the served workload (0: skip)")
@@ -406,6 +408,8 @@ def run_ours(args):
         result["variants"] = variants
         if args.impact_steps > 0:
             result["impact"] = impact(args, torch, T)
+        if args.shear_steps > 0:
+            result["shear"] = shear(args, torch, T)
         if args.batch_count > 0:
             result["batched"] = batched(args, torch, T)
         if args.serve_count > 0:
@@ -484,6 +488,34 @@ def impact(args, torch, T):
         ms = time_steps(L, args.impact_steps, torch, torch.cuda.current_stream())
         out[prec + "_mlups"] = round(w.nx * w.ny * args.impact_steps / (ms / 1e3) / 1e6, 1)
         L.close()
+    return out
+
+
+def shear(args, torch, T):
+    """Compound drop on a wetting wall sheared by the velocity lid (512 x 256,
+    the full 20000 steps), FP64 and FP32 storage: MLUPS of each, and the FP32
+    result's error against the FP64 one (which equals the oracle to 1e-12) and
+    the FP32 mass drift of fluids 1 and 2 (the lid row holds fluid 3 only)."""
+    import workloads as W
+    w = W.compound_drop_shear()
+    n = args.shear_steps
+    out = {"workload": f"{w.name}, lid U0 = 0.01, densities 1:2:1", "steps": n}
+    fields = {}
+    for prec in ("fp64", "fp32"):
+        L = T.lattice_from_workload(w, prec)
+        m0 = np.array(L.diagnostics()["mass"])
+        ms = time_steps(L, n, torch, torch.cuda.current_stream())
+        out[prec + "_mlups"] = round(w.nx * w.ny * n / (ms / 1e3) / 1e6, 1)
+        fields[prec] = L.fields()
+        if prec == "fp32":
+            m1 = np.array(L.diagnostics()["mass"])
+            out["fp32_mass_drift"] = [float(f"{v:.3g}") for v in np.abs(m1[:2] - m0[:2]) / np.abs(m0[:2])]
+        L.close()
+    a, b = fields["fp32"], fields["fp64"]
+    err = {k: float(np.abs(a[k] - b[k]).max()) for k in ("c1", "c2", "c3")}
+    for k in ("ux", "uy", "p"):
+        err[k + "_rel"] = float(np.abs(a[k] - b[k]).max() / max(float(np.abs(b[k]).max()), 1e-12))
+    out["fp32_vs_fp64"] = {k: float(f"{v:.3g}") for k, v in err.items()}
     return out
 
 

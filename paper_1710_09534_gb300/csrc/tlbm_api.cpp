@@ -161,21 +161,59 @@ int build_geometry(tlb_lattice* L)
 
 constexpr int kProfSlots = 512;
 
-// Fold the recorded event triples into the per-kernel totals (synchronizes).
+// Fold the recorded events (per step: interior start/end, near-wall
+// start/end) into the per-kernel totals (synchronizes).
 int prof_fold(tlb_lattice* L)
 {
     if (L->ev_used == 0) return TLB_OK;
-    TLB_CUDA(cudaEventSynchronize(L->ev[3 * (L->ev_used - 1) + 2]));
+    TLB_CUDA(cudaEventSynchronize(L->ev[4 * (L->ev_used - 1) + 1]));
+    TLB_CUDA(cudaEventSynchronize(L->ev[4 * (L->ev_used - 1) + 3]));
     for (int i = 0; i < L->ev_used; i++) {
         float a = 0, b = 0;
-        TLB_CUDA(cudaEventElapsedTime(&a, L->ev[3 * i], L->ev[3 * i + 1]));
-        TLB_CUDA(cudaEventElapsedTime(&b, L->ev[3 * i + 1], L->ev[3 * i + 2]));
+        TLB_CUDA(cudaEventElapsedTime(&a, L->ev[4 * i], L->ev[4 * i + 1]));
+        TLB_CUDA(cudaEventElapsedTime(&b, L->ev[4 * i + 2], L->ev[4 * i + 3]));
         L->prof_ms[0] += a;
         L->prof_ms[1] += b;
         L->prof_n[0] += 1;
         L->prof_n[1] += L->nlist > 0 ? 1 : 0;
     }
     L->ev_used = 0;
+    return TLB_OK;
+}
+
+// One step's launches: `interior` on the lattice's stream and `wall` on the
+// side stream between a fork after `pre` (work both depend on) and a join,
+// then `post` on the lattice's stream; with profiling, events around both.
+template <typename Pre, typename Interior, typename Wall, typename Post>
+int step_launches(tlb_lattice* L, Pre pre, Interior interior, Wall wall, Post post)
+{
+    int rc;
+    cudaEvent_t* ev = nullptr;
+    if (L->prof) {
+        if (L->ev_used == kProfSlots && (rc = prof_fold(L))) return rc;
+        ev = &L->ev[4 * L->ev_used];
+        TLB_CUDA(cudaEventRecord(ev[0], L->stream));
+    }
+    TLB_CUDA(pre());
+    const bool two = L->nlist > 0;
+    if (two) {
+        TLB_CUDA(cudaEventRecord(L->fork, L->stream));
+        TLB_CUDA(cudaStreamWaitEvent(L->side, L->fork, 0));
+    }
+    TLB_CUDA(interior());
+    if (ev) TLB_CUDA(cudaEventRecord(ev[1], L->stream));
+    if (two) {
+        if (ev) TLB_CUDA(cudaEventRecord(ev[2], L->side));
+        TLB_CUDA(wall(L->side));
+        if (ev) TLB_CUDA(cudaEventRecord(ev[3], L->side));
+        TLB_CUDA(cudaEventRecord(L->join, L->side));
+        TLB_CUDA(cudaStreamWaitEvent(L->stream, L->join, 0));
+    } else if (ev) {
+        TLB_CUDA(cudaEventRecord(ev[2], L->stream));
+        TLB_CUDA(cudaEventRecord(ev[3], L->stream));
+    }
+    TLB_CUDA(post());
+    if (ev) L->ev_used++;
     return TLB_OK;
 }
 
@@ -246,7 +284,13 @@ int tlb_create_lattice(int nx, int ny, int precision, const int32_t edges[4], vo
     L->mask.assign((size_t)nx * ny, 0);
     cudaError_t e = cudaGetDevice(&L->device);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        if (L->done) cudaEventDestroy(L->done);
+        if (L->fork) cudaEventDestroy(L->fork);
+        if (L->join) cudaEventDestroy(L->join);
         delete L;
         return fail(TLB_ECUDA, "device set-up failed: %s", cudaGetErrorString(e));
     }
@@ -258,6 +302,9 @@ int tlb_create_lattice(int nx, int ny, int precision, const int32_t edges[4], vo
     }
     if (rc != TLB_OK) {
         cudaEventDestroy(L->done);
+        cudaEventDestroy(L->fork);
+        cudaEventDestroy(L->join);
+        cudaStreamDestroy(L->side);
         delete L;
         return rc;
     }
@@ -498,23 +545,23 @@ static int step_inplace(tlb_lattice* L, int64_t n)
     const bool lid = L->edge[3] == TLB_EDGE_LID;
     for (int64_t s = 0; s < n; s++) {
         const int odd = (int)(s & 1);
-        if (L->prof) {
-            if (L->ev_used == kProfSlots && (rc = prof_fold(L))) return rc;
-            TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used], L->stream));
-        }
-        TLB_CUDA(L->ops->csum_ip(L->bufA(), L->cpl(), L->dcls(), L->geo, odd, L->stream));
-        TLB_CUDA(L->ops->interior_ip(L->bufA(), L->cu(), L->cpl(), L->dcls(), L->geo, L->prm, odd, L->stream));
-        if (L->prof) TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used + 1], L->stream));
-        if (lid)
-            TLB_CUDA(L->ops->wall_ip(L->bufA(), L->cu(), L->cpl(), L->dcls(), L->dlist(), (int)L->nlist, L->geo,
-                                     L->prm, odd, 1, L->stream));
-        TLB_CUDA(L->ops->wall_ip(L->bufA(), L->cu(), L->cpl(), L->dcls(), L->dlist(), (int)L->nlist, L->geo, L->prm,
-                                 odd, 0, L->stream));
-        if (!odd && s == n - 1) TLB_CUDA(L->ops->swap_ip(L->bufA(), L->dcls(), L->geo, L->stream));
-        if (L->prof) {
-            TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used + 2], L->stream));
-            L->ev_used++;
-        }
+        rc = step_launches(
+            L, [&] { return L->ops->csum_ip(L->bufA(), L->cpl(), L->dcls(), L->geo, odd, L->stream); },
+            [&] { return L->ops->interior_ip(L->bufA(), L->cu(), L->cpl(), L->dcls(), L->geo, L->prm, odd, L->stream); },
+            [&](cudaStream_t ws) {
+                cudaError_t e = cudaSuccess;
+                if (lid)
+                    e = L->ops->wall_ip(L->bufA(), L->cu(), L->cpl(), L->dcls(), L->dlist(), (int)L->nlist, L->geo,
+                                        L->prm, odd, 1, ws);
+                if (e == cudaSuccess)
+                    e = L->ops->wall_ip(L->bufA(), L->cu(), L->cpl(), L->dcls(), L->dlist(), (int)L->nlist, L->geo,
+                                        L->prm, odd, 0, ws);
+                return e;
+            },
+            [&] {
+                return (!odd && s == n - 1) ? L->ops->swap_ip(L->bufA(), L->dcls(), L->geo, L->stream) : cudaSuccess;
+            });
+        if (rc) return rc;
     }
     return ok();
 }
@@ -528,18 +575,15 @@ int tlb_step(tlb_lattice* L, int64_t n)
     if (L->batch) return fail(TLB_ESTATE, "lattice belongs to a batch: step the batch");
     if (L->lay.inplace) return step_inplace(L, n);
     for (int64_t s = 0; s < n; s++) {
-        if (L->prof) {
-            if (L->ev_used == kProfSlots && (rc = prof_fold(L))) return rc;
-            TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used], L->stream));
-        }
-        TLB_CUDA(L->ops->interior(L->bufA(), L->bufB(), L->cu(), L->dcls(), L->geo, L->prm, L->stream));
-        if (L->prof) TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used + 1], L->stream));
-        TLB_CUDA(L->ops->wall(L->bufA(), L->bufB(), L->cu(), L->dcls(), L->dlist(), (int)L->nlist, L->geo,
-                              L->prm, L->stream));
-        if (L->prof) {
-            TLB_CUDA(cudaEventRecord(L->ev[3 * L->ev_used + 2], L->stream));
-            L->ev_used++;
-        }
+        rc = step_launches(
+            L, [] { return cudaSuccess; },
+            [&] { return L->ops->interior(L->bufA(), L->bufB(), L->cu(), L->dcls(), L->geo, L->prm, L->stream); },
+            [&](cudaStream_t ws) {
+                return L->ops->wall(L->bufA(), L->bufB(), L->cu(), L->dcls(), L->dlist(), (int)L->nlist, L->geo,
+                                    L->prm, ws);
+            },
+            [] { return cudaSuccess; });
+        if (rc) return rc;
         L->cur ^= 1;
     }
     return ok();
@@ -789,7 +833,7 @@ int tlb_profile(tlb_lattice* L, int enable)
     int rc = check_handle(L);
     if (rc) return rc;
     if (enable && L->ev.empty()) {
-        L->ev.resize(3 * kProfSlots);
+        L->ev.resize(4 * kProfSlots);
         for (auto& e : L->ev) TLB_CUDA(cudaEventCreate(&e));
     }
     if (!enable && (rc = prof_fold(L))) return rc;
@@ -819,6 +863,9 @@ void tlb_destroy(tlb_lattice* L)
     if (L->batch) tlb_batch_remove(L->batch, L);
     for (auto e : L->ev) cudaEventDestroy(e);
     if (L->done) cudaEventDestroy(L->done);
+    if (L->fork) cudaEventDestroy(L->fork);
+    if (L->join) cudaEventDestroy(L->join);
+    if (L->side) cudaStreamDestroy(L->side);
     delete L;
 }
 

@@ -256,10 +256,10 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
 template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT, bool UNI, bool ODD>
 __global__ void __launch_bounds__(BLOCK, MINB)
 k_step_interior_ip(S* f, CuT<S>* __restrict__ cu, const R* __restrict__ cpl, const uint8_t* __restrict__ cls,
-                   Geo g, Prm<R> P)
+                   Geo g, Prm<R> P, int rows)
 {
     __shared__ TileRings<R, BLOCK> sh;
-    interior_tile_ip<S, R, BLOCK, PREFETCH, MRT, UNI, ODD>(f, cu, cpl, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
+    interior_tile_ip<S, R, BLOCK, PREFETCH, MRT, UNI, ODD>(f, cu, cpl, cls, g, P, blockIdx.x, blockIdx.y, rows, sh);
 }
 
 // ---------------------------------------------------------------------------

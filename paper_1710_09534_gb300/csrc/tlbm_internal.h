@@ -25,6 +25,12 @@ struct tlb_lattice {
     int32_t edge[4] = {0, 0, 0, 0};
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    // The near-wall kernel of a step runs on `side`, concurrently with the
+    // interior kernel on `stream` (they read the same state and write disjoint
+    // (node, slot) pairs): `fork` orders it after the previous step, `join`
+    // orders the next step after it.
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     char* ws = nullptr;
     tlb::Layout lay;
     const tlb::Ops* ops = nullptr;
@@ -37,7 +43,8 @@ struct tlb_lattice {
     int64_t nlist = 0;
     std::vector<uint32_t> hlist;  // host copy of the near-wall list
     tlb_batch* batch = nullptr;   // batch this lattice belongs to, if any
-    // optional per-kernel timing: event triples around the two launches of a step
+    // optional per-kernel timing: per step, events around the interior launch
+    // (on `stream`) and around the near-wall launch (on `side`)
     bool prof = false;
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;

@@ -366,7 +366,7 @@ struct PushOffsets {
 // K1: fused interior update, marching along a strip of columns.
 //
 // A block of BLOCK threads owns one column each: columns x0-2 .. x0+BLOCK-3
-// of which the middle TX = BLOCK-4 are updated, over the ROWS rows of its
+// of which the middle TX = BLOCK-4 are updated, over the `rows` rows of its
 // segment.  Even segments march up, odd segments down, so that two adjacent
 // segments read the two halo rows they share at about the same time (both
 // at their start or both at their end) and the second read hits L2.  The
@@ -575,15 +575,15 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
 template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT, bool UNI>
 __global__ void __launch_bounds__(BLOCK, MINB)
 k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
-                const uint8_t* __restrict__ cls, Geo g, Prm<R> P)
+                const uint8_t* __restrict__ cls, Geo g, Prm<R> P, int rows)
 {
     __shared__ TileRings<R, BLOCK> sh;
     if constexpr (kStashPops && std::is_same<R, float>::value && !MRT) {
         __shared__ PopStash<R, BLOCK> stash;
-        interior_tile<S, R, BLOCK, PREFETCH, MRT, UNI, true>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh,
+        interior_tile<S, R, BLOCK, PREFETCH, MRT, UNI, true>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, rows, sh,
                                                             &stash);
     } else {
-        interior_tile<S, R, BLOCK, PREFETCH, MRT, UNI>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, ROWS, sh);
+        interior_tile<S, R, BLOCK, PREFETCH, MRT, UNI>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, rows, sh);
     }
 }
 

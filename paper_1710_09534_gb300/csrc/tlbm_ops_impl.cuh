@@ -60,6 +60,34 @@ inline Prm<R> cast_prm(const Prm<double>& d)
     return r;
 }
 
+// Streaming multiprocessors of the current device (queried once per process).
+inline int sm_count()
+{
+    static int n = 0;
+    if (n <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+    }
+    return n;
+}
+
+// Row-segment length of a single-lattice interior launch: `rows`, halved (down
+// to 4) while the grid would not fill every SM with `per_sm` resident blocks,
+// so that a small lattice still spreads over the chip (the halo work per node
+// grows, but idle SMs cost more).
+#ifndef TLB_ADAPTIVE_ROWS
+#define TLB_ADAPTIVE_ROWS 1
+#endif
+inline int rows_for(const Geo& g, int tx, int rows, int per_sm)
+{
+    if (!TLB_ADAPTIVE_ROWS) return rows;
+    const int strips = (g.nx + tx - 1) / tx;
+    while (rows > 4 && (long long)strips * ((g.ny + rows - 1) / rows) < (long long)sm_count() * per_sm) rows /= 2;
+    return rows;
+}
+
 template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT>
 struct OpsImpl {
     static cudaError_t interior(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
@@ -67,14 +95,15 @@ struct OpsImpl {
     {
         const Prm<R> P = cast_prm<R>(Pd);
         constexpr int TX = BLOCK - 4;
-        dim3 grid((g.nx + TX - 1) / TX, (g.ny + ROWS - 1) / ROWS);
+        const int rows = rows_for(g, TX, ROWS, MINB);
+        dim3 grid((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
         // equal densities and viscosities: the uniform-property update
         if (Pd.uni != 0.0)
             k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT, true><<<grid, BLOCK, 0, s>>>(
-                (const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P);
+                (const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P, rows);
         else
             k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT, false><<<grid, BLOCK, 0, s>>>(
-                (const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P);
+                (const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P, rows);
         return cudaGetLastError();
     }
     static cudaError_t wall(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,
@@ -186,9 +215,10 @@ struct OpsImpl {
                                    const Prm<R>& P, cudaStream_t s)
     {
         constexpr int TX = BLOCK - 4;
-        dim3 grid((g.nx + TX - 1) / TX, (g.ny + ROWS - 1) / ROWS);
+        const int rows = rows_for(g, TX, ROWS, kMinBIp);
+        dim3 grid((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
         k_step_interior_ip<S, R, BLOCK, ROWS, PREFETCH, kMinBIp, MRT, UNI, ODD><<<grid, BLOCK, 0, s>>>(
-            (S*)f, (CuT<S>*)cu, (const R*)cpl, cls, g, P);
+            (S*)f, (CuT<S>*)cu, (const R*)cpl, cls, g, P, rows);
     }
     static cudaError_t interior_ip(void* f, void* cu, const void* cpl, const uint8_t* cls, const Geo& g,
                                    const Prm<double>& Pd, int odd, cudaStream_t s)

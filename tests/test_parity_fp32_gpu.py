@@ -111,3 +111,27 @@ def test_fp32_contact_angle_within_half_degree(T, theta13):
     # the device-side FP64 contact-line diagnostic on the FP32 state
     (_, _, td, _), = L.contact_angles(1)
     assert abs(td - to) < 0.5
+
+
+def test_fp32_sheared_compound_drop_20000_steps(T):
+    """The 512x256 lid-driven compound drop (densities 1:2:1, lambda_3 = 0) over
+    its full 20000 steps: FP32 against the FP64 path (which equals the oracle to
+    1e-12, checked on the same lattice in the FP64 parity tests) within the
+    FP32 bounds, and the mass of fluids 1 and 2 conserved to 1e-6 (the lid row
+    holds fluid 3 only, so Eq. 51 moves none of them)."""
+    w = W.compound_drop_shear()
+    A = T.lattice_from_workload(w, "fp64")
+    B = T.lattice_from_workload(w, "fp32")
+    m0 = np.array(B.diagnostics()["mass"])
+    A.step(20000)
+    B.step(20000)
+    fa, fb = A.fields(), B.fields()
+    for k, (kind, bound) in BOUNDS.items():
+        err = float(np.abs(fb[k] - fa[k]).max())
+        if kind == "rel":
+            err /= max(float(np.abs(fa[k]).max()), 1e-12)
+        assert err < bound, f"shear: {k} error {err:.3e} >= {bound}"
+    d = B.diagnostics()
+    assert d["nonfinite"] == 0
+    drift = np.abs(np.array(d["mass"])[:2] - m0[:2]) / np.abs(m0[:2])
+    assert np.all(drift < 1e-6), drift
