@@ -74,6 +74,11 @@ struct tlb_batch {
     cudaGraphExec_t graph = nullptr;
     int graph_variant = -1;
     const tlb::Ops* graph_ops = nullptr;
+    // the near-wall loop of a step runs on `side`, concurrently with the
+    // interior tile queue (disjoint writes, one state read), between `fork`
+    // and `join` (captured into the graph like the launches)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -147,8 +152,12 @@ int rebuild(tlb_batch* B)
 
 int launch_step(tlb_batch* B, int parity)
 {
+    B_CUDA(cudaEventRecord(B->fork, B->stream));
+    B_CUDA(cudaStreamWaitEvent(B->side, B->fork, 0));
     B_CUDA(B->ops->batch_step(B->ws + B->lay.desc, B->ws + B->lay.tiles, B->ws + B->lay.walls, B->ws + B->lay.ctr,
-                              parity, B->variant, B->grid_interior, B->grid_wall, B->stream));
+                              parity, B->variant, B->grid_interior, B->grid_wall, B->stream, B->side));
+    B_CUDA(cudaEventRecord(B->join, B->side));
+    B_CUDA(cudaStreamWaitEvent(B->stream, B->join, 0));
     return TLB_OK;
 }
 
@@ -266,6 +275,15 @@ int tlb_batch_create(int precision, int max_lattices, int64_t max_tiles, int64_t
     if (cudaGetDevice(&B->device) != cudaSuccess) {
         delete B;
         return err(TLB_ECUDA, "no current device");
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        if (B->fork) cudaEventDestroy(B->fork);
+        if (B->join) cudaEventDestroy(B->join);
+        delete B;
+        return err(TLB_ECUDA, "batch set-up failed: %s", cudaGetErrorString(e));
     }
     *out = B;
     return tlb::clear_error();
@@ -391,6 +409,9 @@ void tlb_batch_destroy(tlb_batch* B)
     cudaStreamSynchronize(B->stream);
     for (tlb_lattice* L : B->members) L->batch = nullptr;
     if (B->graph) cudaGraphExecDestroy(B->graph);
+    cudaEventDestroy(B->fork);
+    cudaEventDestroy(B->join);
+    cudaStreamDestroy(B->side);
     delete B;
 }
 

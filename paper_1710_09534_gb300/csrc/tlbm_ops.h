@@ -30,9 +30,10 @@ struct Ops {
     cudaError_t (*film)(const void* fA, const uint8_t* cls, int x, int y_top, int comps, double* out, const Geo& g,
                         cudaStream_t s);
     // batched step: persistent interior kernel (variant 0: 64-thread blocks,
-    // 1: 128-thread blocks) over the tile list, then the near-wall loop
+    // 1: 128-thread blocks) over the tile list on s, the near-wall loop on ws
+    // (the caller orders ws after the previous step and s's next step after ws)
     cudaError_t (*batch_step)(const void* descs, const void* tiles, const void* walls, void* ctr, int parity,
-                              int variant, int grid_interior, int grid_wall, cudaStream_t s);
+                              int variant, int grid_interior, int grid_wall, cudaStream_t s, cudaStream_t ws);
     // resident blocks per SM of the persistent interior kernel of a variant
     int (*batch_blocks_per_sm)(int variant);
     size_t desc_size;  // bytes of one device lattice descriptor

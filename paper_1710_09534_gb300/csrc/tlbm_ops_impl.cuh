@@ -155,7 +155,7 @@ struct OpsImpl {
     // the two block shapes the batch tuner chooses between
     static constexpr int kMinB64 = std::is_same<R, float>::value ? 8 : 6;
     static cudaError_t batch_step(const void* descs, const void* tiles, const void* walls, void* ctr, int parity,
-                                  int variant, int grid_interior, int grid_wall, cudaStream_t s)
+                                  int variant, int grid_interior, int grid_wall, cudaStream_t s, cudaStream_t ws)
     {
         BatchCounters* c = (BatchCounters*)ctr;
         cudaError_t e = cudaMemsetAsync(&c->next[parity], 0, sizeof(int), s);
@@ -166,7 +166,7 @@ struct OpsImpl {
         else
             k_batch_interior<S, R, 128, PREFETCH, MINB, MRT><<<grid_interior, 128, 0, s>>>(
                 (const LatDesc<R>*)descs, (const TileItem*)tiles, c, parity);
-        k_batch_wall<S, R, MRT><<<grid_wall, 128, 0, s>>>((const LatDesc<R>*)descs, (const WallItem*)walls, c, parity);
+        k_batch_wall<S, R, MRT><<<grid_wall, 128, 0, ws>>>((const LatDesc<R>*)descs, (const WallItem*)walls, c, parity);
         return cudaGetLastError();
     }
     static int batch_blocks_per_sm(int variant)
