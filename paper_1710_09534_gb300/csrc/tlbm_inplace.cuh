@@ -139,7 +139,28 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
 #pragma unroll
             for (int q = 0; q < 4; q++) cp[q] = R(cu[q * PL + ou]);
         };
-        if (PREFETCH && upd) load_g();
+        // With FP32 arithmetic all 18 order-parameter populations are read
+        // before the collision, and with PREFETCH already here, so that their
+        // latency overlaps the shared-memory phases: plain loads cannot be
+        // moved past the stores of earlier directions, so reading them pair by
+        // pair would expose one load latency per pair.  (FP64 keeps the pairs:
+        // its registers are the tighter limit.)
+        constexpr bool kPre = std::is_same<R, float>::value;
+        R f1[9], f2[9];
+        auto load_f = [&](auto kc, R& f1k, R& f2k) {
+            constexpr int K = decltype(kc)::value;
+            const long long s = (ODD && K != 0) ? po.template dest<opp(K)>() : ou;
+            constexpr int q = ODD ? opp(K) : K;
+            f1k = ld_pop<R, false>(f, q, PL, s);
+            f2k = ld_pop<R, false>(f, 9 + q, PL, s);
+        };
+        auto load_all_f = [&]() {
+            static_for<0, 9>([&](auto kc) { load_f(kc, f1[decltype(kc)::value], f2[decltype(kc)::value]); });
+        };
+        if (PREFETCH && upd) {
+            load_g();
+            if constexpr (kPre) load_all_f();
+        }
         // 1) c of row yc from the planes
         {
             int yw = yc;
@@ -207,21 +228,9 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
         cu[1 * PL + ou] = CuT<S>(c1uy);
         cu[2 * PL + ou] = CuT<S>(c2ux);
         cu[3 * PL + ou] = CuT<S>(c2uy);
-        // With FP32 arithmetic all 18 order-parameter populations are read
-        // before the collision: plain loads cannot be moved past the stores
-        // of earlier directions, so reading them pair by pair would expose
-        // one load latency per pair.  (FP64 keeps the pairs: its registers
-        // are the tighter limit.)
-        constexpr bool kPre = std::is_same<R, float>::value;
-        R f1[9], f2[9];
-        auto load_f = [&](auto kc, R& f1k, R& f2k) {
-            constexpr int K = decltype(kc)::value;
-            const long long s = (ODD && K != 0) ? po.template dest<opp(K)>() : ou;
-            constexpr int q = ODD ? opp(K) : K;
-            f1k = ld_pop<R, false>(f, q, PL, s);
-            f2k = ld_pop<R, false>(f, 9 + q, PL, s);
-        };
-        if constexpr (kPre) static_for<0, 9>([&](auto kc) { load_f(kc, f1[decltype(kc)::value], f2[decltype(kc)::value]); });
+        if constexpr (kPre) {
+            if (!PREFETCH) load_all_f();
+        }
         CollideOf<MRT, R, UNI> col;
         col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
         collide_all_inplace<S, R>(col, gv,
