@@ -101,6 +101,9 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--serve-count", type=int, default=40, help="requests in the served workload (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=2.0)
+    ap.add_argument("--serve-hi", type=int, default=1024, help="largest side of a served lattice")
+    ap.add_argument("--serve-steps-lo", type=int, default=500)
+    ap.add_argument("--serve-steps-hi", type=int, default=5000)
     return ap.parse_args()
 
 
@@ -532,13 +535,16 @@ def shear(args, torch, T):
 
 def served(args, torch, T):
     """The served workload: Poisson arrivals (20 requests/s, seed 1710) of
-    drop-on-wall and drop-on-cylinder jobs, sides log-uniform 128..1024, steps
-    log-uniform 500..5000, FP32 and FP16 storage alternating, admitted by
-    device footprint against an HBM budget; time to result and aggregate
-    MLUPS over the whole run."""
+    drop-on-wall and drop-on-cylinder jobs, sides log-uniform 128..serve_hi,
+    steps log-uniform serve_steps_lo..serve_steps_hi (default 1024, 500..5000:
+    a run of seconds; the full configuration is 200 requests, 128..2048,
+    1000..20000), FP32 and FP16 storage alternating, admitted by device
+    footprint against an HBM budget; time to result and aggregate MLUPS over
+    the whole run."""
     import workloads as W
     from paper_1710_09534_gb300.serve import Request, Server, poisson_arrivals
-    jobs = W.served_requests(args.serve_count, seed=1710, lo=128, hi=1024, steps_lo=500, steps_hi=5000)
+    hi, slo, shi = args.serve_hi, args.serve_steps_lo, args.serve_steps_hi
+    jobs = W.served_requests(args.serve_count, seed=1710, lo=128, hi=hi, steps_lo=slo, steps_hi=shi)
     t_arr = poisson_arrivals(len(jobs), 20.0, seed=1710)
     # every other request asks for shifted-FP16 storage; the server keeps one batch per precision
     reqs = [Request(i, w, s, "fp16" if i % 2 else "fp32", float(t)) for i, ((w, s), t) in enumerate(zip(jobs, t_arr))]
@@ -546,7 +552,7 @@ def served(args, torch, T):
     stats = srv.run(reqs)
     srv.close()
     out = stats.summary()
-    out["workload"] = (f"{len(reqs)} requests, Poisson 20/s (seed 1710), sides 128..1024, steps 500..5000, "
+    out["workload"] = (f"{len(reqs)} requests, Poisson 20/s (seed 1710), sides 128..{hi}, steps {slo}..{shi}, "
                        f"FP32 and shifted-FP16 alternating, HBM budget {args.serve_budget_gb} GB")
     return out
 
