@@ -244,6 +244,12 @@ def cpu_baseline(w, budget_s=12.0, single_s=5.0):
         oracle.set_threads(thr)
     out["single_core"] = {"value": round(m1, 3), "unit": "MLUPS", "cores": 1,
                           "sample": f"the same strip, {steps1} steps, {dt1:.1f} s"}
+    # the 128x64 two-drop wetting case, its full 2000 steps, on all cores
+    import workloads as W
+    c1 = W.binary_drops_on_wall()
+    mc, dtc, _ = oracle_run(c1, 2000)
+    out["binary_drops_128x64"] = {"value": round(mc, 3), "unit": "MLUPS", "cores": thr,
+                                  "sample": f"{c1.name}, 2000 steps, {dtc:.1f} s"}
     return out
 
 
