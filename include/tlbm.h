@@ -193,7 +193,10 @@ int tlb_set_fields_device(tlb_lattice *lat, const double *c1, const double *c2,
 /* Advance n >= 0 time steps, asynchronously on the stream: per step one fused
  * interior kernel and one near-wall kernel (in-place lattices: the
  * order-parameter pass, the interior kernel, the lid row if any, the
- * near-wall kernel, and after a last even step the in-place streaming).
+ * near-wall kernel, and after a last even step the in-place streaming).  The
+ * near-wall launches run on a stream the lattice owns, ordered after the
+ * step's earlier work and joined back into the caller's stream before the
+ * step ends, so work the caller queues after tlb_step sees the whole step.
  * TLB_ESTATE before set_fields. */
 int tlb_step(tlb_lattice *lat, int64_t n);
 
