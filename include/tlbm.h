@@ -150,7 +150,9 @@ typedef struct {
 int64_t tlb_workspace_bytes(int nx, int ny, int precision);
 
 /* Create a lattice of nx*ny nodes (nx, ny >= 3 and <= 32768) with the
- * storage precision (| TLB_INPLACE for in-place streaming).  dev_workspace:
+ * storage precision (| TLB_INPLACE for in-place streaming).  The handle owns
+ * one CUDA stream and a few events of its own (no device memory), released
+ * by tlb_destroy.  dev_workspace:
  * caller-owned device memory of at least tlb_workspace_bytes, 256-byte aligned.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).  *out receives
  * the handle.  The lattice starts all-fluid; parameters and fields must be set
@@ -276,10 +278,12 @@ int64_t tlb_wall_nodes(tlb_lattice *lat);
 /* ---- Batches: many lattices advanced together -------------------------
  * A batch steps all its member lattices in lockstep: per step, one
  * persistent kernel whose blocks take (member, strip, segment) tiles of the
- * fused interior update from a shared counter, then one loop over all the
- * members' near-wall nodes (same per-node arithmetic as tlb_step, so a
- * member's result does not depend on the rest of the batch).  Pairs of steps
- * run as one captured CUDA graph on the batch's stream.  Members keep their
+ * fused interior update from a shared counter and, concurrently on a stream
+ * the batch owns, one loop over all the members' near-wall nodes (same
+ * per-node arithmetic as tlb_step, so a member's result does not depend on
+ * the rest of the batch).  Pairs of steps run as one captured CUDA graph on
+ * the batch's stream (the side stream's launches are captured with it).
+ * In-place lattices (TLB_INPLACE) cannot be members.  Members keep their
  * own workspaces; the batch workspace holds the device descriptors and work
  * lists.  Not in the paper: it serves many independent simulations.
  *
