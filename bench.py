@@ -420,8 +420,10 @@ def run_ours(args):
             V.sync()
             n_ip = max(10, args.steps // (4 if prec == "fp64" else 1)) // 2 * 2
             vms = time_steps(V, n_ip, torch, stream)
+            v_mlups = n_nodes * n_ip / (vms / 1e3) / 1e6
             variants[prec + "_inplace"] = {
-                "value": round(n_nodes * n_ip / (vms / 1e3) / 1e6, 2), "unit": "MLUPS", "steps": n_ip,
+                "value": round(v_mlups, 2), "unit": "MLUPS", "steps": n_ip,
+                "hbm_roofline_pct": round(100 * v_mlups * 1e6 * bytes_per_node(prec) / (hbm_gbs * 1e9), 2),
                 "workspace_bytes": int(V.workspace.numel()),
                 "two_buffer_workspace_bytes": int(T.load_library().tlb_workspace_bytes(w.nx, w.ny, T.PRECISIONS[prec]))}
             del V
