@@ -207,17 +207,28 @@ struct OpsImpl {
         else k_csum<S, R, false><<<grid, 128, 0, s>>>((const S*)f, (R*)cpl, cls, g);
         return cudaGetLastError();
     }
-    // resident blocks of the in-place interior kernel: its FP32 form holds all
-    // 18 order-parameter populations at once, which needs 128 registers
-    static constexpr int kMinBIp = std::is_same<R, float>::value ? 4 : MINB;
+    // resident blocks of the in-place interior kernel per step parity: its
+    // FP32 form holds all 18 order-parameter populations at once; at 5 blocks
+    // (96 registers) the odd (gathering) form spills a few words, and is still
+    // faster than at 4 blocks (GB300, 2048^2: FP32 13.0 -> 14.1, FP16 13.6 ->
+    // 15.1 G node updates/s with both parities at 5)
+#ifndef TLB_IP_MINB_EVEN
+#define TLB_IP_MINB_EVEN 5
+#endif
+#ifndef TLB_IP_MINB_ODD
+#define TLB_IP_MINB_ODD 5
+#endif
+    static constexpr int kMinBIpEven = std::is_same<R, float>::value ? TLB_IP_MINB_EVEN : MINB;
+    static constexpr int kMinBIpOdd = std::is_same<R, float>::value ? TLB_IP_MINB_ODD : MINB;
     template <bool UNI, bool ODD>
     static void launch_interior_ip(void* f, void* cu, const void* cpl, const uint8_t* cls, const Geo& g,
                                    const Prm<R>& P, cudaStream_t s)
     {
         constexpr int TX = BLOCK - 4;
-        const int rows = rows_for(g, TX, ROWS, kMinBIp);
+        constexpr int kMinB = ODD ? kMinBIpOdd : kMinBIpEven;
+        const int rows = rows_for(g, TX, ROWS, kMinB);
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
-        k_step_interior_ip<S, R, BLOCK, ROWS, PREFETCH, kMinBIp, MRT, UNI, ODD><<<grid, BLOCK, 0, s>>>(
+        k_step_interior_ip<S, R, BLOCK, ROWS, PREFETCH, kMinB, MRT, UNI, ODD><<<grid, BLOCK, 0, s>>>(
             (S*)f, (CuT<S>*)cu, (const R*)cpl, cls, g, P, rows);
     }
     static cudaError_t interior_ip(void* f, void* cu, const void* cpl, const uint8_t* cls, const Geo& g,
