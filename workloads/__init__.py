@@ -99,6 +99,21 @@ def _zeros(nx, ny):
     return np.zeros((ny, nx))
 
 
+def _window(nx, ny, xc, yc, R, D, period_x=None):
+    """Rows y0..y1-1 and columns `cols` of the nodes within R + 10 D of (xc, yc)
+    (minimum image in x when periodic).  Beyond that distance the profile
+    0.5 + 0.5 tanh(2 (R - r) / D) is exactly 0 in FP64 (tanh(-20) rounds to -1),
+    so a profile evaluated on this window only is the whole-grid one, bit for bit."""
+    reach = R + 10.0 * D
+    y0, y1 = max(0, int(np.floor(yc - reach))), min(ny, int(np.ceil(yc + reach)) + 1)
+    lo, hi = int(np.floor(xc - reach)), int(np.ceil(xc + reach)) + 1
+    if period_x:
+        cols = np.arange(lo, hi) % nx if hi - lo < nx else np.arange(nx)
+    else:
+        cols = np.arange(max(0, lo), min(nx, hi))
+    return y0, max(y0, y1), cols
+
+
 # ---- the paper-shaped workloads -------------------------------------------
 
 def binary_drops_on_wall(nx=128, ny=64, R=16.0, sep=40.0, theta=(60.0, 90.0, 120.0),
@@ -222,25 +237,34 @@ def tiled_drops(nx=2048, ny=2048, seed=1710, steps=1000) -> Workload:
     fluid 2 (R = 16) every 40 nodes along a wetting bottom wall, a neutral top
     wall, periodic in x, plus seeded free compound drops in the bulk."""
     rng = np.random.default_rng(seed)
-    x, y = grid(nx, ny)
     c1 = np.zeros((ny, nx))
     c2 = np.zeros((ny, nx))
+
+    # each drop is evaluated on the window where its profile is nonzero (the
+    # same values as on the whole grid; the maxima below leave the rest as is)
+    def win(xc, yc, R):
+        y0, y1, cols = _window(nx, ny, xc, yc, R, 4.0, period_x=nx)
+        xs = cols.astype(float)[None, :]
+        ys = np.arange(y0, y1, dtype=float)[:, None]
+        return (slice(y0, y1), cols), xs, ys
+
     for i, xc in enumerate(np.arange(20.0, nx, 40.0)):
-        prof = profile(x, y, xc, -0.5, 16.0, 4.0, period_x=nx)
-        if i % 2 == 0:
-            c1 = np.maximum(c1, prof)
-        else:
-            c2 = np.maximum(c2, prof)
+        ix, xs, ys = win(xc, -0.5, 16.0)
+        prof = profile(xs, ys, xc, -0.5, 16.0, 4.0, period_x=nx)
+        tgt = c1 if i % 2 == 0 else c2
+        tgt[ix] = np.maximum(tgt[ix], prof)
     n_free = max(1, (nx * ny) // 60000)
     for _ in range(n_free):
         xc = rng.uniform(0, nx)
         yc = rng.uniform(80, ny - 60)
         rs = rng.uniform(10, 24)
-        prof_s = profile(x, y, xc, yc, rs, 4.0, period_x=nx)
-        prof_c = profile(x, y, xc, yc, 0.55 * rs, 4.0, period_x=nx)
-        keep = c1 + c2 < 0.01
-        c1 = np.where(keep, np.maximum(c1, prof_c), c1)
-        c2 = np.where(keep, np.maximum(c2, prof_s - prof_c), c2)
+        ix, xs, ys = win(xc, yc, rs)
+        prof_s = profile(xs, ys, xc, yc, rs, 4.0, period_x=nx)
+        prof_c = profile(xs, ys, xc, yc, 0.55 * rs, 4.0, period_x=nx)
+        a, b = c1[ix], c2[ix]
+        keep = a + b < 0.01
+        c1[ix] = np.where(keep, np.maximum(a, prof_c), a)
+        c2[ix] = np.where(keep, np.maximum(b, prof_s - prof_c), b)
     P = params(sigma=(1e-3, 1e-3, 1e-3), theta=(60.0, 90.0, 120.0), mobility=0.1, D=4.0)
     return Workload(f"tiled_drops_{nx}x{ny}", nx, ny, (PERIODIC, PERIODIC, WETTING, NEUTRAL),
                     np.zeros((ny, nx), np.uint8), P, np.clip(c1, 0, 1), np.clip(c2, 0, 1),
