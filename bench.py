@@ -32,11 +32,25 @@ METRIC = "MLUPS & % of HBM roofline, batched/served vs plain; p50/p99 solve late
 
 
 def bytes_per_node(precision):
-    """Algorithmic bytes per node update: the state that must persist, read
-    and written once -- 27 distributions (FP32 storage adds the lo halves of
-    the two rest populations) and the 4 c_i u values of Eq. 19.  16-bit
-    storage: 25 populations of 2 bytes, the two rest populations as FP32
-    pairs (16 bytes) and the c_i u values in FP32."""
+    """Algorithmic bytes per node update: the state the method must carry from
+    one step to the next, read once and written once -- the 27 distributions
+    f^1, f^2, g (Eqs. 1a, 1b) and the 4 c_i u values of Eq. 19 (62 values):
+    496 B in FP64, 248 B in FP32, 140 B with 16-bit distributions and FP32
+    c_i u.  Storage-layout extras (the lo halves that keep the rest
+    populations mass-conserving) are not the method's work and are reported
+    apart (storage_bytes_per_node)."""
+    if precision == "fp64":
+        return 2 * (27 + 4) * 8
+    if precision == "fp32":
+        return 2 * (27 + 4) * 4
+    return 2 * (27 * 2 + 4 * 4)
+
+
+def storage_bytes_per_node(precision):
+    """Bytes per node update that this library's storage layout moves: FP32
+    keeps the two rest populations as float pairs (two extra planes); 16-bit
+    storage keeps the 25 moving populations in 16 bits and the two rest
+    populations as FP32 pairs (16 bytes)."""
     if precision == "fp64":
         return 2 * (27 + 4) * 8
     if precision == "fp32":
@@ -135,6 +149,18 @@ def measured_traffic(precision, units):
         return None
     e = d[precision]
     return round(e["dram_bytes"] / e["interior_nodes"] * units)
+
+
+def measured_fp64_peak(T):
+    """FP64 fused-multiply-add rate measured on this device just before the
+    timed region (tlb_fma_peak: independent FMA chains on every SM, fastest of
+    five launches); the nominal figure if the measurement fails."""
+    try:
+        r = T.fma_peak("fp64")
+        return r["tflops"], (f"measured in this run: tlb_fma_peak FP64 FMA chains on every SM, "
+                             f"{r['ms']:.3f} ms per launch, fastest of 5")
+    except Exception as e:  # the kernel roofline still needs a denominator
+        return FP64_PEAK_TFLOPS, f"nominal (FMA measurement failed: {e})"
 
 
 def peaks():
@@ -305,6 +331,7 @@ def run_ours(args):
     n_nodes = w.nx * w.ny
     L.step(args.warmup)
     L.sync()
+    fp64_peak = measured_fp64_peak(T) if args.precision == "fp64" else None
     # timed region: K steps, barrier + synchronize on both sides
     if D:
         D.barrier()
@@ -336,9 +363,12 @@ def run_ours(args):
         dp_inst, dp_flops = FP64_DP[path]
         ach_tf = interior_nodes * dp_flops / (k1_avg / 1e3) / 1e12
         dp_issue = interior_nodes * dp_inst / (k1_avg / 1e3) / FP64_DP_INST_PEAK
-        roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(ach_tf / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 2 DP inst/clk x 2 flop x 2.07 GHz (FMA-chain probe measured 1.25-1.257 TFLOP/s)",
+        peak_tf, peak_src = fp64_peak
+        roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(peak_tf, 4),
+                "unit": "TFLOP/s", "frac": round(ach_tf / peak_tf, 4), "traffic": traffic,
+                "peak_source": peak_src,
+                "peak_nominal": round(FP64_PEAK_TFLOPS, 4),
+                "peak_nominal_source": "152 SMs x 2 DP inst/clk x 2 flop x 2.07 GHz",
                 "kernel": "k_step_interior<double>", "update": path,
                 "dp_inst_per_node": dp_inst, "flops_per_node": dp_flops,
                 "dp_issue_frac": round(dp_issue, 4),
@@ -347,7 +377,9 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": round(ach_gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
                 "frac": round(hbm_frac, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": ("k_csum + k_step_interior_ip" if args.inplace else KERNEL[args.precision])}
+                "kernel": ("k_csum + k_step_interior_ip" if args.inplace else KERNEL[args.precision]),
+                "algorithmic_bytes_per_node": bytes_node,
+                "storage_bytes_per_node": storage_bytes_per_node(args.precision)}
     result = {
         "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
@@ -384,7 +416,9 @@ def run_ours(args):
             vms = time_steps(V, args.steps, torch, stream)
             v_mlups = n_nodes * args.steps / (vms / 1e3) / 1e6
             variants[prec] = {"value": round(v_mlups, 2), "unit": "MLUPS",
-                              "hbm_roofline_pct": round(100 * v_mlups * 1e6 * bytes_per_node(prec) / (hbm_gbs * 1e9), 2)}
+                              "hbm_roofline_pct": round(100 * v_mlups * 1e6 * bytes_per_node(prec) / (hbm_gbs * 1e9), 2),
+                              "algorithmic_bytes_per_node": bytes_per_node(prec),
+                              "storage_bytes_per_node": storage_bytes_per_node(prec)}
             del V
         # the general (per-node density and viscosity) update: fluid 2 three times denser
         for prec in ("fp64", "fp32") if extras else ():

@@ -296,10 +296,20 @@ int64_t tlb_wall_nodes(tlb_lattice *lat);
  * tlb_batch_remove synchronizes the batch stream.  tlb_batch_step advances
  * every member n steps, asynchronously.  tlb_batch_config sets the tile shape
  * (threads 64 or 128; row segments rows_small for members with ny <=
- * small_ny, rows_large otherwise); tlb_batch_tune times candidate shapes for
- * trial_steps steps each (it advances every member by 8 * (trial_steps + 2)
- * steps), keeps the fastest and reports {threads, rows_small, rows_large,
- * small_ny} and its time per step. */
+ * small_ny, rows_large otherwise).
+ *
+ * tlb_batch_tune times 8 candidate shapes on the batch's own members,
+ * trial_steps + 2 trial steps each, keeps the fastest and reports {threads,
+ * rows_small, rows_large, small_ny} and its time per step.  It leaves every
+ * member's state as it was: each trial step reads the members' current
+ * distributions and writes their spare buffer without making it current, and
+ * the c_i u planes of Eq. 19 (the only state a step updates in place) are
+ * saved to dev_scratch before the trials and restored after them.
+ * dev_scratch: caller-owned device memory, 256-byte aligned, of at least
+ * tlb_batch_tune_scratch_bytes(batch) bytes for the current members (the
+ * library does not allocate it).  Synchronizes the batch stream.  TLB_ESTATE
+ * for an empty batch or a member without state; TLB_ENOMEM for too little
+ * scratch.  On failure the previous shape is kept. */
 int64_t tlb_batch_workspace_bytes(int max_lattices, int64_t max_tiles, int64_t max_wall_nodes);
 int64_t tlb_batch_tiles_needed(int nx, int ny);
 int tlb_batch_create(int precision, int max_lattices, int64_t max_tiles, int64_t max_wall_nodes,
@@ -309,7 +319,9 @@ int tlb_batch_remove(tlb_batch *batch, tlb_lattice *lat);
 int tlb_batch_size(tlb_batch *batch);
 int tlb_batch_step(tlb_batch *batch, int64_t n);
 int tlb_batch_config(tlb_batch *batch, int threads, int rows_small, int rows_large, int small_ny);
-int tlb_batch_tune(tlb_batch *batch, int trial_steps, int out_config[4], double *out_ms_per_step);
+int64_t tlb_batch_tune_scratch_bytes(tlb_batch *batch);
+int tlb_batch_tune(tlb_batch *batch, int trial_steps, void *dev_scratch, int64_t scratch_bytes,
+                   int out_config[4], double *out_ms_per_step);
 void tlb_batch_destroy(tlb_batch *batch);
 
 /* Allocation-free variant of the tlb_diagnostics reduction.  The paper has
@@ -325,12 +337,26 @@ void tlb_batch_destroy(tlb_batch *batch);
  *     get TLB_EINVAL with a message (use tlb_diagnostics for those).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
- *   - All calls share the one array: calls whose work overlaps on the GPU
- *     (different streams, or devices sharing nothing but this array) race
- *     and may return wrong totals; order them on one stream.  Each call
- *     overwrites every partial it reads, so nothing needs clearing.
+ *   - Each device holds its own copy of the array, and every call on that
+ *     device shares it: calls on the same device whose work overlaps (for
+ *     example on different streams) race and may return wrong totals; order
+ *     them on one stream.  Calls on different devices do not interfere.
+ *     Each call overwrites every partial it reads, so nothing needs
+ *     clearing.
  * TLB_ESTATE before set_fields; TLB_EINVAL for a null dev_out. */
 int tlb_diagnostics_noalloc(tlb_lattice *lat, double *dev_out);
+
+/* Arithmetic ceiling of the FP64 (or FP32) update, for its roofline.  The
+ * paper has no counterpart; it is a measurement aid.  Launches a kernel of
+ * independent fused-multiply-add chains on every SM of the current device
+ * (one warm-up launch, then the fastest of five, timed with CUDA events on a
+ * stream the call creates and destroys) and returns the achieved rate in
+ * *tflops (an FMA counts as 2 flops) and the kernel time in *ms (may be
+ * NULL).  precision: TLB_FP64 or TLB_FP32.  dev_sink: caller-owned device
+ * memory of at least 8 bytes; the kernel writes it only in a case that does
+ * not occur, so that the chains are not optimised away.  Synchronizes.
+ * TLB_EINVAL for a null pointer or another precision. */
+int tlb_fma_peak(int precision, void *dev_sink, double *tflops, double *ms);
 
 /* Release the host handle (the workspace stays the caller's). */
 void tlb_destroy(tlb_lattice *lat);

@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tlb_profile": (i32, [vp, i32]),
         "tlb_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "tlb_destroy": (None, [vp]),
+        "tlb_fma_peak": (i32, [i32, vp, dp, dp]),
         "tlb_batch_workspace_bytes": (i64, [i32, i64, i64]),
         "tlb_batch_tiles_needed": (i64, [i32, i32]),
         "tlb_batch_create": (i32, [i32, i32, i64, i64, vp, i64, vp, ctypes.POINTER(vp)]),
@@ -98,7 +99,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tlb_batch_size": (i32, [vp]),
         "tlb_batch_step": (i32, [vp, i64]),
         "tlb_batch_config": (i32, [vp, i32, i32, i32, i32]),
-        "tlb_batch_tune": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int), dp]),
+        "tlb_batch_tune_scratch_bytes": (i64, [vp]),
+        "tlb_batch_tune": (i32, [vp, i32, vp, i64, ctypes.POINTER(ctypes.c_int), dp]),
         "tlb_batch_destroy": (None, [vp]),
         "tlb_last_error": (ctypes.c_char_p, []),
     }
@@ -282,6 +284,17 @@ class Lattice:
         return _check(self.lib.tlb_wall_nodes(self._h))
 
 
+def fma_peak(precision="fp64") -> dict:
+    """Measured fused-multiply-add rate of the current device (tlb_fma_peak):
+    {"tflops": ..., "ms": ...}."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().tlb_fma_peak(PRECISIONS[precision], ctypes.c_void_p(sink.data_ptr()),
+                                       ctypes.byref(tf), ctypes.byref(ms)))
+    return {"tflops": tf.value, "ms": ms.value}
+
+
 def theta12_from(s12, s13, s23, th13, th23) -> float:
     out = ctypes.c_double()
     _check(load_library().tlb_theta12_from(s12, s13, s23, th13, th23, ctypes.byref(out)))
@@ -346,10 +359,18 @@ class Batch:
         _check(self.lib.tlb_batch_config(self._h, int(threads), int(rows_small), int(rows_large), int(small_ny)))
 
     def tune(self, trial_steps: int = 5):
-        """Pick the fastest tile shape; advances every member 8*(trial_steps+2) steps."""
+        """Pick the fastest tile shape by timing the candidates on the current
+        members; every member's state is left as it was (the library saves
+        and restores the c_i u planes in a scratch buffer allocated here)."""
+        import torch
         cfg = (ctypes.c_int * 4)()
         ms = ctypes.c_double()
-        _check(self.lib.tlb_batch_tune(self._h, int(trial_steps), cfg, ctypes.byref(ms)))
+        nbytes = _check(self.lib.tlb_batch_tune_scratch_bytes(self._h))
+        with torch.cuda.device(self.device):
+            scratch = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.device)
+            _check(self.lib.tlb_batch_tune(self._h, int(trial_steps), ctypes.c_void_p(scratch.data_ptr()),
+                                           int(scratch.numel()), cfg, ctypes.byref(ms)))
+        del scratch
         return dict(threads=cfg[0], rows_small=cfg[1], rows_large=cfg[2], small_ny=cfg[3], ms_per_step=ms.value)
 
     def synchronize(self):

@@ -218,6 +218,44 @@ int advance(tlb_batch* B, int64_t n, bool use_graph)
     return TLB_OK;
 }
 
+// Bytes of one member's c_i u planes (Eq. 19), the only state a step
+// updates in place.
+int64_t cu_bytes(const tlb_lattice* L) { return 4 * L->lay.plane * (int64_t)tlb::cu_elem_for(L->precision); }
+
+int64_t tune_scratch_bytes(const tlb_batch* B)
+{
+    int64_t total = 0;
+    for (const tlb_lattice* L : B->members) total += align_up(cu_bytes(L));
+    return total;
+}
+
+// n trial steps that leave every member's state as it was, apart from the
+// c_i u planes: each reads the members' current buffer and writes the spare
+// one (the step parity is never flipped), so the current distributions are
+// untouched; the caller saves and restores the c_i u planes around them.
+int trial_steps(tlb_batch* B, int64_t n)
+{
+    int rc;
+    if (B->dirty && (rc = rebuild(B))) return rc;
+    for (int64_t s = 0; s < n; s++)
+        if ((rc = launch_step(B, 0))) return rc;
+    return TLB_OK;
+}
+
+// Copy every member's c_i u planes to (save = true) or from the scratch.
+int copy_cu(tlb_batch* B, char* scratch, bool save)
+{
+    int64_t off = 0;
+    for (tlb_lattice* L : B->members) {
+        const int64_t nb = cu_bytes(L);
+        char* keep = scratch + off;
+        B_CUDA(cudaMemcpyAsync(save ? keep : (char*)L->cu(), save ? (const char*)L->cu() : keep, (size_t)nb,
+                               cudaMemcpyDeviceToDevice, B->stream));
+        off += align_up(nb);
+    }
+    return TLB_OK;
+}
+
 }  // namespace
 
 namespace tlb {
@@ -353,45 +391,81 @@ int tlb_batch_config(tlb_batch* B, int threads, int rows_small, int rows_large, 
     return tlb::clear_error();
 }
 
-int tlb_batch_tune(tlb_batch* B, int trial_steps, int out_config[4], double* out_ms_per_step)
+int64_t tlb_batch_tune_scratch_bytes(tlb_batch* B)
+{
+    if (!B) return err(TLB_EINVAL, "null batch handle");
+    tlb::clear_error();
+    return tune_scratch_bytes(B);
+}
+
+int tlb_batch_tune(tlb_batch* B, int trial_steps_n, void* dev_scratch, int64_t scratch_bytes, int out_config[4],
+                   double* out_ms_per_step)
 {
     int rc = check_batch(B);
     if (rc) return rc;
-    if (trial_steps < 1) return err(TLB_EINVAL, "trial_steps must be >= 1");
+    if (trial_steps_n < 1) return err(TLB_EINVAL, "trial_steps must be >= 1");
     if (B->members.empty()) return err(TLB_ESTATE, "empty batch");
+    for (size_t i = 0; i < B->members.size(); i++) {
+        const tlb_lattice* L = B->members[i];
+        if (!L->have_params || !L->have_fields) return err(TLB_ESTATE, "member %zu has no state", i);
+    }
+    const int64_t need = tune_scratch_bytes(B);
+    if (!dev_scratch || ((uintptr_t)dev_scratch) % kAlign) return err(TLB_EINVAL, "scratch must be 256-byte aligned device memory");
+    if (scratch_bytes < need)
+        return err(TLB_ENOMEM, "tuning scratch has %lld bytes, needs %lld", (long long)scratch_bytes, (long long)need);
     B_CUDA(cudaStreamSynchronize(B->stream));
     cudaEvent_t e0, e1;
     B_CUDA(cudaEventCreate(&e0));
-    B_CUDA(cudaEventCreate(&e1));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return err(TLB_ECUDA, "cudaEventCreate failed");
+    }
     const int shapes[][3] = {{128, 16, 16}, {128, 8, 16}, {128, 8, 32}, {128, 16, 32},
                              {64, 8, 16}, {64, 16, 16}, {64, 8, 32}, {64, 16, 32}};
+    const int saved[4] = {B->variant, B->rows_small, B->rows_large, B->small_ny};
     double best = 1e30;
     int best_i = 0;
-    for (int i = 0; i < (int)(sizeof shapes / sizeof shapes[0]); i++) {
+    rc = copy_cu(B, (char*)dev_scratch, true);
+    for (int i = 0; rc == TLB_OK && i < (int)(sizeof shapes / sizeof shapes[0]); i++) {
         B->variant = shapes[i][0] == 64 ? 0 : 1;
         B->rows_small = shapes[i][1];
         B->rows_large = shapes[i][2];
         B->small_ny = 128;
         B->dirty = true;
-        if ((rc = advance(B, 2, false))) break;  // warm-up (also rebuilds the lists)
-        B_CUDA(cudaEventRecord(e0, B->stream));
-        if ((rc = advance(B, trial_steps, false))) break;
-        B_CUDA(cudaEventRecord(e1, B->stream));
-        B_CUDA(cudaEventSynchronize(e1));
+        if ((rc = trial_steps(B, 2))) break;  // warm-up (also rebuilds the lists)
+        cudaError_t ce = cudaEventRecord(e0, B->stream);
+        if (ce == cudaSuccess && (rc = trial_steps(B, trial_steps_n)) == TLB_OK) ce = cudaEventRecord(e1, B->stream);
+        if (rc) break;
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
         float ms = 0;
-        B_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms / trial_steps < best) {
-            best = ms / trial_steps;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) {
+            rc = err(TLB_ECUDA, "tuner timing failed: %s", cudaGetErrorString(ce));
+            break;
+        }
+        if (ms / trial_steps_n < best) {
+            best = ms / trial_steps_n;
             best_i = i;
         }
     }
+    // put back the c_i u planes the trial steps overwrote (the distributions
+    // of the current buffer were only read)
+    const int rc_restore = copy_cu(B, (char*)dev_scratch, false);
+    const cudaError_t es = cudaStreamSynchronize(B->stream);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc) return rc;
+    B->dirty = true;
+    if (rc || rc_restore) {
+        B->variant = saved[0];
+        B->rows_small = saved[1];
+        B->rows_large = saved[2];
+        B->small_ny = saved[3];
+        return rc ? rc : rc_restore;
+    }
+    if (es != cudaSuccess) return err(TLB_ECUDA, "batch stream: %s", cudaGetErrorString(es));
     B->variant = shapes[best_i][0] == 64 ? 0 : 1;
     B->rows_small = shapes[best_i][1];
     B->rows_large = shapes[best_i][2];
-    B->dirty = true;
     if (out_config) {
         out_config[0] = shapes[best_i][0];
         out_config[1] = shapes[best_i][1];

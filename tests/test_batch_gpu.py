@@ -1,4 +1,5 @@
-"""Batched execution: a lattice's result is the same alone and in a batch.
+"""Batched execution: every member matches the FP64 oracle, and a lattice's
+result is the same alone and in a batch.
 
 The batch runs the same per-tile and per-node device code as tlb_step, with
 the member's parameters read from its device descriptor instead of kernel
@@ -13,7 +14,10 @@ and tuning.
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
+from oracle import OracleLattice
+from parity import assert_bounded, assert_oracle_parity, plane_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -22,8 +26,25 @@ TOL = dict(fp64=1e-12, fp32=1e-5)
 
 
 def same(a, m, precision):
-    sa, sm = a.state(), m.state()
-    return float(np.abs(sa - sm).max() / max(np.abs(sa).max(), 1e-6)) < TOL[precision]
+    """Per-plane relative max-norm (parity.plane_errors) of two raw states."""
+    return float(plane_errors(m.state(), a.state()).max()) < TOL[precision]
+
+
+def oracle_of(w):
+    O = OracleLattice(w.nx, w.ny, w.edges, w.mask, w.params)
+    O.set_fields(w.c1, w.c2, w.ux, w.uy, w.p)
+    return O
+
+
+def _members_for_oracle():
+    """A mixed population: random walls, solids and densities, velocity lids
+    (two of them), a curved wetting cylinder with a falling compound drop and
+    a drops-on-wall lattice."""
+    ws = _mix(5, seed=41)
+    ws.append(W.compound_drop_on_cylinder(nx=96, ny=144, R_cyl=12, R_core=7, R_shell=13, We=10.0, theta=40.0,
+                                          cyl_center=(48, 40), drop_center=(48, 80)))
+    ws.append(W.drops_on_wall(72, 5))
+    return ws
 
 
 @pytest.fixture(scope="module")
@@ -98,7 +119,7 @@ def test_tune_and_config_keep_results(T):
     B.config(64, 8, 32, 100)
     B.step(3)
     for L in alone:
-        L.step(8 * (2 + 2) + 3)
+        L.step(3)  # tuning advanced no member
     for a, m in zip(alone, mem):
         assert same(a, m, "fp32")
 
@@ -119,3 +140,81 @@ def test_batch_errors(T):
     assert e.value.code == T.ENOMEM
     B.remove(L)
     L.step(1)
+
+
+def test_fp64_batch_members_match_the_oracle(T):
+    """Each member of a mixed FP64 batch -- walls, solids, lids, a cylinder --
+    against its own oracle lattice at 1e-12 per field and per raw-state plane,
+    after odd and even step counts and a membership change."""
+    ws = _members_for_oracle()
+    mem = [T.lattice_from_workload(w, "fp64") for w in ws]
+    orc = [oracle_of(w) for w in ws]
+    B = T.Batch("fp64", max_lattices=len(ws))
+    for L in mem[:-2]:
+        B.add(L)
+    B.step(5)                      # odd: members end on the other buffer
+    B.remove(mem[2])
+    B.add(mem[-2])
+    B.add(mem[-1])
+    B.step(8)
+    B.step(3)
+    steps = [16, 16, 5, 16, 16, 11, 11]
+    for L, O, n, w in zip(mem, orc, steps, ws):
+        O.step(n)
+        assert_oracle_parity(L, O, w.params, what=f"batch member {w.name}")
+    B.close()
+
+
+def test_fp64_mrt_batch_members_match_the_oracle(T):
+    ws = _mix(3, seed=43)
+    for w in ws:
+        w.params.update(collision=1.0, mrt_s_f=1.2, mrt_s_g=1.3)
+    mem = [T.lattice_from_workload(w, "fp64") for w in ws]
+    B = T.Batch("fp64", max_lattices=3)
+    for L in mem:
+        B.add(L)
+    B.step(9)
+    for L, w in zip(mem, ws):
+        O = oracle_of(w)
+        O.step(9)
+        assert_oracle_parity(L, O, w.params, what=f"MRT batch member {w.name}")
+    B.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_reduced_precision_batch_members_within_their_bounds_of_the_oracle(T, precision):
+    ws = _members_for_oracle()
+    mem = [T.lattice_from_workload(w, precision) for w in ws]
+    B = T.Batch(precision, max_lattices=len(ws))
+    for L in mem:
+        B.add(L)
+    B.step(60)
+    for L, w in zip(mem, ws):
+        O = oracle_of(w)
+        O.step(60)
+        assert_bounded(L.fields(), O.fields(), precision, what=f"batch member {w.name}")
+    B.close()
+
+
+def test_tune_leaves_members_unchanged(T):
+    """A batch's results are identical with and without a tune() call before
+    step(): the tuner's trial steps write only the spare buffers and the c_i u
+    planes it restores."""
+    ws = _mix(4, seed=5)
+    for precision in ("fp64", "fp32"):
+        plain = [T.lattice_from_workload(w, precision) for w in ws]
+        tuned = [T.lattice_from_workload(w, precision) for w in ws]
+        Bp, Bt = T.Batch(precision, max_lattices=4), T.Batch(precision, max_lattices=4)
+        for a, b in zip(plain, tuned):
+            Bp.add(a)
+            Bt.add(b)
+        Bp.step(3)
+        Bt.step(3)
+        cfg = Bt.tune(trial_steps=2)
+        Bp.config(cfg["threads"], cfg["rows_small"], cfg["rows_large"], cfg["small_ny"])
+        Bp.step(4)
+        Bt.step(4)
+        for a, b in zip(plain, tuned):
+            assert np.array_equal(a.state(), b.state())
+        Bp.close()
+        Bt.close()

@@ -1,37 +1,18 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 FP64 storage/arithmetic must match the oracle within 1e-12 relative max-norm
-on every macroscopic field and on the raw state (27 distributions and the 4
-c_i u planes of Eq. 19).  The relative max-norm of a field is
-max|gpu - oracle| / max(max|oracle|, floor), with a scale floor per field:
-1 for c_i and rho, 1e-4 for u, max sigma / 32 for p (the Laplace jump of a
-radius-32 drop) and max sigma / D for mu_i.  The mu floor matters: mu (Eq. 8)
-is the difference of two terms of size ~ 12 lambda/D c(1-c)(1-2c) and
-3/4 D lambda lap c that cancel at equilibrium, so its round-off is set by
-those terms, not by |mu|.
+on every macroscopic field and on every plane of the raw state (27
+distributions and the 4 c_i u planes of Eq. 19); the norms and their scale
+floors are defined in parity.py.
 """
 import numpy as np
 import pytest
 
 import workloads as W
 from oracle import OracleLattice
+from parity import FIELDS, TOL64, field_errors, floors, is_mrt, relnorm, state_error as _plane_state_error  # noqa: F401
 
 pytestmark = pytest.mark.gpu
-
-FIELDS = ("c1", "c2", "c3", "rho", "ux", "uy", "p", "mu1", "mu2", "mu3")
-FLOOR = dict(c1=1.0, c2=1.0, c3=1.0, rho=1.0, ux=1e-4, uy=1e-4)
-
-
-def floors(params):
-    smax = max(params["sigma12"], params["sigma13"], params["sigma23"])
-    return dict(FLOOR, p=smax / 32, mu1=smax / params["D"], mu2=smax / params["D"], mu3=smax / params["D"])
-
-
-TOL64 = 1e-12
-
-
-def relnorm(a, b, floor):
-    return float(np.abs(a - b).max() / max(float(np.abs(b).max()), floor))
 
 
 @pytest.fixture(scope="module")
@@ -53,24 +34,13 @@ def pair(T, w, precision="fp64"):
     return L, O
 
 
-def field_errors(L, O, params):
-    fg, fo = L.fields(), O.fields()
-    fl = floors(params)
-    return {k: relnorm(fg[k], fo[k], fl[k]) for k in FIELDS}
-
-
-def state_error(L, O):
-    sg, so = L.state(), O.state()
-    scale = max(float(np.abs(so).max()), 1e-6)
-    return float(np.abs(sg - so).max() / scale)
-
-
 def assert_parity(L, O, tol=TOL64, what=""):
-    errs = field_errors(L, O, O.param_dict)
+    """Every field and every raw-state plane of L within `tol` of the oracle."""
+    errs = field_errors(L.fields(), O.fields(), O.param_dict)
     bad = {k: v for k, v in errs.items() if not v < tol}
     assert not bad, f"{what} field errors above {tol}: {bad}"
-    se = state_error(L, O)
-    assert se < tol, f"{what} raw state error {se}"
+    se, q = _plane_state_error(L.state(), O.state(), is_mrt(O.param_dict))
+    assert se < tol, f"{what} raw state error {se:.3e} in plane {q}"
 
 
 def test_binary_drops_128x64_fp64_1000_and_2000_steps(T):

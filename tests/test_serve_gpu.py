@@ -1,12 +1,33 @@
 """Continuous-batching server: admission by HBM footprint, requests joining a
-running batch, and each result equal to the same job run alone (FP32 within
-1e-5 of the field scale, FP64 within 1e-12)."""
+running batch, each result equal to the same job run alone (FP32 within 1e-5
+of the field scale, FP64 within 1e-12), and each result against the FP64
+oracle run on the same request: FP64 at 1e-12 per field, FP32 / FP16 / BF16
+within their parity bounds, contact angles within 0.5 degrees."""
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
+from oracle import OracleLattice
+from parity import TOL64, assert_bounded, field_errors
 
 pytestmark = pytest.mark.gpu
+
+
+def oracle_fields(w, steps):
+    O = OracleLattice(w.nx, w.ny, w.edges, w.mask, w.params)
+    O.set_fields(w.c1, w.c2, w.ux, w.uy, w.p)
+    O.step(steps)
+    return O.fields()
+
+
+def budget_for(T, reqs, resident, caps):
+    """Room for the `resident` largest requests plus one batch workspace per precision."""
+    lib = T.load_library()
+    sizes = sorted(int(lib.tlb_workspace_bytes(r.workload.nx, r.workload.ny, T.PRECISIONS[r.precision]))
+                   for r in reqs)
+    nprec = len({r.precision for r in reqs})
+    return sum(sizes[-resident:]) + nprec * int(lib.tlb_batch_workspace_bytes(*caps))
 
 
 @pytest.fixture(scope="module")
@@ -26,15 +47,15 @@ def test_served_results_equal_runs_alone(T):
     reqs = []
     for i, (w, steps) in enumerate(jobs):
         reqs.append(Request(i, w, steps, ("fp32", "fp16", "fp32", "fp64", "bf16")[i % 5], arrival=0.02 * i))
-    lib = T.load_library()
-    sizes = sorted(int(lib.tlb_workspace_bytes(w.nx, w.ny, T.PRECISIONS[r.precision])) for r, (w, _) in zip(reqs, jobs))
-    budget = sizes[-1] + sizes[-2] + sizes[-3]  # at most a few resident at once
-    srv = Server(budget, max_lattices=8, chunk=64)
+    caps = (8, 4096, 1 << 16)
+    budget = budget_for(T, reqs, 3, caps)  # at most a few resident at once
+    srv = Server(budget, max_lattices=caps[0], chunk=64, max_tiles=caps[1], max_wall_nodes=caps[2])
     stats = srv.run(reqs)
     srv.close()
     s = stats.summary()
     assert s["requests"] == 10 and s["peak_resident_bytes"] <= budget
     assert 1 <= s["peak_resident_lattices"] < 10  # the budget forced queueing
+    assert s["tuned"], "the tuner picks a shape for the served mix"
     assert s["p99_s"] >= s["p50_s"] > 0
     for r in reqs:
         assert r.done is not None and r.admitted >= r.arrival - 1e-9
@@ -54,3 +75,36 @@ def test_request_larger_than_budget_is_rejected(T):
     with pytest.raises(ValueError):
         srv.run([Request(0, w, steps)])
     srv.close()
+
+
+def test_served_results_match_the_oracle(T):
+    """Served requests of every storage precision, each compared with the
+    FP64 oracle stepped the same number of steps on the same inputs."""
+    from paper_1710_09534_gb300.serve import Request, Server
+    jobs = W.served_requests(8, seed=11, lo=64, hi=160, steps_lo=60, steps_hi=240)
+    precs = ("fp64", "fp32", "fp16", "bf16")
+    reqs = [Request(i, w, steps, precs[i % 4], arrival=0.01 * i) for i, (w, steps) in enumerate(jobs)]
+    # two drop-on-wall requests long enough for a contact line to form
+    wd = W.binary_drops_on_wall()
+    reqs.append(Request(8, wd, 400, "fp32", arrival=0.05))
+    reqs.append(Request(9, wd, 400, "fp16", arrival=0.06))
+    caps = (8, 4096, 1 << 16)
+    srv = Server(budget_for(T, reqs, 4, caps), max_lattices=caps[0], chunk=50, max_tiles=caps[1],
+                 max_wall_nodes=caps[2])
+    srv.run(reqs)
+    srv.close()
+    for r in reqs:
+        fo = oracle_fields(r.workload, r.steps)
+        what = f"request {r.rid} ({r.workload.name}, {r.precision}, {r.steps} steps)"
+        if r.precision == "fp64":
+            errs = field_errors(r.fields, fo, r.workload.params)
+            bad = {k: v for k, v in errs.items() if not v < TOL64}
+            assert not bad, f"{what}: {bad}"
+        else:
+            assert_bounded(r.fields, fo, r.precision, what=what)
+        if r.rid >= 8:
+            for comp in ("c1", "c2"):
+                got, ref = oracle.contact_angle_deg(r.fields[comp]), oracle.contact_angle_deg(fo[comp])
+                assert len(got) == len(ref) >= 1, (what, comp)
+                for a, b in zip(got, ref):
+                    assert abs(a - b) < 0.5, (what, comp, a, b)

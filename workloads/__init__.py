@@ -320,7 +320,7 @@ def random_lattice(nx, ny, seed, edges=None, solids=("disc",), u_amp=0.01, rho=(
     ux[mask > 0] = 0
     uy[mask > 0] = 0
     sigma = tuple(rng.uniform(0.8e-3, 1.5e-3, 3))
-    # keep lambda_i > 0.5 lambda_T by drawing near-equal tensions
+    # keep lambda_i > 0.5 lambda_T (the well-posedness condition stated after Eq. 7) by drawing near-equal tensions
     th13, th23 = rng.uniform(40, 140, 2)
     try:
         th12 = theta12_from(*sigma, th13, th23)
