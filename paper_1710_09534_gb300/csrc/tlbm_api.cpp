@@ -422,7 +422,24 @@ int tlb_set_params(tlb_lattice* L, const tlb_params* p)
             P.Rw3[c] = w[c] * p->rho3 * itg;
             P.Kw3[c] = w[c] * P.kG3;
         }
+        P.p3tg3 = 3.0 * itg;
+        P.rg3x = p->rho3 * p->gx;
+        P.rg3y = p->rho3 * p->gy;
     }
+    // constants of the scaled stencils: grad9s = 12 grad, lap9s = 6 lap
+    for (int i = 0; i < 2; i++) {
+        P.Kl[i] = P.k12D * P.lam[i];
+        P.K34l6[i] = P.k34Dlam[i] / 6.0;
+        P.drho12[i] = P.drho[i] / 12.0;
+        P.aM6[i] = P.aM[i] / 6.0;
+        P.k3tau[i] = 3.0 / tau[i];
+    }
+    P.Kt = P.k12D * P.two_lamT;
+    // mu_1 - mu_3 = (1 + l3/l1) mu_1 + (l3/l2) mu_2, mu_2 - mu_3 = (l3/l1) mu_1 + (1 + l3/l2) mu_2
+    P.qa[0][0] = (1.0 + P.l3_l1) / 12.0;
+    P.qa[0][1] = P.l3_l2 / 12.0;
+    P.qa[1][0] = P.l3_l1 / 12.0;
+    P.qa[1][1] = (1.0 + P.l3_l2) / 12.0;
     P.mrt = mrt ? 1.0 : 0.0;
     P.mrt_s_f = mrt ? p->mrt_s_f : 1.0;
     P.mrt_s_g = mrt ? p->mrt_s_g : 1.0;

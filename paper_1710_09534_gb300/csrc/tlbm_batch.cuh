@@ -49,7 +49,8 @@ k_batch_interior(const LatDesc<R>* __restrict__ descs, const TileItem* __restric
     __shared__ PopStash<R, kStash ? BLOCK : 1> stash;
     __shared__ Prm<R> Ps;
     __shared__ int item_s;
-    static_assert(sizeof(Prm<R>) % sizeof(R) == 0 && sizeof(Prm<R>) / sizeof(R) <= BLOCK, "params fit one pass");
+    static_assert(sizeof(Prm<R>) % sizeof(R) == 0, "params are whole words");
+    constexpr int kWords = (int)(sizeof(Prm<R>) / sizeof(R));
     const int n = ctr->n_tiles;
     for (;;) {
         if (threadIdx.x == 0) item_s = atomicAdd(&ctr->next[parity], 1);
@@ -58,8 +59,8 @@ k_batch_interior(const LatDesc<R>* __restrict__ descs, const TileItem* __restric
         if (it >= n) break;
         const TileItem ti = items[it];
         const LatDesc<R>* d = descs + ti.lat;
-        if (threadIdx.x < sizeof(Prm<R>) / sizeof(R))
-            reinterpret_cast<R*>(&Ps)[threadIdx.x] = reinterpret_cast<const R*>(&d->P)[threadIdx.x];
+        for (int i = threadIdx.x; i < kWords; i += BLOCK)
+            reinterpret_cast<R*>(&Ps)[i] = reinterpret_cast<const R*>(&d->P)[i];
         __syncthreads();
         const Geo g = d->g;
         // members with equal densities and viscosities take the uniform-property

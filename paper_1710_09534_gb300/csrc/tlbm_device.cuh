@@ -72,6 +72,16 @@ struct Prm {
     R uni;            // 1 when both hold
     R inv_rho3, inv_taug3, omtg3, kG3;  // 1/rho, 1/tau_g, 1 - 1/tau_g, 1 - 1/(2 tau_g)
     R Rw3[2], Kw3[2];                   // rho w / tau_g, w (1 - 1/(2 tau_g)) per class
+    R p3tg3;                            // 3 / tau_g
+    R rg3x, rg3y;                       // rho g (the body force G of a uniform density)
+    // constants of the scaled stencils (grad9s = 12 grad, lap9s = 6 lap)
+    R Kl[2];          // 12 lambda_i / D
+    R Kt;             // 12 / D * 2 lambda_T
+    R K34l6[2];       // 3/4 D lambda_i / 6
+    R qa[2][2];       // F_s weights: (mu_i - mu_3) / 12 = qa[i][0] mu_1 + qa[i][1] mu_2
+    R drho12[2];      // (rho_i - rho_3) / 12
+    R aM6[2];         // (rho_i - rho_3) M_i / 6
+    R k3tau[2];       // 3 / tau_i
 };
 
 // Site of (x, y), possibly outside the lattice; on an inside site sets the
@@ -111,34 +121,39 @@ __device__ __forceinline__ double rcp(double a)
 __device__ __forceinline__ float rcp(float a) { return 1.0f / a; }
 
 // ---- stencils (Eqs. 20a, 20b): v[k] = chi(x + e_k) -----------------------
+// Both are returned scaled so that their weights are small integers (the
+// constant factor is folded into the constants that multiply them):
+// grad9s = 12 grad (w_k e_k / cs^2 is 1/3 on axis links, 1/12 on diagonals),
+// lap9s = 6 lap (2 w_k / cs^2 is 2/3 on axis links, 1/6 on diagonals, the
+// centre weight -10/3).
 template <typename R>
-__device__ __forceinline__ void grad9(const R v[9], R& gx, R& gy)
+__device__ __forceinline__ void grad9s(const R v[9], R& gx12, R& gy12)
 {
-    // w_k e_k / cs^2: 1/3 on axis links, 1/12 on diagonals
     const R d57 = v[5] - v[7], d86 = v[8] - v[6];
-    gx = fma(R(1.0 / 3.0), v[1] - v[3], R(1.0 / 12.0) * (d57 + d86));
-    gy = fma(R(1.0 / 3.0), v[2] - v[4], R(1.0 / 12.0) * (d57 - d86));
+    gx12 = fma(R(4), v[1] - v[3], d57 + d86);
+    gy12 = fma(R(4), v[2] - v[4], d57 - d86);
 }
 
 template <typename R>
-__device__ __forceinline__ R lap9(const R v[9])
+__device__ __forceinline__ R lap9s(const R v[9])
 {
-    // 2 w_k / cs^2: 2/3 on axis links, 1/6 on diagonals; centre weight -10/3
     const R ax = (v[1] + v[3]) + (v[2] + v[4]);
     const R dg = (v[5] + v[7]) + (v[6] + v[8]);
-    return fma(R(2.0 / 3.0), ax, fma(R(1.0 / 6.0), dg, R(-10.0 / 3.0) * v[0]));
+    return fma(R(4), ax, fma(R(-20), v[0], dg));
 }
 
-// ---- Eq. 8 for i = 1, 2 ---------------------------------------------------
+// ---- Eq. 8 for i = 1, 2, from the scaled Laplacians lap6_i = 6 lap c_i -------
+//   mu_i = 12/D [lambda_i c_i (1 - c_i)(1 - 2 c_i) - 2 lambda_T c1 c2 c3] - 3/4 D lambda_i lap c_i
 template <typename R>
-__device__ __forceinline__ void chem_pot(const Prm<R>& P, R c1, R c2, R lap1, R lap2, R& mu1, R& mu2)
+__device__ __forceinline__ void chem_pot(const Prm<R>& P, R c1, R c2, R lap6_1, R lap6_2, R& mu1, R& mu2)
 {
     const R c3 = R(1) - c1 - c2;
-    const R t = P.two_lamT * (c1 * c2) * c3;
-    const R b1 = fma(P.lam[0], c1 * (R(1) - c1) * fma(R(-2), c1, R(1)), -t);
-    const R b2 = fma(P.lam[1], c2 * (R(1) - c2) * fma(R(-2), c2, R(1)), -t);
-    mu1 = fma(P.k12D, b1, -P.k34Dlam[0] * lap1);
-    mu2 = fma(P.k12D, b2, -P.k34Dlam[1] * lap2);
+    const R tt = P.Kt * (c1 * c2) * c3;
+    // c (1 - c)(1 - 2c) = c (1 + c (2c - 3))
+    const R p1 = c1 * fma(c1, fma(R(2), c1, R(-3)), R(1));
+    const R p2 = c2 * fma(c2, fma(R(2), c2, R(-3)), R(1));
+    mu1 = fma(P.Kl[0], p1, -fma(P.K34l6[0], lap6_1, tt));
+    mu2 = fma(P.Kl[1], p2, -fma(P.K34l6[1], lap6_2, tt));
 }
 
 // ---- Eq. 42: c_ghost - c_f on a link into a wetting solid ----------------
@@ -154,8 +169,8 @@ __device__ __forceinline__ void wet_offset(const Prm<R>& P, R c1, R c2, R& o1, R
 template <typename R>
 struct Macro {
     R c1, c2, mu1, mu2, rho;
-    R g1x, g1y, g2x, g2y;   // grad c1, grad c2 (Eq. 20a)
-    R lm1, lm2;             // lap mu1, lap mu2 (Eq. 20b)
+    R g1x, g1y, g2x, g2y;   // 12 grad c1, 12 grad c2 (Eq. 20a, grad9s)
+    R lm1, lm2;             // 6 lap mu1, 6 lap mu2 (Eq. 20b, lap9s)
 };
 
 // Velocity, pressure and forces (Eqs. 12, 13b, 13c).
@@ -180,11 +195,14 @@ __device__ __forceinline__ R density(const Prm<R>& P, R c1, R c2)
 template <bool UNI = false, typename R>
 __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m, const R g[9], Hydro<R>& h)
 {
-    const R mu3 = -fma(P.l3_l1, m.mu1, P.l3_l2 * m.mu2);
-    const R q1 = m.mu1 - mu3, q2 = m.mu2 - mu3;
-    // F_s = sum_i mu_i grad c_i with grad c3 = -grad c1 - grad c2; G = rho g
-    h.Ftx = fma(q1, m.g1x, fma(q2, m.g2x, m.rho * P.gx));
-    h.Fty = fma(q1, m.g1y, fma(q2, m.g2y, m.rho * P.gy));
+    // F_s = sum_i mu_i grad c_i with grad c3 = -grad c1 - grad c2, i.e.
+    // sum_{i=1,2} (mu_i - mu_3) grad c_i, mu_3 from sum_i mu_i / lambda_i = 0;
+    // q_i = (mu_i - mu_3) / 12 against the scaled gradients; G = rho g
+    const R q1 = fma(P.qa[0][0], m.mu1, P.qa[0][1] * m.mu2);
+    const R q2 = fma(P.qa[1][0], m.mu1, P.qa[1][1] * m.mu2);
+    const R Gx = UNI ? P.rg3x : m.rho * P.gx, Gy = UNI ? P.rg3y : m.rho * P.gy;
+    h.Ftx = fma(q1, m.g1x, fma(q2, m.g2x, Gx));
+    h.Fty = fma(q1, m.g1y, fma(q2, m.g2y, Gy));
     const R g57 = g[5] - g[7], g86 = g[8] - g[6];
     const R mx = (g[1] - g[3]) + (g57 + g86);
     const R my = (g[2] - g[4]) + (g57 - g86);
@@ -198,8 +216,8 @@ __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m,
         h.a = R(0);
         h.inv_taug = P.inv_taug3;
     } else {
-        h.grx = fma(P.drho[0], m.g1x, P.drho[1] * m.g2x);
-        h.gry = fma(P.drho[0], m.g1y, P.drho[1] * m.g2y);
+        h.grx = fma(P.drho12[0], m.g1x, P.drho12[1] * m.g2x);
+        h.gry = fma(P.drho12[0], m.g1y, P.drho12[1] * m.g2y);
         const R inv_rho = rcp(m.rho);
         h.ux = fma(R(0.5), h.Ftx, mx) * inv_rho;
         h.uy = fma(R(0.5), h.Fty, my) * inv_rho;
@@ -207,40 +225,46 @@ __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m,
         // p = cs^2/(1 - w0) [sum_{k!=0} g_k + u.grad rho / 2 + rho s_0(u)], s_0 = -w0 u.u / (2 cs^2)
         const R ug = fma(h.ux, h.grx, h.uy * h.gry);
         h.p = R(0.6) * fma(R(-2.0 / 3.0) * m.rho, h.usq, fma(R(0.5), ug, sumg));
-        h.a = fma(P.aM[0], m.lm1, P.aM[1] * m.lm2);
+        h.a = fma(P.aM6[0], m.lm1, P.aM6[1] * m.lm2);
         const R nu = fma(m.c2, P.dnu[1], fma(m.c1, P.dnu[0], P.nu[2]));
         h.inv_taug = rcp(fma(R(3), nu, R(0.5)));
     }
 }
 
 // Per-node precomputation of the BGK update (Eqs. 1a, 1b, 2a, 2b, 4, 11a,
-// 11b, 45), arranged so that each direction costs a few fused operations:
-//   f'_k = (1 - 1/tau) f_k + f^eq_k / tau + F_k
-//   g'_k = (1 - 1/tau_g) g_k + g^eq_k / tau_g + G_k
-//   g^eq_k / tau_g = w (3p + rho q_k) / tau_g,  q_k = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u
-//   G_k = w (1 - 1/(2 tau_g)) [q_k (e - u).H + (e - u).T] + 3 w e.F_a,
-//   H = grad rho + 3 (F_s + G), T = 3 (F_s + G)   (s_k = w q_k)
+// 11b, 45), arranged so that a direction k and its opposite k-bar share most
+// of their arithmetic.  With s = +1 for k and -1 for k-bar, E = e_k . u and
+// beta = 3E:
+//   f'^i = (1 - 1/tau_i) f^i + A_i + s V_i,
+//     A_i = eta_i w mu_i / tau_i,  V_i = w e_k . Q_i,
+//     Q_i = (3 c_i / tau_i) u + 3 (1 - 1/(2 tau_i)) d/dt(c_i u)   (Eqs. 2a, 11a, 19)
+//   g'   = (1 - 1/tau_g) g + Sym + s Anti,
+// where, with q = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u = a + s beta
+// (a = 4.5 E^2 - 1.5 u.u), the equilibrium and source of g (Eqs. 2b, 4, 11b),
+//   g^eq / tau_g + G_k = Rw q + Pw + Kw [q (e - u).H + (e - u).T] + 3 w e.F_a,
+//   Rw = w rho / tau_g, Pw = 3 w p / tau_g, Kw = w (1 - 1/(2 tau_g)),
+//   H = grad rho + 3 (F_s + G), T = 3 (F_s + G), F_a = a_F u,
+// expand to
+//   Sym  = beta KX + a RX + PX,   Anti = a KX + beta RX + AX,
+//   KX = Kw e.H, RX = Rw - Kw u.H, PX = Pw - Kw u.T,
+//   AX = Kw e.T + 3 w a_F e.u   (= KX with equal densities, where H = T).
+// Every term is small (of the size of the populations themselves): the O(1)
+// parts of Rw and of (q + 1) never meet in a difference.
 template <typename R, bool UNI = false>
 struct Collider {
-    R eu[4];            // e.u for +x, +y, (1,1), (1,-1)
-    R A1[2], A2[2];     // f^eq / tau constant parts per class, with the source folded in below
-    R B1[2], B2[2];     // 3 w c_i / tau_i per class
-    R F1[4], F2[4];     // F^i for the 4 components (sign applied per direction)
+    R A1[2], A2[2];     // per class (0 axis, 1 diagonal)
+    R V1[4], V2[4];     // per component: +x, +y, (1,1), (1,-1)
     R E1, E2;           // f^{i,eq}_0 / tau_i
-    R omt1, omt2, omtg;
+    R b[4];             // beta = 3 e.u per component
     R t0;               // -1.5 u.u
-    R H[4], T[4], uH, uT;
-    R Z[4];             // 3 w e.F_a per component (class weight included)
-    R Pw[2], Rw[2], Kw[2];  // 3 p w / tau_g, rho w / tau_g, w (1 - 1/(2 tau_g))
+    R KX[4], RX[2], PX[2], AX[4];
+    R omt1, omt2, omtg;
     R P0;               // g^eq_0 / tau_g + G_0
 
     __device__ __forceinline__ void build(const Prm<R>& P, const Macro<R>& m, const Hydro<R>& h,
                                           R d1x, R d1y, R d2x, R d2y)
     {
-        eu[0] = h.ux;
-        eu[1] = h.uy;
-        eu[2] = h.ux + h.uy;
-        eu[3] = h.ux - h.uy;
+        constexpr R w9 = R(1.0 / 9.0), w36 = R(1.0 / 36.0), w0 = R(4.0 / 9.0);
         // order parameters
         omt1 = P.omt[0];
         omt2 = P.omt[1];
@@ -250,91 +274,108 @@ struct Collider {
         for (int c = 0; c < 2; c++) {
             A1[c] = P.aw[0][c] * m.mu1;
             A2[c] = P.aw[1][c] * m.mu2;
-            B1[c] = P.bw[0][c] * m.c1;
-            B2[c] = P.bw[1][c] * m.c2;
         }
-        F1[0] = P.sw[0][0] * d1x;
-        F1[1] = P.sw[0][0] * d1y;
-        F1[2] = P.sw[0][1] * (d1x + d1y);
-        F1[3] = P.sw[0][1] * (d1x - d1y);
-        F2[0] = P.sw[1][0] * d2x;
-        F2[1] = P.sw[1][0] * d2y;
-        F2[2] = P.sw[1][1] * (d2x + d2y);
-        F2[3] = P.sw[1][1] * (d2x - d2y);
+        const R k1 = P.k3tau[0] * m.c1, k2 = P.k3tau[1] * m.c2;
+        const R Q1x = fma(k1, h.ux, P.src_f[0] * d1x), Q1y = fma(k1, h.uy, P.src_f[0] * d1y);
+        const R Q2x = fma(k2, h.ux, P.src_f[1] * d2x), Q2y = fma(k2, h.uy, P.src_f[1] * d2y);
+        V1[0] = w9 * Q1x;
+        V1[1] = w9 * Q1y;
+        V1[2] = w36 * (Q1x + Q1y);
+        V1[3] = w36 * (Q1x - Q1y);
+        V2[0] = w9 * Q2x;
+        V2[1] = w9 * Q2y;
+        V2[2] = w36 * (Q2x + Q2y);
+        V2[3] = w36 * (Q2x - Q2y);
         // hydrodynamics
-        const R itg = h.inv_taug;
+        b[0] = R(3) * h.ux;
+        b[1] = R(3) * h.uy;
+        b[2] = b[0] + b[1];
+        b[3] = b[0] - b[1];
         t0 = R(-1.5) * h.usq;
+        const R itg = h.inv_taug;
         const R Tx = R(3) * h.Ftx, Ty = R(3) * h.Fty;
-        T[0] = Tx;
-        T[1] = Ty;
-        T[2] = Tx + Ty;
-        T[3] = Tx - Ty;
-        uT = fma(h.ux, Tx, h.uy * Ty);
-        const R p3 = R(3) * h.p * itg;
-        Pw[0] = R(1.0 / 9.0) * p3;
-        Pw[1] = R(1.0 / 36.0) * p3;
-        R kG;
+        const R uT = fma(h.ux, Tx, h.uy * Ty);
+        R uH, kG, Kw[2];
         if constexpr (UNI) {
             // H = T (grad rho = 0), F_a = 0; tau_g and rho are constants
             omtg = P.omtg3;
             kG = P.kG3;
-            Rw[0] = P.Rw3[0];
-            Rw[1] = P.Rw3[1];
             Kw[0] = P.Kw3[0];
             Kw[1] = P.Kw3[1];
             uH = uT;
+            KX[0] = Kw[0] * Tx;
+            KX[1] = Kw[0] * Ty;
+            KX[2] = Kw[1] * (Tx + Ty);
+            KX[3] = Kw[1] * (Tx - Ty);
+            const R p3 = h.p * P.p3tg3;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                RX[c] = fma(-Kw[c], uT, P.Rw3[c]);
+                PX[c] = fma(-Kw[c], uT, (c == 0 ? w9 : w36) * p3);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) AX[c] = KX[c];
         } else {
             omtg = R(1) - itg;
             kG = fma(R(-0.5), itg, R(1));
-            const R Hx = h.grx + Tx, Hy = h.gry + Ty;
-            H[0] = Hx;
-            H[1] = Hy;
-            H[2] = Hx + Hy;
-            H[3] = Hx - Hy;
-            uH = fma(h.ux, Hx, h.uy * Hy);
-            const R za = R(3.0 / 9.0) * h.a, zd = R(3.0 / 36.0) * h.a;  // 3 w_c a, F_a = u a
-            Z[0] = za * eu[0];
-            Z[1] = za * eu[1];
-            Z[2] = zd * eu[2];
-            Z[3] = zd * eu[3];
+            Kw[0] = w9 * kG;
+            Kw[1] = w36 * kG;
             const R ri = m.rho * itg;
-            Rw[0] = R(1.0 / 9.0) * ri;
-            Rw[1] = R(1.0 / 36.0) * ri;
-            Kw[0] = R(1.0 / 9.0) * kG;
-            Kw[1] = R(1.0 / 36.0) * kG;
+            const R Hx = h.grx + Tx, Hy = h.gry + Ty;
+            uH = fma(h.ux, Hx, h.uy * Hy);
+            KX[0] = Kw[0] * Hx;
+            KX[1] = Kw[0] * Hy;
+            KX[2] = Kw[1] * (Hx + Hy);
+            KX[3] = Kw[1] * (Hx - Hy);
+            const R p3 = R(3) * h.p * itg;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const R wc = c == 0 ? w9 : w36;
+                RX[c] = fma(-Kw[c], uH, wc * ri);
+                PX[c] = fma(-Kw[c], uT, wc * p3);
+            }
+            // AX = Kw e.T + 3 w a_F e.u = Kw e.T + (w a_F) beta
+            const R wa0 = w9 * h.a, wa1 = w36 * h.a;
+            AX[0] = fma(wa0, b[0], Kw[0] * Tx);
+            AX[1] = fma(wa0, b[1], Kw[0] * Ty);
+            AX[2] = fma(wa1, b[2], Kw[1] * (Tx + Ty));
+            AX[3] = fma(wa1, b[3], Kw[1] * (Tx - Ty));
         }
         // k = 0: g^eq_0 = 3p (w0 - 1) + rho w0 t0; G_0 = -w0 kG (t0 u.H + u.T)
-        const R w0 = R(4.0 / 9.0);
         const R geq0 = fma(m.rho * w0, t0, R(3) * (w0 - R(1)) * h.p);
         P0 = fma(geq0, itg, -(w0 * kG) * fma(t0, uH, uT));
     }
 
-    template <int K>
-    __device__ __forceinline__ void post(R f1k, R f2k, R gk, R& o1, R& o2, R& og) const
+    // rest direction
+    __device__ __forceinline__ void post0(R f10, R f20, R g0, R& o1, R& o2, R& og) const
     {
-        if constexpr (K == 0) {
-            o1 = fma(omt1, f1k, E1);
-            o2 = fma(omt2, f2k, E2);
-            og = fma(omtg, gk, P0);
-        } else {
-            constexpr int C = comp(K), W = wclass(K);
-            constexpr R s = R(sgn(K));
-            const R e = s * eu[C];
-            const R q = fma(e, fma(R(4.5), e, R(3)), t0);
-            o1 = fma(omt1, f1k, fma(B1[W], e, fma(s, F1[C], A1[W])));
-            o2 = fma(omt2, f2k, fma(B2[W], e, fma(s, F2[C], A2[W])));
-            const R Y = fma(s, T[C], -uT);
-            if constexpr (UNI) {
-                // X = Y: G_k = w kG (q + 1) (e - u).T
-                og = fma(omtg, gk, fma(Kw[W], fma(q, Y, Y), fma(Rw[W], q, Pw[W])));
-            } else {
-                const R X = fma(s, H[C], -uH);
-                const R Gk = fma(Kw[W], fma(q, X, Y), s * Z[C]);
-                og = fma(omtg, gk, fma(Rw[W], q, Pw[W]) + Gk);
-            }
-        }
+        o1 = fma(omt1, f10, E1);
+        o2 = fma(omt2, f20, E2);
+        og = fma(omtg, g0, P0);
+    }
+
+    // direction K (one of 1, 2, 5, 8: s = +1) and its opposite opp(K)
+    template <int K>
+    __device__ __forceinline__ void pair(R f1p, R f2p, R gp, R f1m, R f2m, R gm, R& o1p, R& o2p, R& ogp, R& o1m,
+                                         R& o2m, R& ogm) const
+    {
+        static_assert(K == 1 || K == 2 || K == 5 || K == 8, "pair<K> takes the direction with s = +1");
+        constexpr int C = comp(K), W = wclass(K);
+        o1p = fma(omt1, f1p, A1[W] + V1[C]);
+        o1m = fma(omt1, f1m, A1[W] - V1[C]);
+        o2p = fma(omt2, f2p, A2[W] + V2[C]);
+        o2m = fma(omt2, f2m, A2[W] - V2[C]);
+        const R beta = b[C];
+        const R a = fma(beta, R(0.5) * beta, t0);
+        const R sym = fma(beta, KX[C], fma(a, RX[W], PX[W]));
+        const R anti = fma(a, KX[C], fma(beta, RX[W], AX[C]));
+        ogp = fma(omtg, gp, sym + anti);
+        ogm = fma(omtg, gm, sym - anti);
     }
 };
+
+// The four directions with s = +1 of the opposite pairs (k, opp(k)).
+__host__ __device__ constexpr int pair_dir(int p) { return p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 8)); }
 
 // Equilibria alone (Eqs. 2a, 2b), used by the lid (Eq. 51) and set-up.
 template <typename R>

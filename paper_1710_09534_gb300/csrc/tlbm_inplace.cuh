@@ -190,7 +190,7 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
                 v2[k] = sc2[sl][t + ex(k)];
             }
             R mu1, mu2;
-            chem_pot(P, v1[0], v2[0], lap9(v1), lap9(v2), mu1, mu2);
+            chem_pot(P, v1[0], v2[0], lap9s(v1), lap9s(v2), mu1, mu2);
             const int ml = (ym + 9) % 3;
             sm1[ml][t] = mu1;
             sm2[ml][t] = mu2;
@@ -214,10 +214,10 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
             m.c2 = v2[0];
             m.mu1 = w1[0];
             m.mu2 = w2[0];
-            grad9(v1, m.g1x, m.g1y);
-            grad9(v2, m.g2x, m.g2y);
-            m.lm1 = lap9(w1);
-            m.lm2 = lap9(w2);
+            grad9s(v1, m.g1x, m.g1y);
+            grad9s(v2, m.g2x, m.g2y);
+            m.lm1 = lap9s(w1);
+            m.lm2 = lap9s(w2);
             m.rho = UNI ? P.rho[2] : density(P, m.c1, m.c2);
         }
         if (!PREFETCH) load_g();

@@ -203,18 +203,28 @@ __device__ __forceinline__ void collide_all(const Collider<R, UNI>& col, const R
 {
     constexpr bool ff = Store<S>::kLo;
     R d1 = R(0), d2 = R(0);  // sum_k (f_k - o'_k) over the moving directions
-    static_for<1, 9>([&](auto kc) {
-        constexpr int K = decltype(kc)::value;
-        R f1k, f2k, o1, o2, og;
-        load(kc, f1k, f2k);
-        col.template post<K>(f1k, f2k, gv[K], o1, o2, og);
-        o1 = as_stored<S>(K, o1);
-        o2 = as_stored<S>(9 + K, o2);
+    // the directions go in opposite pairs (k, k-bar), which share most of
+    // their arithmetic; both inputs of a pair are read before either output
+    // is written (the in-place update relies on it)
+    static_for<0, 4>([&](auto pc) {
+        constexpr int K = pair_dir(decltype(pc)::value);
+        constexpr int KB = opp(K);
+        std::integral_constant<int, K> kc;
+        std::integral_constant<int, KB> kbc;
+        R a1, a2, b1, b2, oa1, oa2, oag, ob1, ob2, obg;
+        load(kc, a1, a2);
+        load(kbc, b1, b2);
+        col.template pair<K>(a1, a2, gv[K], b1, b2, gv[KB], oa1, oa2, oag, ob1, ob2, obg);
+        oa1 = as_stored<S>(K, oa1);
+        oa2 = as_stored<S>(9 + K, oa2);
+        ob1 = as_stored<S>(KB, ob1);
+        ob2 = as_stored<S>(9 + KB, ob2);
         if constexpr (ff) {
-            d1 += f1k - o1;
-            d2 += f2k - o2;
+            d1 += (a1 - oa1) + (b1 - ob1);
+            d2 += (a2 - oa2) + (b2 - ob2);
         }
-        store(kc, o1, o2, og);
+        store(kc, oa1, oa2, oag);
+        store(kbc, ob1, ob2, obg);
     });
     std::integral_constant<int, 0> k0;
     R f10, f20, o1, o2, og;
@@ -223,14 +233,14 @@ __device__ __forceinline__ void collide_all(const Collider<R, UNI>& col, const R
         R l1, l2;
         load_lo(l1, l2);
         // the collision sees the rest population as hi + lo
-        col.template post<0>(f10 + l1, f20 + l2, gv[0], o1, o2, og);
+        col.post0(f10 + l1, f20 + l2, gv[0], o1, o2, og);
         R h1, h2, lo1, lo2;
         rest_add(f10, l1, d1, h1, lo1);
         rest_add(f20, l2, d2, h2, lo2);
         store(k0, h1, h2, og);
         store_lo(lo1, lo2);
     } else {
-        col.template post<0>(f10, f20, gv[0], o1, o2, og);
+        col.post0(f10, f20, gv[0], o1, o2, og);
         store(k0, o1, o2, og);
     }
 }
@@ -283,52 +293,13 @@ __device__ __forceinline__ void collide_all(const MrtNode<R>& col, const R gv[9]
 
 // In-place form of the BGK collide_all: the post-collision populations of
 // direction k land in the location the input of direction k-bar came from
-// (and vice versa), so the directions go in opposite pairs, both inputs read
-// before either output is written.  Otherwise the same update.
+// (and vice versa); collide_all already reads both inputs of an opposite pair
+// before it writes either output.
 template <typename S, typename R, bool UNI, typename Load, typename LoadLo, typename St, typename StLo>
 __device__ __forceinline__ void collide_all_inplace(const Collider<R, UNI>& col, const R gv[9], Load load,
                                                     LoadLo load_lo, St store, StLo store_lo)
 {
-    constexpr bool ff = Store<S>::kLo;
-    R d1 = R(0), d2 = R(0);
-    static_for<0, 4>([&](auto pc) {
-        constexpr int P = decltype(pc)::value;
-        constexpr int K = P == 0 ? 1 : (P == 1 ? 2 : (P == 2 ? 5 : 6));
-        constexpr int KB = opp(K);
-        std::integral_constant<int, K> kc;
-        std::integral_constant<int, KB> kbc;
-        R a1, a2, b1, b2, oa1, oa2, oag, ob1, ob2, obg;
-        load(kc, a1, a2);
-        load(kbc, b1, b2);
-        col.template post<K>(a1, a2, gv[K], oa1, oa2, oag);
-        col.template post<KB>(b1, b2, gv[KB], ob1, ob2, obg);
-        oa1 = as_stored<S>(K, oa1);
-        oa2 = as_stored<S>(9 + K, oa2);
-        ob1 = as_stored<S>(KB, ob1);
-        ob2 = as_stored<S>(9 + KB, ob2);
-        if constexpr (ff) {
-            d1 += (a1 - oa1) + (b1 - ob1);
-            d2 += (a2 - oa2) + (b2 - ob2);
-        }
-        store(kc, oa1, oa2, oag);
-        store(kbc, ob1, ob2, obg);
-    });
-    std::integral_constant<int, 0> k0;
-    R f10, f20, o1, o2, og;
-    load(k0, f10, f20);
-    if constexpr (ff) {
-        R l1, l2;
-        load_lo(l1, l2);
-        col.template post<0>(f10 + l1, f20 + l2, gv[0], o1, o2, og);
-        R h1, h2, lo1, lo2;
-        rest_add(f10, l1, d1, h1, lo1);
-        rest_add(f20, l2, d2, h2, lo2);
-        store(k0, h1, h2, og);
-        store_lo(lo1, lo2);
-    } else {
-        col.template post<0>(f10, f20, gv[0], o1, o2, og);
-        store(k0, o1, o2, og);
-    }
+    collide_all<S, R>(col, gv, load, load_lo, store, store_lo);
 }
 // MRT already reads all nine populations before writing any.
 template <typename S, typename R, typename Load, typename LoadLo, typename St, typename StLo>
@@ -490,7 +461,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                 v2[k] = sc2[sl][t + ex(k)];
             }
             R mu1, mu2;
-            chem_pot(P, v1[0], v2[0], lap9(v1), lap9(v2), mu1, mu2);
+            chem_pot(P, v1[0], v2[0], lap9s(v1), lap9s(v2), mu1, mu2);
             const int ml = (ym + 9) % 3;
             sm1[ml][t] = mu1;
             sm2[ml][t] = mu2;
@@ -514,10 +485,10 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
             m.c2 = v2[0];
             m.mu1 = w1[0];
             m.mu2 = w2[0];
-            grad9(v1, m.g1x, m.g1y);
-            grad9(v2, m.g2x, m.g2y);
-            m.lm1 = lap9(w1);
-            m.lm2 = lap9(w2);
+            grad9s(v1, m.g1x, m.g1y);
+            grad9s(v2, m.g2x, m.g2y);
+            m.lm1 = lap9s(w1);
+            m.lm2 = lap9s(w2);
             m.rho = UNI ? P.rho[2] : density(P, m.c1, m.c2);
         }
         if (!PREFETCH) {
@@ -649,7 +620,7 @@ __device__ __forceinline__ void window_macros(const Geo& g, const uint8_t* __res
                         v2[k] = cc2;
                     }
                 }
-                chem_pot(P, cc1, cc2, lap9(v1), lap9(v2), mu1, mu2);
+                chem_pot(P, cc1, cc2, lap9s(v1), lap9s(v2), mu1, mu2);
             }
             wm1[j - 1][i - 1] = mu1;
             wm2[j - 1][i - 1] = mu2;
@@ -680,10 +651,10 @@ __device__ __forceinline__ void window_macros(const Geo& g, const uint8_t* __res
     m.c2 = wc2[2][2];
     m.mu1 = wm1[1][1];
     m.mu2 = wm2[1][1];
-    grad9(v1, m.g1x, m.g1y);
-    grad9(v2, m.g2x, m.g2y);
-    m.lm1 = lap9(w1);
-    m.lm2 = lap9(w2);
+    grad9s(v1, m.g1x, m.g1y);
+    grad9s(v2, m.g2x, m.g2y);
+    m.lm1 = lap9s(w1);
+    m.lm2 = lap9s(w2);
     m.rho = density(P, m.c1, m.c2);
 }
 

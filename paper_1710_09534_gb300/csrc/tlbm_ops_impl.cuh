@@ -57,6 +57,19 @@ inline Prm<R> cast_prm(const Prm<double>& d)
         r.Rw3[c] = R(d.Rw3[c]);
         r.Kw3[c] = R(d.Kw3[c]);
     }
+    r.p3tg3 = R(d.p3tg3);
+    r.rg3x = R(d.rg3x);
+    r.rg3y = R(d.rg3y);
+    for (int i = 0; i < 2; i++) {
+        r.Kl[i] = R(d.Kl[i]);
+        r.K34l6[i] = R(d.K34l6[i]);
+        r.drho12[i] = R(d.drho12[i]);
+        r.aM6[i] = R(d.aM6[i]);
+        r.k3tau[i] = R(d.k3tau[i]);
+        r.qa[i][0] = R(d.qa[i][0]);
+        r.qa[i][1] = R(d.qa[i][1]);
+    }
+    r.Kt = R(d.Kt);
     return r;
 }
 
