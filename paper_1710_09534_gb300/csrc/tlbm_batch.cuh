@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
 k_batch_interior(const LatDesc<R>* __restrict__ descs, const TileItem* __restrict__ items,
                  BatchCounters* __restrict__ ctr, int parity)
 {
-    __shared__ TileRings<R, BLOCK> sh;
+    __shared__ ColRings<R, BLOCK> sh;
     constexpr bool kStash = kStashPops && std::is_same<R, float>::value && !MRT;
     __shared__ PopStash<R, kStash ? BLOCK : 1> stash;
     __shared__ Prm<R> Ps;

@@ -2,5 +2,5 @@
 #include "tlbm_ops_impl.cuh"
 
 namespace tlb {
-const Ops& ops_f16_mrt() { return OpsImpl<__half, float, kBlock32, kRows32, kPrefetch32, kMinB32, true>::table(); }
+const Ops& ops_f16_mrt() { return OpsImpl<__half, float, kBlock32, kRows32, kPrefetch32, kMinB32Mrt, true>::table(); }
 }  // namespace tlb

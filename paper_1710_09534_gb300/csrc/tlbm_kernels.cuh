@@ -354,6 +354,26 @@ struct TileRings {
     R m1[3][BLOCK], m2[3][BLOCK];  // mu rings (row r in slot (r + 9) % 3)
 };
 
+// Column sums of the two-buffer interior tile.  For one row r of an order
+// parameter c and each column j of the strip:
+//   A_j = c(j, r-1) + 4 c(j, r) + c(j, r+1),   D_j = c(j, r+1) - c(j, r-1),
+// from which the scaled stencils of Eq. 20 at (j, r) need only the two
+// neighbouring columns:
+//   12 d_x c = A_{j+1} - A_{j-1},   12 d_y c = D_{j-1} + 4 D_j + D_{j+1},
+//   6 lap c  = A_{j-1} + A_{j+1} + 4 (c(j, r-1) + c(j, r+1) - 5 c(j, r)).
+// Each thread forms them for its own column from the c values it summed
+// itself (kept in registers), so every stencil costs a few operations per
+// node and the 3x3 neighbourhood is never gathered.  A and D of row r live in
+// slot (r + 9) % 3 (written two barriers before the last read of the slot
+// that the next write replaces); M: the A of mu for the row being updated
+// (the general update's lap mu).
+template <typename R, int BLOCK>
+struct ColRings {
+    R A1[3][BLOCK], A2[3][BLOCK];
+    R D1[3][BLOCK], D2[3][BLOCK];
+    R M1[BLOCK], M2[BLOCK];
+};
+
 // Per-thread copy of the 18 order-parameter populations (and the two rest lo
 // parts) that phase 1 reads for the c sums of a row, kept until the same
 // thread updates that row two iterations later (row r in slot (r + 9) % 3).
@@ -374,13 +394,9 @@ constexpr bool kStashPops = TLB_STASH32 != 0;
 template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT, bool UNI = false, bool STASH = false>
 __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
                                               const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
-                                              int bx, int by, int rows, TileRings<R, BLOCK>& sh,
+                                              int bx, int by, int rows, ColRings<R, BLOCK>& sh,
                                               PopStash<R, BLOCK>* stash = nullptr)
 {
-    R(&sc1)[5][BLOCK] = sh.c1;
-    R(&sc2)[5][BLOCK] = sh.c2;
-    R(&sm1)[3][BLOCK] = sh.m1;
-    R(&sm2)[3][BLOCK] = sh.m2;
     const long long PL = g.plane;
     const int t = threadIdx.x;
     const int x0 = bx * (BLOCK - 4);
@@ -398,6 +414,10 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
     const int y1 = min(y0 + rows, g.ny);
     const int dir = (by & 1) ? -1 : 1;
     const int iters = (y1 - y0) + 4;
+    // this column's c of rows yc, yc - dir, yc - 2 dir and mu of rows ym,
+    // ym - dir, ym - 2 dir (index 0 the newest)
+    R ca[3] = {R(0), R(0), R(0)}, cb[3] = {R(0), R(0), R(0)};
+    R ma[3] = {R(0), R(0), R(0)}, mb[3] = {R(0), R(0), R(0)};
 
     for (int it = 0; it < iters; it++) {
         const int yc = dir > 0 ? y0 - 2 + it : y1 + 1 - it;  // c row of this iteration
@@ -417,7 +437,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
 #pragma unroll
             for (int q = 0; q < 4; q++) cp[q] = R(cu[q * PL + ou]);
         }
-        // 1) c of row yc (Eq. 13a)
+        // 1) c of row yc (Eq. 13a); column sums of row ym
         {
             int yw = yc;
             bool in = col_in && yc < g.ny + 2;
@@ -446,49 +466,63 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                     order_params<R>(fA, PL, oc, a, b);
                 }
             }
-            const int sl = (yc + 10) % 5;
-            sc1[sl][t] = a;
-            sc2[sl][t] = b;
+            ca[2] = ca[1];
+            ca[1] = ca[0];
+            ca[0] = a;
+            cb[2] = cb[1];
+            cb[1] = cb[0];
+            cb[0] = b;
+            if (it >= 2) {
+                // row ym = yc - dir: its rows ym - 1, ym + 1 are ca[0], ca[2]
+                // in the order of the march
+                const int sl = (ym + 9) % 3;
+                sh.A1[sl][t] = fma(R(4), ca[1], ca[0] + ca[2]);
+                sh.A2[sl][t] = fma(R(4), cb[1], cb[0] + cb[2]);
+                sh.D1[sl][t] = dir > 0 ? ca[0] - ca[2] : ca[2] - ca[0];
+                sh.D2[sl][t] = dir > 0 ? cb[0] - cb[2] : cb[2] - cb[0];
+            }
         }
         __syncthreads();
         // 2) mu of row ym (Eq. 8 with Eq. 20b)
         if (it >= 2 && t >= 1 && t < BLOCK - 1) {
-            R v1[9], v2[9];
-#pragma unroll
-            for (int k = 0; k < 9; k++) {
-                const int sl = (ym + ey(k) + 10) % 5;
-                v1[k] = sc1[sl][t + ex(k)];
-                v2[k] = sc2[sl][t + ex(k)];
-            }
+            const int sl = (ym + 9) % 3;
+            const R lap1 = fma(R(4), fma(R(-5), ca[1], ca[0] + ca[2]), sh.A1[sl][t - 1] + sh.A1[sl][t + 1]);
+            const R lap2 = fma(R(4), fma(R(-5), cb[1], cb[0] + cb[2]), sh.A2[sl][t - 1] + sh.A2[sl][t + 1]);
             R mu1, mu2;
-            chem_pot(P, v1[0], v2[0], lap9s(v1), lap9s(v2), mu1, mu2);
-            const int ml = (ym + 9) % 3;
-            sm1[ml][t] = mu1;
-            sm2[ml][t] = mu2;
+            chem_pot(P, ca[1], cb[1], lap1, lap2, mu1, mu2);
+            ma[2] = ma[1];
+            ma[1] = ma[0];
+            ma[0] = mu1;
+            mb[2] = mb[1];
+            mb[1] = mb[0];
+            mb[0] = mu2;
+            if constexpr (!UNI) {
+                // column sums of mu for row yu = ym - dir (the general update's lap mu)
+                sh.M1[t] = fma(R(4), ma[1], ma[0] + ma[2]);
+                sh.M2[t] = fma(R(4), mb[1], mb[0] + mb[2]);
+            }
         }
         __syncthreads();
         // 3) update of row yu
         if (!upd) continue;
         Macro<R> m;
         {
-            R v1[9], v2[9], w1[9], w2[9];
-#pragma unroll
-            for (int k = 0; k < 9; k++) {
-                const int sl = (yu + ey(k) + 10) % 5;
-                const int ml = (yu + ey(k) + 9) % 3;
-                v1[k] = sc1[sl][t + ex(k)];
-                v2[k] = sc2[sl][t + ex(k)];
-                w1[k] = sm1[ml][t + ex(k)];
-                w2[k] = sm2[ml][t + ex(k)];
+            // c(yu) = ca[2]; mu(yu) = ma[1] (mu rows yu + dir, yu - dir: ma[0], ma[2])
+            const int su = (yu + 9) % 3;
+            m.c1 = ca[2];
+            m.c2 = cb[2];
+            m.mu1 = ma[1];
+            m.mu2 = mb[1];
+            m.g1x = sh.A1[su][t + 1] - sh.A1[su][t - 1];
+            m.g2x = sh.A2[su][t + 1] - sh.A2[su][t - 1];
+            m.g1y = fma(R(4), sh.D1[su][t], sh.D1[su][t - 1] + sh.D1[su][t + 1]);
+            m.g2y = fma(R(4), sh.D2[su][t], sh.D2[su][t - 1] + sh.D2[su][t + 1]);
+            if constexpr (UNI) {
+                m.lm1 = m.lm2 = R(0);  // F_a vanishes with equal densities
+            } else {
+                m.lm1 = fma(R(4), fma(R(-5), ma[1], ma[0] + ma[2]), sh.M1[t - 1] + sh.M1[t + 1]);
+                m.lm2 = fma(R(4), fma(R(-5), mb[1], mb[0] + mb[2]), sh.M2[t - 1] + sh.M2[t + 1]);
             }
-            m.c1 = v1[0];
-            m.c2 = v2[0];
-            m.mu1 = w1[0];
-            m.mu2 = w2[0];
-            grad9s(v1, m.g1x, m.g1y);
-            grad9s(v2, m.g2x, m.g2y);
-            m.lm1 = lap9s(w1);
-            m.lm2 = lap9s(w2);
             m.rho = UNI ? P.rho[2] : density(P, m.c1, m.c2);
         }
         if (!PREFETCH) {
@@ -548,7 +582,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
 k_step_interior(const S* __restrict__ fA, S* __restrict__ fB, CuT<S>* __restrict__ cu,
                 const uint8_t* __restrict__ cls, Geo g, Prm<R> P, int rows)
 {
-    __shared__ TileRings<R, BLOCK> sh;
+    __shared__ ColRings<R, BLOCK> sh;
     if constexpr (kStashPops && std::is_same<R, float>::value && !MRT) {
         __shared__ PopStash<R, BLOCK> stash;
         interior_tile<S, R, BLOCK, PREFETCH, MRT, UNI, true>(fA, fB, cu, cls, g, P, blockIdx.x, blockIdx.y, rows, sh,

@@ -110,8 +110,13 @@ inline const Ops& ops_for(int precision, bool mrt)
 #ifndef TLB_PREFETCH32
 #define TLB_PREFETCH32 1
 #endif
+// the FP32-arithmetic MRT update keeps two 9-moment vectors per distribution
+// live: at 5 blocks per SM (96 registers) it spills, at 4 (128) it does not
+#ifndef TLB_MINB32_MRT
+#define TLB_MINB32_MRT 4
+#endif
 constexpr int kBlock64 = TLB_BLOCK64, kRows64 = TLB_ROWS64, kMinB64 = TLB_MINB64;
-constexpr int kBlock32 = TLB_BLOCK32, kRows32 = TLB_ROWS32, kMinB32 = TLB_MINB32;
+constexpr int kBlock32 = TLB_BLOCK32, kRows32 = TLB_ROWS32, kMinB32 = TLB_MINB32, kMinB32Mrt = TLB_MINB32_MRT;
 constexpr bool kPrefetch32 = TLB_PREFETCH32 != 0;
 
 
