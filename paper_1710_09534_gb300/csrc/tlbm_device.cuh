@@ -192,7 +192,8 @@ __device__ __forceinline__ R density(const Prm<R>& P, R c1, R c2)
 // UNI (equal densities and viscosities): grad rho, u.grad rho and F_a vanish
 // identically and rho, tau_g are constants, so those terms are skipped (the
 // general form would add exact zeros).
-template <bool UNI = false, typename R>
+// SE: the g populations are given in units of 2^SE (see collide_all).
+template <bool UNI = false, int SE = 0, typename R>
 __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m, const R g[9], Hydro<R>& h)
 {
     // F_s = sum_i mu_i grad c_i with grad c3 = -grad c1 - grad c2, i.e.
@@ -204,9 +205,15 @@ __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m,
     h.Ftx = fma(q1, m.g1x, fma(q2, m.g2x, Gx));
     h.Fty = fma(q1, m.g1y, fma(q2, m.g2y, Gy));
     const R g57 = g[5] - g[7], g86 = g[8] - g[6];
-    const R mx = (g[1] - g[3]) + (g57 + g86);
-    const R my = (g[2] - g[4]) + (g57 - g86);
-    const R sumg = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
+    R mx = (g[1] - g[3]) + (g57 + g86);
+    R my = (g[2] - g[4]) + (g57 - g86);
+    R sumg = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
+    if constexpr (SE != 0) {
+        constexpr R inv = R(1.0 / double(1 << SE));
+        mx *= inv;
+        my *= inv;
+        sumg *= inv;
+    }
     if constexpr (UNI) {
         h.grx = h.gry = R(0);
         h.ux = fma(R(0.5), h.Ftx, mx) * P.inv_rho3;
@@ -261,6 +268,9 @@ struct Collider {
     R omt1, omt2, omtg;
     R P0;               // g^eq_0 / tau_g + G_0
 
+    // SE: the moving populations and g_0 are handled in units of 2^SE (see
+    // collide_all); the constants that add to them are scaled to match.
+    template <int SE = 0>
     __device__ __forceinline__ void build(const Prm<R>& P, const Macro<R>& m, const Hydro<R>& h,
                                           R d1x, R d1y, R d2x, R d2y)
     {
@@ -344,6 +354,24 @@ struct Collider {
         // k = 0: g^eq_0 = 3p (w0 - 1) + rho w0 t0; G_0 = -w0 kG (t0 u.H + u.T)
         const R geq0 = fma(m.rho * w0, t0, R(3) * (w0 - R(1)) * h.p);
         P0 = fma(geq0, itg, -(w0 * kG) * fma(t0, uH, uT));
+        if constexpr (SE != 0) {
+            constexpr R sc = R(1 << SE);
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                A1[c] *= sc;
+                A2[c] *= sc;
+                RX[c] *= sc;
+                PX[c] *= sc;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                V1[c] *= sc;
+                V2[c] *= sc;
+                KX[c] *= sc;
+                AX[c] *= sc;
+            }
+            P0 *= sc;
+        }
     }
 
     // rest direction
@@ -454,9 +482,11 @@ struct MrtNode {
     R H[4], T[4], uH, uT, Z[4];
     R s_f[2][9], s_g[9];
 
+    template <int SE = 0>
     __device__ __forceinline__ void build(const Prm<R>& P, const Macro<R>& m, const Hydro<R>& h,
                                           R d1x, R d1y, R d2x, R d2y)
     {
+        static_assert(SE == 0, "the MRT update works in plain units");
         c[0] = m.c1;
         c[1] = m.c2;
         emu[0] = P.eta[0] * m.mu1;

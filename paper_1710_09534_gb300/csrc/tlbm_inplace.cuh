@@ -121,14 +121,13 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
         const int yc = dir > 0 ? y0 - 2 + it : y1 + 1 - it;
         const int ym = yc - dir;
         const int yu = yc - 2 * dir;
-        bool upd = updater && it >= 4;
-        long long ou = 0;
-        if (upd) {
-            ou = (long long)yu * g.pitch + xs;
-            upd = (cls[ou] & CLS_INTERIOR) != 0;
-        }
+        // the update node's loads are issued before its node class is known
+        // (see interior_tile); all their addresses are inside the lattice
+        const bool in_rows = updater && it >= 4;
+        const long long ou = in_rows ? (long long)yu * g.pitch + xs : 0;
+        const bool upd = in_rows && (cls[ou] & CLS_INTERIOR) != 0;
         R gv[9], cp[4];
-        PushOffsets po(g, upd ? xs : 0, upd ? yu : 0);
+        PushOffsets po(g, in_rows ? xs : 0, in_rows ? yu : 0);
         // g of direction k: own slot k (even) or slot k-bar of x - e_k (odd)
         auto load_g = [&]() {
             static_for<0, 9>([&](auto kc) {
@@ -157,7 +156,7 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
         auto load_all_f = [&]() {
             static_for<0, 9>([&](auto kc) { load_f(kc, f1[decltype(kc)::value], f2[decltype(kc)::value]); });
         };
-        if (PREFETCH && upd) {
+        if (PREFETCH && in_rows) {
             load_g();
             if constexpr (kPre) load_all_f();
         }
@@ -247,7 +246,7 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
                 l1 = ld_lo<R, false>(f, 0, PL, ou);
                 l2 = ld_lo<R, false>(f, 1, PL, ou);
             },
-            [&](auto kc, R o1, R o2, R og) {
+            [&](auto kc, auto o1, auto o2, auto og) {
                 constexpr int K = decltype(kc)::value;
                 const long long d = (ODD && K != 0) ? po.template dest<K>() : ou;
                 constexpr int q = ODD ? K : opp(K);
@@ -277,9 +276,9 @@ k_step_interior_ip(S* f, CuT<S>* __restrict__ cu, const R* __restrict__ cpl, con
 // a launch of their own before the others: LID selects which kind a launch
 // takes.
 // ---------------------------------------------------------------------------
-template <bool ODD, typename S, typename R>
+template <bool ODD, typename S, typename V1, typename V2, typename VG>
 __device__ __forceinline__ void store_ip(const Geo& g, const uint8_t* __restrict__ cls, S* f, int K, int x, int y,
-                                         long long o, R o1, R o2, R og)
+                                         long long o, V1 o1, V2 o2, VG og)
 {
     const long long PL = g.plane;
     long long d = o;
@@ -290,7 +289,11 @@ __device__ __forceinline__ void store_ip(const Geo& g, const uint8_t* __restrict
             q = K;
         } else {
             d = o;  // wall: bounce back into own slot k-bar (Eq. 44)
-            if (s == ST_VOID) o1 = o2 = og = R(0);  // leaves through the lid; nothing comes in
+            if (s == ST_VOID) {  // leaves through the lid; nothing comes in
+                o1 = V1{};
+                o2 = V2{};
+                og = VG{};
+            }
         }
     }
     st_pop(f, q, PL, d, o1);
@@ -316,7 +319,7 @@ __device__ __forceinline__ void wall_node_ip(S* f, CuT<S>* __restrict__ cu, cons
         int slot;
         return src_ip<ODD>(g, cls, k, xn, yn, on, off, slot) ? ld_pop<R, false>(f, base + slot, PL, off) : R(0);
     };
-    auto store = [&](auto kc, R o1, R o2, R og) { store_ip<ODD>(g, cls, f, decltype(kc)::value, x, y, o, o1, o2, og); };
+    auto store = [&](auto kc, auto o1, auto o2, auto og) { store_ip<ODD>(g, cls, f, decltype(kc)::value, x, y, o, o1, o2, og); };
     auto store_lo = [&](R l1, R l2) {
         st_lo(f, 0, PL, o, l1);
         st_lo(f, 1, PL, o, l2);

@@ -38,6 +38,17 @@ __device__ __forceinline__ R sum9(const R* v)
 {
     return v[0] + (((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8])));
 }
+// The same with the moving populations in units of 2^SE (v[0] in plain units).
+template <int SE, typename R>
+__device__ __forceinline__ R sum9s(const R* v)
+{
+    if constexpr (SE == 0) {
+        return sum9(v);
+    } else {
+        const R m = ((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8]));
+        return fma(R(1.0 / double(1 << SE)), m, v[0]);
+    }
+}
 
 // Storage formats of the distributions (template parameter S):
 //   double  27 FP64 planes (q = 0..8 f^1_k, 9..17 f^2_k, 18..26 g_k).
@@ -98,18 +109,27 @@ __device__ __forceinline__ T ld_any(const T* p)
 }
 
 // Population q (0..26) of node offset o, as the arithmetic type R (for the
-// rest populations of the paired formats: the hi part).
-template <typename R, bool NC = true, typename S>
+// rest populations of the paired formats: the hi part).  RAW: a 16-bit
+// population in the units it is stored in (FP16: 2^kF16ScaleExp times its
+// value), so that an update working in those units skips the scaling.
+template <typename R, bool NC = true, bool RAW = false, typename S>
 __device__ __forceinline__ R ld_pop(const S* __restrict__ f, int q, long long PL, long long o)
 {
     if constexpr (Store<S>::k16) {
         if (q == 0 || q == 9) return R(ld_any<NC>(rest_region(f, PL) + (q == 9 ? PL : 0) + o));
+        const float v = dec16(S{}, ld_any<NC>(reinterpret_cast<const unsigned short*>(f) + q * PL + o));
+        if constexpr (RAW) return R(v);
         constexpr float inv = 1.0f / float(1 << Store<S>::kScaleExp);
-        return R(dec16(S{}, ld_any<NC>(reinterpret_cast<const unsigned short*>(f) + q * PL + o)) * inv);
+        return R(v * inv);
     } else {
         return R(ld_any<NC>(f + q * PL + o));
     }
 }
+
+// A 16-bit population already encoded (the bits as stored).
+struct Bits16 {
+    unsigned short b;
+};
 // lo part of rest population i (0: f^1_0, 1: f^2_0); zero for FP64
 template <typename R, bool NC = true, typename S>
 __device__ __forceinline__ R ld_lo(const S* __restrict__ f, int i, long long PL, long long o)
@@ -133,7 +153,10 @@ __device__ __forceinline__ R as_stored(int q, R v)
 template <typename S, typename R>
 __device__ __forceinline__ void st_pop(S* __restrict__ f, int q, long long PL, long long o, R v)
 {
-    if constexpr (Store<S>::k16) {
+    if constexpr (std::is_same<R, Bits16>::value) {
+        static_assert(Store<S>::k16, "encoded values belong to a 16-bit format");
+        reinterpret_cast<unsigned short*>(f)[q * PL + o] = v.b;
+    } else if constexpr (Store<S>::k16) {
         if (q == 0 || q == 9) {
             rest_region(f, PL)[(q == 9 ? PL : 0) + o] = float(v);
         } else {
@@ -197,11 +220,36 @@ __device__ __forceinline__ void rest_add(float hi, float lo, float d, float& nhi
 // (Sterbenz), which covers near-equilibrium nodes, and exact for 16-bit
 // storage -- while the O(1) rest value itself is never rounded; FP64 uses the
 // direct form.
-template <typename S, typename R, bool UNI, typename Load, typename LoadLo, typename St, typename StLo>
+//
+// SE: the moving populations (and g_0) are passed in and produced in units of
+// 2^SE (SE = kF16ScaleExp when the update works in the units of FP16
+// storage, 0 otherwise).  With 16-bit storage the outputs are encoded once
+// here and handed to `store` as Bits16; the rest pair sees the decoded
+// (stored) values, so the mass bookkeeping is unchanged.
+template <typename S, typename R, int SE = 0, bool UNI, typename Load, typename LoadLo, typename St, typename StLo>
 __device__ __forceinline__ void collide_all(const Collider<R, UNI>& col, const R gv[9], Load load, LoadLo load_lo,
                                             St store, StLo store_lo)
 {
     constexpr bool ff = Store<S>::kLo;
+    constexpr bool k16 = Store<S>::k16;
+    static_assert(SE == 0 || (k16 && SE == Store<S>::kScaleExp), "scaled units are those of FP16 storage");
+    // encode a value for 16-bit storage and decode it back (in the units of the values)
+    auto enc = [](R v) -> Bits16 {
+        if constexpr (k16) {
+            constexpr float sc = SE ? 1.0f : float(1 << Store<S>::kScaleExp);
+            return Bits16{enc16(S{}, float(v) * sc)};
+        } else {
+            return Bits16{0};
+        }
+    };
+    auto dec = [](Bits16 h) -> R {
+        if constexpr (k16) {
+            constexpr float inv = SE ? 1.0f : 1.0f / float(1 << Store<S>::kScaleExp);
+            return R(dec16(S{}, h.b) * inv);
+        } else {
+            return R(0);
+        }
+    };
     R d1 = R(0), d2 = R(0);  // sum_k (f_k - o'_k) over the moving directions
     // the directions go in opposite pairs (k, k-bar), which share most of
     // their arithmetic; both inputs of a pair are read before either output
@@ -215,17 +263,26 @@ __device__ __forceinline__ void collide_all(const Collider<R, UNI>& col, const R
         load(kc, a1, a2);
         load(kbc, b1, b2);
         col.template pair<K>(a1, a2, gv[K], b1, b2, gv[KB], oa1, oa2, oag, ob1, ob2, obg);
-        oa1 = as_stored<S>(K, oa1);
-        oa2 = as_stored<S>(9 + K, oa2);
-        ob1 = as_stored<S>(KB, ob1);
-        ob2 = as_stored<S>(9 + KB, ob2);
-        if constexpr (ff) {
-            d1 += (a1 - oa1) + (b1 - ob1);
-            d2 += (a2 - oa2) + (b2 - ob2);
+        if constexpr (k16) {
+            const Bits16 ha1 = enc(oa1), ha2 = enc(oa2), hb1 = enc(ob1), hb2 = enc(ob2);
+            d1 += (a1 - dec(ha1)) + (b1 - dec(hb1));
+            d2 += (a2 - dec(ha2)) + (b2 - dec(hb2));
+            store(kc, ha1, ha2, enc(oag));
+            store(kbc, hb1, hb2, enc(obg));
+        } else {
+            if constexpr (ff) {
+                d1 += (a1 - oa1) + (b1 - ob1);
+                d2 += (a2 - oa2) + (b2 - ob2);
+            }
+            store(kc, oa1, oa2, oag);
+            store(kbc, ob1, ob2, obg);
         }
-        store(kc, oa1, oa2, oag);
-        store(kbc, ob1, ob2, obg);
     });
+    if constexpr (SE != 0) {
+        constexpr R inv = R(1.0 / double(1 << SE));
+        d1 *= inv;
+        d2 *= inv;
+    }
     std::integral_constant<int, 0> k0;
     R f10, f20, o1, o2, og;
     load(k0, f10, f20);
@@ -237,7 +294,8 @@ __device__ __forceinline__ void collide_all(const Collider<R, UNI>& col, const R
         R h1, h2, lo1, lo2;
         rest_add(f10, l1, d1, h1, lo1);
         rest_add(f20, l2, d2, h2, lo2);
-        store(k0, h1, h2, og);
+        if constexpr (k16) store(k0, h1, h2, enc(og));
+        else store(k0, h1, h2, og);
         store_lo(lo1, lo2);
     } else {
         col.post0(f10, f20, gv[0], o1, o2, og);
@@ -246,11 +304,13 @@ __device__ __forceinline__ void collide_all(const Collider<R, UNI>& col, const R
 }
 
 // The same contract with the MRT collision: the nine populations of each
-// distribution are relaxed together in moment space, so all are loaded first.
-template <typename S, typename R, typename Load, typename LoadLo, typename St, typename StLo>
+// distribution are relaxed together in moment space, so all are loaded first
+// (in plain units: SE = 0).
+template <typename S, typename R, int SE = 0, typename Load, typename LoadLo, typename St, typename StLo>
 __device__ __forceinline__ void collide_all(const MrtNode<R>& col, const R gv[9], Load load, LoadLo load_lo,
                                             St store, StLo store_lo)
 {
+    static_assert(SE == 0, "the MRT update works in plain units");
     constexpr bool ff = Store<S>::kLo;
     R f1[9], f2[9], o1[9], o2[9], og[9];
     static_for<0, 9>([&](auto kc) {
@@ -388,6 +448,12 @@ struct PopStash {
 #define TLB_STASH32 1
 #endif
 constexpr bool kStashPops = TLB_STASH32 != 0;
+// Load the order-parameter populations of the next c row one iteration ahead
+// (register double buffering).
+#ifndef TLB_PIPE32
+#define TLB_PIPE32 0
+#endif
+constexpr bool kPipeRows = TLB_PIPE32 != 0;
 
 // One tile: strip bx (columns bx*(BLOCK-4) .. +BLOCK-5), segment by (rows
 // by*rows .. +rows-1, marching up for even by and down for odd by).
@@ -399,6 +465,9 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
 {
     const long long PL = g.plane;
     const int t = threadIdx.x;
+    // the BGK update of FP16 storage works in the units the populations are
+    // stored in (2^kF16ScaleExp times their value)
+    constexpr int SE = (Store<S>::k16 && !MRT) ? Store<S>::kScaleExp : 0;
     const int x0 = bx * (BLOCK - 4);
     const int xs = x0 - 2 + t;  // this thread's column, in [-2, nx + BLOCK]
     // wrapped column (periodic x) and whether it holds data at all; only
@@ -418,22 +487,56 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
     // ym - dir, ym - 2 dir (index 0 the newest)
     R ca[3] = {R(0), R(0), R(0)}, cb[3] = {R(0), R(0), R(0)};
     R ma[3] = {R(0), R(0), R(0)}, mb[3] = {R(0), R(0), R(0)};
+    // PIPE: the 18 order-parameter populations (and the two rest lo parts) of
+    // the next iteration's c row are loaded one iteration ahead, so that their
+    // memory latency overlaps a whole iteration instead of stalling phase 1
+    constexpr bool PIPE = STASH && kPipeRows;
+    auto load_c_row = [&](int ycr, R (&v)[18], R (&l)[2]) {
+        int yw = ycr;
+        bool in = col_in && ycr < g.ny + 2;
+        if (ycr < 0 || ycr >= g.ny) {
+            if (g.edge[2] == EDGE_PERIODIC) yw = ycr < 0 ? ycr + g.ny : ycr - g.ny;
+            else in = false;
+        }
+        if (in) {
+            const long long oc = (long long)yw * g.pitch + xw;
+#pragma unroll
+            for (int k = 0; k < 18; k++) v[k] = ld_pop<R, true, SE != 0>(fA, k, PL, oc);
+            l[0] = ld_lo<R>(fA, 0, PL, oc);
+            l[1] = ld_lo<R>(fA, 1, PL, oc);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 18; k++) v[k] = R(0);
+            l[0] = l[1] = R(0);
+        }
+    };
+    R nv[18], nl[2];
+    if constexpr (PIPE) load_c_row(dir > 0 ? y0 - 2 : y1 + 1, nv, nl);
 
     for (int it = 0; it < iters; it++) {
         const int yc = dir > 0 ? y0 - 2 + it : y1 + 1 - it;  // c row of this iteration
         const int ym = yc - dir;                              // mu row
         const int yu = yc - 2 * dir;                          // updated row
-        bool upd = updater && it >= 4;
-        long long ou = 0;
-        if (upd) {
-            ou = (long long)yu * g.pitch + xs;
-            upd = (cls[ou] & CLS_INTERIOR) != 0;
-        }
-        // g and c_i u of the update node: first touches of HBM, issued early
-        R gv[9], cp[4];
-        if (PREFETCH && upd) {
+        R cv[18], cl[2];
+        if constexpr (PIPE) {
 #pragma unroll
-            for (int k = 0; k < 9; k++) gv[k] = ld_pop<R>(fA, 18 + k, PL, ou);
+            for (int k = 0; k < 18; k++) cv[k] = nv[k];
+            cl[0] = nl[0];
+            cl[1] = nl[1];
+            if (it + 1 < iters) load_c_row(yc + dir, nv, nl);
+        }
+        // the update node (row yu of this column, if any): its g and c_i u
+        // are the first touches of HBM, issued before its node class is
+        // known (the load of the class is consumed only in phase 3, so its
+        // latency overlaps phases 1 and 2; a node that is not interior was
+        // read for nothing)
+        const bool in_rows = updater && it >= 4;
+        const long long ou = in_rows ? (long long)yu * g.pitch + xs : 0;
+        const bool upd = in_rows && (cls[ou] & CLS_INTERIOR) != 0;
+        R gv[9], cp[4];
+        if (PREFETCH && in_rows) {
+#pragma unroll
+            for (int k = 0; k < 9; k++) gv[k] = ld_pop<R, true, SE != 0>(fA, 18 + k, PL, ou);
 #pragma unroll
             for (int q = 0; q < 4; q++) cp[q] = R(cu[q * PL + ou]);
         }
@@ -446,13 +549,21 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                 else in = false;
             }
             R a = R(0), b = R(0);
-            if (in) {
+            if (PIPE || in) {
                 const long long oc = (long long)yw * g.pitch + xw;
                 if constexpr (STASH) {
-                    R v[18];
+                    R v[18], l1, l2;
+                    if constexpr (PIPE) {
 #pragma unroll
-                    for (int k = 0; k < 18; k++) v[k] = ld_pop<R>(fA, k, PL, oc);
-                    const R l1 = ld_lo<R>(fA, 0, PL, oc), l2 = ld_lo<R>(fA, 1, PL, oc);
+                        for (int k = 0; k < 18; k++) v[k] = cv[k];
+                        l1 = cl[0];
+                        l2 = cl[1];
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 18; k++) v[k] = ld_pop<R, true, SE != 0>(fA, k, PL, oc);
+                        l1 = ld_lo<R>(fA, 0, PL, oc);
+                        l2 = ld_lo<R>(fA, 1, PL, oc);
+                    }
                     R(&st)[20][BLOCK] = stash->v[(yc + 9) % 3];
 #pragma unroll
                     for (int k = 0; k < 18; k++) st[k][t] = v[k];
@@ -460,8 +571,8 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                     st[19][t] = l2;
                     v[0] += l1;
                     v[9] += l2;
-                    a = sum9(v);
-                    b = sum9(v + 9);
+                    a = sum9s<SE>(v);
+                    b = sum9s<SE>(v + 9);
                 } else {
                     order_params<R>(fA, PL, oc, a, b);
                 }
@@ -527,12 +638,12 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         }
         if (!PREFETCH) {
 #pragma unroll
-            for (int k = 0; k < 9; k++) gv[k] = ld_pop<R>(fA, 18 + k, PL, ou);
+            for (int k = 0; k < 9; k++) gv[k] = ld_pop<R, true, SE != 0>(fA, 18 + k, PL, ou);
 #pragma unroll
             for (int q = 0; q < 4; q++) cp[q] = R(cu[q * PL + ou]);
         }
         Hydro<R> h;
-        hydro_from_g<UNI>(P, m, gv, h);
+        hydro_from_g<UNI, SE>(P, m, gv, h);
         // Eq. 19: d/dt (c_i u) against the stored product of the previous step
         const R c1ux = m.c1 * h.ux, c1uy = m.c1 * h.uy, c2ux = m.c2 * h.ux, c2uy = m.c2 * h.uy;
         cu[0 * PL + ou] = CuT<S>(c1ux);
@@ -540,18 +651,18 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         cu[2 * PL + ou] = CuT<S>(c2ux);
         cu[3 * PL + ou] = CuT<S>(c2uy);
         CollideOf<MRT, R, UNI> col;
-        col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
+        col.template build<SE>(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
         const PushOffsets po(g, xs, yu);
         const int su = (yu + 9) % 3;
-        collide_all<S, R>(col, gv,
+        collide_all<S, R, SE>(col, gv,
             [&](auto kc, R& f1k, R& f2k) {
                 constexpr int K = decltype(kc)::value;
                 if constexpr (STASH) {
                     f1k = stash->v[su][K][t];
                     f2k = stash->v[su][9 + K][t];
                 } else {
-                    f1k = ld_pop<R>(fA, K, PL, ou);
-                    f2k = ld_pop<R>(fA, 9 + K, PL, ou);
+                    f1k = ld_pop<R, true, SE != 0>(fA, K, PL, ou);
+                    f2k = ld_pop<R, true, SE != 0>(fA, 9 + K, PL, ou);
                 }
             },
             [&](R& l1, R& l2) {
@@ -563,7 +674,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                     l2 = ld_lo<R>(fA, 1, PL, ou);
                 }
             },
-            [&](auto kc, R o1, R o2, R og) {
+            [&](auto kc, auto o1, auto o2, auto og) {
                 constexpr int K = decltype(kc)::value;
                 const long long d = (K == 0) ? ou : po.template dest<K>();
                 st_pop(fB, K, PL, d, o1);
@@ -736,9 +847,9 @@ struct PlaneFetch {
 // Push of one post-collision triple along direction K from node (x, y) with
 // the wall rules: into a fluid node, back into slot K-bar on a solid link
 // (Eq. 44), or out through the lid.
-template <int K, typename S, typename R>
+template <int K, typename S, typename V1, typename V2, typename VG>
 __device__ __forceinline__ void push_wall(const Geo& g, const uint8_t* __restrict__ cls, S* __restrict__ fB,
-                                          int x, int y, long long o, R o1, R o2, R og)
+                                          int x, int y, long long o, V1 o1, V2 o2, VG og)
 {
     const long long PL = g.plane;
     if (K == 0) {
@@ -802,7 +913,7 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
                 l1 = ld_lo<R>(fA, 0, PL, o);
                 l2 = ld_lo<R>(fA, 1, PL, o);
             },
-            [&](auto kc, R o1, R o2, R og) {
+            [&](auto kc, auto o1, auto o2, auto og) {
                 constexpr int K = decltype(kc)::value;
                 push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
             },
@@ -861,7 +972,7 @@ __device__ __forceinline__ void wall_node(const S* __restrict__ fA, S* __restric
                 l1 = R(0);
                 l2 = R(0);
             },
-            [&](auto kc, R o1, R o2, R og) {
+            [&](auto kc, auto o1, auto o2, auto og) {
                 constexpr int K = decltype(kc)::value;
                 push_wall<K>(g, cls, fB, x, y, o, o1, o2, og);
                 // slots fed from beyond the lid receive nothing: keep them zero
