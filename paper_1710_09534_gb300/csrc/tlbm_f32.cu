@@ -2,5 +2,5 @@
 #include "tlbm_ops_impl.cuh"
 
 namespace tlb {
-const Ops& ops_f32() { return OpsImpl<float, float, kBlock32, kRows32, kPrefetch32, kMinB32, false>::table(); }
+const Ops& ops_f32() { return OpsImpl<float, float, kBlock32, kRows32, kPrefetch32, kMinBF32, false>::table(); }
 }  // namespace tlb

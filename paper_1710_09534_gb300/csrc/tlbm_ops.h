@@ -116,7 +116,13 @@ inline const Ops& ops_for(int precision, bool mrt)
 #define TLB_MINB32_MRT 4
 #endif
 constexpr int kBlock64 = TLB_BLOCK64, kRows64 = TLB_ROWS64, kMinB64 = TLB_MINB64;
+// FP32 storage with the one-row-ahead population loads holds about 20 more
+// registers per thread: 4 blocks per SM
+#ifndef TLB_MINB_F32
+#define TLB_MINB_F32 4
+#endif
 constexpr int kBlock32 = TLB_BLOCK32, kRows32 = TLB_ROWS32, kMinB32 = TLB_MINB32, kMinB32Mrt = TLB_MINB32_MRT;
+constexpr int kMinBF32 = TLB_MINB_F32;
 constexpr bool kPrefetch32 = TLB_PREFETCH32 != 0;
 
 
