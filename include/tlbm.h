@@ -70,7 +70,7 @@ enum { TLB_FP64 = 0, TLB_FP32 = 1, TLB_FP16 = 2, TLB_BF16 = 3 };
  * Because the chemical potentials need the order parameters of neighbours
  * (Eqs. 8, 20), a first pass per step writes c_1, c_2 of every node to two
  * planes of the arithmetic type, which the update then reads.  Workspace:
- * 0.57 (FP64, FP32) and 0.61 (FP16, BF16) of the two-buffer size at
+ * 0.57 (FP64, FP32) and 0.62 (FP16, BF16) of the two-buffer size at
  * 2048x2048; each step also moves the order-parameter pass.  The results equal
  * the two-buffer update's up to rounding order.  Every call sees the usual
  * layout (a call that ends on an even step streams its result in place), so

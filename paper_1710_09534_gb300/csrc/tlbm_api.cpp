@@ -641,7 +641,7 @@ int tlb_read_fields(tlb_lattice* L, uint32_t mask, double* host_out)
     if (!L->have_params || !L->have_fields) return fail(TLB_ESTATE, "no state yet");
     if (!host_out || (mask & ~(uint32_t)TLB_F_ALL) || !mask) return fail(TLB_EINVAL, "bad output or field mask");
     // stage in the spare distribution buffer, as many FP64 planes per pass as
-    // it holds (8 or more: it has >= 70 bytes per node in every precision);
+    // it holds (8 or more: it has >= 66 bytes per node in every precision);
     // in-place lattices stage in the order-parameter planes (1 or 2 per pass)
     const size_t N = (size_t)L->n();
     const size_t spare = L->lay.inplace ? (size_t)L->lay.cpl_bytes
@@ -775,10 +775,12 @@ int tlb_read_state(tlb_lattice* L, double* host_out)
         const size_t r = q == 9 ? 1 : 0;
         if (es == 8) return f64((q * PL + i) * 8);
         if (es == 4) return rest ? f32((q * PL + i) * 4) + f32(((27 + r) * PL + i) * 4) : f32((q * PL + i) * 4);
-        const size_t fr = 27 * PL * 2;  // FP32 region after the 16-bit planes
+        const size_t fr = 25 * PL * 2;  // FP32 region after the 16-bit planes
         if (rest) return f32(fr + (r * PL + i) * 4) + f32(fr + ((2 + r) * PL + i) * 4);
+        // f^1_k, f^2_k share 32-bit word k-1 of a node (low, high half); g_k follow
+        const size_t e = q < 9 ? (q - 1) * 2 * PL + 2 * i : (q < 18 ? (q - 10) * 2 * PL + 2 * i + 1 : (16 + (q - 18)) * PL + i);
         uint16_t b;
-        memcpy(&b, raw.data() + (q * PL + i) * 2, 2);
+        memcpy(&b, raw.data() + e * 2, 2);
         return L->precision == TLB_FP16 ? half_bits(b) * inv16 : bf16_bits(b);
     };
     auto cuv = [&](size_t q, size_t i) { return ces == 8 ? f64(dbytes + (q * PL + i) * 8) : f32(dbytes + (q * PL + i) * 4); };

@@ -150,8 +150,12 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
             constexpr int K = decltype(kc)::value;
             const long long s = (ODD && K != 0) ? po.template dest<opp(K)>() : ou;
             constexpr int q = ODD ? opp(K) : K;
-            f1k = ld_pop<R, false>(f, q, PL, s);
-            f2k = ld_pop<R, false>(f, 9 + q, PL, s);
+            if constexpr (q == 0) {
+                f1k = ld_pop<R, false>(f, 0, PL, s);
+                f2k = ld_pop<R, false>(f, 9, PL, s);
+            } else {
+                ld_pair<R, false>(f, q, PL, s, f1k, f2k);
+            }
         };
         auto load_all_f = [&]() {
             static_for<0, 9>([&](auto kc) { load_f(kc, f1[decltype(kc)::value], f2[decltype(kc)::value]); });
@@ -250,9 +254,7 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
                 constexpr int K = decltype(kc)::value;
                 const long long d = (ODD && K != 0) ? po.template dest<K>() : ou;
                 constexpr int q = ODD ? K : opp(K);
-                st_pop(f, q, PL, d, o1);
-                st_pop(f, 9 + q, PL, d, o2);
-                st_pop(f, 18 + q, PL, d, og);
+                st_three(f, q, PL, d, o1, o2, og);
             },
             [&](R l1, R l2) {
                 st_lo(f, 0, PL, ou, l1);
@@ -296,9 +298,7 @@ __device__ __forceinline__ void store_ip(const Geo& g, const uint8_t* __restrict
             }
         }
     }
-    st_pop(f, q, PL, d, o1);
-    st_pop(f, 9 + q, PL, d, o2);
-    st_pop(f, 18 + q, PL, d, og);
+    st_three(f, q, PL, d, o1, o2, og);
 }
 
 template <typename S, typename R, bool MRT, bool ODD>
@@ -431,10 +431,14 @@ __global__ void k_swap(S* f, const uint8_t* __restrict__ cls, Geo g)
 {
     using E = typename std::conditional<Store<S>::k16, unsigned short, S>::type;  // raw element
     E* e = reinterpret_cast<E*>(f);
+    // element index of moving population q of node n (16-bit: the paired layout)
+    auto at = [&](int q, long long n) -> long long {
+        if constexpr (Store<S>::k16) return idx16(q, g.plane, n);
+        else return q * g.plane + n;
+    };
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= g.nx) return;
-    const long long PL = g.plane;
     const long long o = (long long)y * g.pitch + x;
     if (!fluidlike(cls[o] & CLS_KIND_MASK)) return;
     static_for<1, 9>([&](auto kc) {
@@ -446,14 +450,14 @@ __global__ void k_swap(S* f, const uint8_t* __restrict__ cls, Geo g)
             if constexpr (K == 1 || K == 2 || K == 5 || K == 6) {
 #pragma unroll
                 for (int b = 0; b < 27; b += 9) {
-                    const E a = e[(b + KB) * PL + o];
-                    e[(b + KB) * PL + o] = e[(b + K) * PL + d];
-                    e[(b + K) * PL + d] = a;
+                    const E a = e[at(b + KB, o)];
+                    e[at(b + KB, o)] = e[at(b + K, d)];
+                    e[at(b + K, d)] = a;
                 }
             }
         } else if (s == ST_VOID) {
 #pragma unroll
-            for (int b = 0; b < 27; b += 9) e[(b + KB) * PL + o] = E(0);
+            for (int b = 0; b < 27; b += 9) e[at(b + KB, o)] = E(0);
         }
     });
 }

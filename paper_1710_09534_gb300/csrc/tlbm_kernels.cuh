@@ -64,14 +64,17 @@ __device__ __forceinline__ R sum9s(const R* v)
 //           proportional to mu_i and u; Eq. 2b: g^eq is pressure-based), and
 //           (FP16) scaled by 2^kF16ScaleExp so that small populations stay normal
 //           numbers; the rest populations, whose equilibrium at rest is c_i
-//           itself, stay FP32 pairs.  Layout: 27 16-bit planes (0 and 9
-//           unused) then 4 FP32 planes: f^1_0 hi, f^2_0 hi, f^1_0 lo, f^2_0 lo.
+//           itself, stay FP32 pairs.  Layout: 8 planes of 32-bit words, word
+//           k-1 of a node holding f^1_k (low half) and f^2_k (high half) for
+//           k = 1..8 (both stream to the same node, so one 32-bit access moves
+//           both); 9 16-bit planes g_0..g_8; then 4 FP32 planes: f^1_0 hi,
+//           f^2_0 hi, f^1_0 lo, f^2_0 lo.
 // The c_i u planes of Eq. 19 are FP64 with FP64 storage and FP32 otherwise.
 template <typename S>
 struct Store {
     static constexpr bool k16 = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
     static constexpr bool kLo = !std::is_same<S, double>::value;
-    static constexpr int kPlanes = std::is_same<S, double>::value ? 27 : (k16 ? 35 : 29);  // in units of S
+    static constexpr int kPlanes = std::is_same<S, double>::value ? 27 : (k16 ? 33 : 29);  // in units of S
     static constexpr int kScaleExp = std::is_same<S, __half>::value ? kF16ScaleExp : 0;
     using Cu = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
     using R = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
@@ -87,16 +90,24 @@ __device__ __forceinline__ unsigned short enc16(__nv_bfloat16, float v)
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
-// FP32 region of a 16-bit buffer (after the 27 16-bit planes)
+// FP32 region of a 16-bit buffer (after the 16 + 9 16-bit planes)
 template <typename S>
 __device__ __forceinline__ const float* rest_region(const S* f, long long PL)
 {
-    return reinterpret_cast<const float*>(f + 27 * PL);
+    return reinterpret_cast<const float*>(f + 25 * PL);
 }
 template <typename S>
 __device__ __forceinline__ float* rest_region(S* f, long long PL)
 {
-    return reinterpret_cast<float*>(f + 27 * PL);
+    return reinterpret_cast<float*>(f + 25 * PL);
+}
+// 16-bit element index of moving population q (1..8, 10..26) of node o in a
+// 16-bit buffer: f^1_k, f^2_k share 32-bit word k-1 of the node, g_k follow
+__device__ __forceinline__ long long idx16(int q, long long PL, long long o)
+{
+    if (q < 9) return (long long)(q - 1) * 2 * PL + 2 * o;
+    if (q < 18) return (long long)(q - 10) * 2 * PL + 2 * o + 1;
+    return 16 * PL + (long long)(q - 18) * PL + o;
 }
 
 // Load through the read-only path (NC: the buffer is not written during the
@@ -117,7 +128,7 @@ __device__ __forceinline__ R ld_pop(const S* __restrict__ f, int q, long long PL
 {
     if constexpr (Store<S>::k16) {
         if (q == 0 || q == 9) return R(ld_any<NC>(rest_region(f, PL) + (q == 9 ? PL : 0) + o));
-        const float v = dec16(S{}, ld_any<NC>(reinterpret_cast<const unsigned short*>(f) + q * PL + o));
+        const float v = dec16(S{}, ld_any<NC>(reinterpret_cast<const unsigned short*>(f) + idx16(q, PL, o)));
         if constexpr (RAW) return R(v);
         constexpr float inv = 1.0f / float(1 << Store<S>::kScaleExp);
         return R(v * inv);
@@ -155,13 +166,13 @@ __device__ __forceinline__ void st_pop(S* __restrict__ f, int q, long long PL, l
 {
     if constexpr (std::is_same<R, Bits16>::value) {
         static_assert(Store<S>::k16, "encoded values belong to a 16-bit format");
-        reinterpret_cast<unsigned short*>(f)[q * PL + o] = v.b;
+        reinterpret_cast<unsigned short*>(f)[idx16(q, PL, o)] = v.b;
     } else if constexpr (Store<S>::k16) {
         if (q == 0 || q == 9) {
             rest_region(f, PL)[(q == 9 ? PL : 0) + o] = float(v);
         } else {
             constexpr float sc = float(1 << Store<S>::kScaleExp);
-            reinterpret_cast<unsigned short*>(f)[q * PL + o] = enc16(S{}, float(v) * sc);
+            reinterpret_cast<unsigned short*>(f)[idx16(q, PL, o)] = enc16(S{}, float(v) * sc);
         }
     } else {
         f[q * PL + o] = S(v);
@@ -173,6 +184,39 @@ __device__ __forceinline__ void st_lo(S* __restrict__ f, int i, long long PL, lo
     if constexpr (Store<S>::k16) rest_region(f, PL)[(2 + i) * PL + o] = float(v);
     else if constexpr (Store<S>::kLo) f[(27 + i) * PL + o] = S(v);
 }
+// f^1_k and f^2_k (k = 1..8) of node o; with 16-bit storage one 32-bit load
+// (RAW as for ld_pop).
+template <typename R, bool NC = true, bool RAW = false, typename S>
+__device__ __forceinline__ void ld_pair(const S* __restrict__ f, int k, long long PL, long long o, R& f1k, R& f2k)
+{
+    if constexpr (Store<S>::k16) {
+        const unsigned w = ld_any<NC>(reinterpret_cast<const unsigned*>(f) + (long long)(k - 1) * PL + o);
+        constexpr float inv = RAW ? 1.0f : 1.0f / float(1 << Store<S>::kScaleExp);
+        f1k = R(dec16(S{}, (unsigned short)(w & 0xffffu)) * inv);
+        f2k = R(dec16(S{}, (unsigned short)(w >> 16)) * inv);
+    } else {
+        f1k = ld_pop<R, NC>(f, k, PL, o);
+        f2k = ld_pop<R, NC>(f, 9 + k, PL, o);
+    }
+}
+// The populations k of f^1, f^2 and g pushed to node d: values of the
+// arithmetic type or, for 16-bit storage, Bits16 already encoded (the f^1_k,
+// f^2_k pair of a 16-bit buffer goes out as one 32-bit store).
+template <typename S, typename V1, typename V2, typename VG>
+__device__ __forceinline__ void st_three(S* __restrict__ f, int k, long long PL, long long d, V1 o1, V2 o2, VG og)
+{
+    if constexpr (Store<S>::k16 && std::is_same<V1, Bits16>::value && std::is_same<V2, Bits16>::value) {
+        if (k != 0) {
+            reinterpret_cast<unsigned*>(f)[(long long)(k - 1) * PL + d] = (unsigned)o1.b | ((unsigned)o2.b << 16);
+            st_pop(f, 18 + k, PL, d, og);
+            return;
+        }
+    }
+    st_pop(f, k, PL, d, o1);
+    st_pop(f, 9 + k, PL, d, o2);
+    st_pop(f, 18 + k, PL, d, og);
+}
+
 // c_i = sum_k f^i_k of node o for i = 1, 2 (rest population hi + lo)
 template <typename R, typename S>
 __device__ __forceinline__ void order_params(const S* __restrict__ f, long long PL, long long o, R& c1, R& c2)
@@ -502,8 +546,10 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         }
         if (in) {
             const long long oc = (long long)yw * g.pitch + xw;
+            v[0] = ld_pop<R>(fA, 0, PL, oc);
+            v[9] = ld_pop<R>(fA, 9, PL, oc);
 #pragma unroll
-            for (int k = 0; k < 18; k++) v[k] = ld_pop<R, true, SE != 0>(fA, k, PL, oc);
+            for (int k = 1; k < 9; k++) ld_pair<R, true, SE != 0>(fA, k, PL, oc, v[k], v[9 + k]);
             l[0] = ld_lo<R>(fA, 0, PL, oc);
             l[1] = ld_lo<R>(fA, 1, PL, oc);
         } else {
@@ -561,8 +607,10 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                         l1 = cl[0];
                         l2 = cl[1];
                     } else {
+                        v[0] = ld_pop<R>(fA, 0, PL, oc);
+                        v[9] = ld_pop<R>(fA, 9, PL, oc);
 #pragma unroll
-                        for (int k = 0; k < 18; k++) v[k] = ld_pop<R, true, SE != 0>(fA, k, PL, oc);
+                        for (int k = 1; k < 9; k++) ld_pair<R, true, SE != 0>(fA, k, PL, oc, v[k], v[9 + k]);
                         l1 = ld_lo<R>(fA, 0, PL, oc);
                         l2 = ld_lo<R>(fA, 1, PL, oc);
                     }
@@ -663,8 +711,12 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                     f1k = stash->v[su][K][t];
                     f2k = stash->v[su][9 + K][t];
                 } else {
-                    f1k = ld_pop<R, true, SE != 0>(fA, K, PL, ou);
-                    f2k = ld_pop<R, true, SE != 0>(fA, 9 + K, PL, ou);
+                    if constexpr (K == 0) {
+                        f1k = ld_pop<R>(fA, 0, PL, ou);
+                        f2k = ld_pop<R>(fA, 9, PL, ou);
+                    } else {
+                        ld_pair<R, true, SE != 0>(fA, K, PL, ou, f1k, f2k);
+                    }
                 }
             },
             [&](R& l1, R& l2) {
@@ -679,9 +731,7 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
             [&](auto kc, auto o1, auto o2, auto og) {
                 constexpr int K = decltype(kc)::value;
                 const long long d = (K == 0) ? ou : po.template dest<K>();
-                st_pop(fB, K, PL, d, o1);
-                st_pop(fB, 9 + K, PL, d, o2);
-                st_pop(fB, 18 + K, PL, d, og);
+                st_three(fB, K, PL, d, o1, o2, og);
             },
             [&](R l1, R l2) {
                 st_lo(fB, 0, PL, ou, l1);
@@ -863,14 +913,9 @@ __device__ __forceinline__ void push_wall(const Geo& g, const uint8_t* __restric
     long long d = 0;
     const int s = site_of(g, cls, x + ex(K), y + ey(K), d);
     if (fluidlike(s)) {
-        st_pop(fB, K, PL, d, o1);
-        st_pop(fB, 9 + K, PL, d, o2);
-        st_pop(fB, 18 + K, PL, d, og);
+        st_three(fB, K, PL, d, o1, o2, og);
     } else if (s == ST_WET || s == ST_NEUTRAL) {
-        constexpr int KB = opp(K);
-        st_pop(fB, KB, PL, o, o1);
-        st_pop(fB, 9 + KB, PL, o, o2);
-        st_pop(fB, 18 + KB, PL, o, og);
+        st_three(fB, opp(K), PL, o, o1, o2, og);
     }
 }
 

@@ -64,7 +64,7 @@ struct Ops {
 // bytes per distribution scalar, planes of that size per buffer, bytes per
 // c_i u scalar.
 inline size_t elem_for(int precision) { return precision == 0 ? 8 : (precision == 1 ? 4 : 2); }
-inline int ndist_for(int precision) { return precision == 0 ? 27 : (precision == 1 ? 29 : 35); }
+inline int ndist_for(int precision) { return precision == 0 ? 27 : (precision == 1 ? 29 : 33); }
 inline size_t cu_elem_for(int precision) { return precision == 0 ? 8 : 4; }
 
 const Ops& ops_f64();

@@ -51,10 +51,10 @@ def test_workspace_size_validation(lib):
 
 def test_inplace_workspace_is_smaller(lib):
     """One distribution buffer plus two order-parameter planes instead of two
-    buffers: 0.57 (FP64, FP32) and 0.61 (16-bit) of the two-buffer workspace
+    buffers: 0.57 (FP64, FP32) and 0.62 (16-bit) of the two-buffer workspace
     at 2048x2048; an unknown precision with the flag is still rejected."""
     import paper_1710_09534_gb300 as T
-    for p, ratio in ((T.FP64, 0.58), (T.FP32, 0.58), (T.FP16, 0.62), (T.BF16, 0.62)):
+    for p, ratio in ((T.FP64, 0.58), (T.FP32, 0.58), (T.FP16, 0.63), (T.BF16, 0.63)):
         two = lib.tlb_workspace_bytes(2048, 2048, p)
         one = lib.tlb_workspace_bytes(2048, 2048, p | T.INPLACE)
         assert 0 < one < ratio * two, (p, one, two)
