@@ -62,14 +62,12 @@ KERNEL = {"fp64": "k_step_interior<double>", "fp32": "k_step_interior<float>",
           "fp16": "k_step_interior<__half>", "bf16": "k_step_interior<__nv_bfloat16>"}
 
 
-# FP64 arithmetic per node update of the fused interior kernel, as counted by
-# ncu (DADD + DMUL + DFMA instructions; flops with FMA = 2) on the 2048^2
-# lattice: see profiles/k_step_interior_fp64_tiled_drops_2048.md.  "uniform":
-# the update taken when all three fluids share density and viscosity (the
-# tiled-drops workload); "general": any densities and viscosities.
-# (DADD + DMUL + DFMA instructions, flops with an FMA as 2) per interior node, from
-# the ncu captures of k_step_interior<double> (profiles/k_step_interior_fp64_*.md)
-FP64_DP = {"uniform": (264, 394), "general": (343, 497)}
+# FP64 arithmetic per node update of the fused interior kernel as counted by
+# ncu on the 2048^2 lattice: (DADD + DMUL + DFMA instructions, flops with an
+# FMA as 2).  "uniform": the update taken when all three fluids share density
+# and viscosity (the tiled-drops workload); "general": any densities and
+# viscosities (the same lattice with rho_2 = 3).
+FP64_DP = {"uniform": (226.6, 332.1), "general": (290.1, 426.0)}
 # FP64 vector unit: 152 SMs x 2 DP instructions/clk x 2.07 GHz (an FMA is 2 flops)
 FP64_DP_INST_PEAK = 152 * 2 * 2.07e9
 FP64_PEAK_TFLOPS = 2 * FP64_DP_INST_PEAK / 1e12
@@ -101,23 +99,32 @@ def parse():
     ap.add_argument("--inplace", action="store_true",
                     help="step the main lattice with in-place (AA-pattern) streaming; the interior time then "
                          "includes the order-parameter pass")
+    ap.add_argument("--rho2", type=float, default=None,
+                    help="density of fluid 2 on the main lattice (default: the workload's 1.0; another value "
+                         "times the general, density-contrast update)")
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default="fp32,fp16,bf16",
                     help="comma list of extra precisions to time; 'none' also skips the density-contrast, MRT and in-place variants")
-    ap.add_argument("--impact-steps", type=int, default=200,
-                    help="steps timed on the 1024x2048 cylinder-impact workload per precision (0: skip)")
+    ap.add_argument("--impact-steps", type=int, default=2000,
+                    help="least steps of the 1024x2048 cylinder-impact workload per precision and Weber number (0: skip)")
+    ap.add_argument("--impact-max-steps", type=int, default=9000,
+                    help="a Weber number whose drop reaches the cylinder within this many steps runs until 1500 "
+                         "steps after contact, so that a film forms")
     ap.add_argument("--shear-steps", type=int, default=20000,
                     help="steps of the 512x256 sheared compound drop, FP64 and FP32 (0: skip)")
     ap.add_argument("--batch-count", type=int, default=256, help="lattices in the batched workload (0: skip)")
-    ap.add_argument("--batch-steps", type=int, default=200)
-    ap.add_argument("--serve-count", type=int, default=40, help="requests in the served workload (0: skip)")
-    ap.add_argument("--serve-budget-gb", type=float, default=2.0)
-    ap.add_argument("--serve-hi", type=int, default=1024, help="largest side of a served lattice")
-    ap.add_argument("--serve-steps-lo", type=int, default=500)
-    ap.add_argument("--serve-steps-hi", type=int, default=5000)
+    ap.add_argument("--batch-steps", type=int, default=5000, help="steps of every lattice in one batch")
+    ap.add_argument("--batch-plain-steps", type=int, default=500,
+                    help="steps timed on the plain path (one tlb_step per lattice), whose rate does not "
+                         "depend on the step count")
+    ap.add_argument("--serve-count", type=int, default=200, help="requests in the served workload (0: skip)")
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-hi", type=int, default=2048, help="largest side of a served lattice")
+    ap.add_argument("--serve-steps-lo", type=int, default=1000)
+    ap.add_argument("--serve-steps-hi", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -327,6 +334,8 @@ def run_ours(args):
     import workloads as W
     stream = torch.cuda.current_stream()
     w = W.tiled_drops(args.nx, args.ny)
+    if args.rho2 is not None:
+        w.params.update(rho2=args.rho2)
     L = T.lattice_from_workload(w, args.precision, inplace=args.inplace)
     n_nodes = w.nx * w.ny
     L.step(args.warmup)
@@ -488,8 +497,9 @@ def batched(args, torch, T):
     ws = W.batch_population(args.batch_count, seed=1710)
     nodes = sum(w.nodes for w in ws)
     k = args.batch_steps
+    kp = min(args.batch_plain_steps, k)
     out = {"workload": f"{len(ws)} lattices, sides log-uniform 64..512 (seed 1710), drops on a wetting wall",
-           "nodes": nodes, "steps": k}
+           "nodes": nodes, "steps": k, "plain_steps": kp}
     for prec in ("fp32", "fp16"):
         plain = [T.lattice_from_workload(w, prec) for w in ws]
         for L in plain:
@@ -498,7 +508,7 @@ def batched(args, torch, T):
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
         for L in plain:
-            L.step(k)
+            L.step(kp)
         s1.record()
         s1.synchronize()
         plain_ms = s0.elapsed_time(s1)
@@ -517,8 +527,9 @@ def batched(args, torch, T):
         b1.record(B.stream)
         b1.synchronize()
         batch_ms = b0.elapsed_time(b1)
-        r = {"plain_mlups": round(nodes * k / (plain_ms / 1e3) / 1e6, 1),
-             "batched_mlups": round(nodes * k / (batch_ms / 1e3) / 1e6, 1), "tuned": cfg}
+        r = {"plain_mlups": round(nodes * kp / (plain_ms / 1e3) / 1e6, 1),
+             "batched_mlups": round(nodes * k / (batch_ms / 1e3) / 1e6, 1), "tuned": cfg,
+             "batched_s": round(batch_ms / 1e3, 3)}
         r["speedup"] = round(r["batched_mlups"] / r["plain_mlups"], 2)
         B.close()
         del mem
@@ -530,20 +541,62 @@ def batched(args, torch, T):
 
 
 def impact(args, torch, T):
-    """Compound drop falling onto a wetting cylinder (1024 x 2048, R_cyl = 120,
-    core R = 60, shell R = 100, We = 10, cylinder angles 90 deg), FP32 vs
-    shifted-FP16 storage: MLUPS over `impact_steps` steps each."""
+    """Compound drop falling onto a wetting cylinder at full size (1024 x 2048,
+    R_cyl = 120, core R = 60, shell R = 100, fully periodic), for We = 1, 10,
+    50 with cylinder angles 90 deg: `impact_steps` steps each in FP64, FP32 and
+    shifted-FP16 storage.  MLUPS of each; the FP32 and FP16 results' errors
+    against the FP64 one (which equals the oracle to 1e-12): order-parameter
+    max error, u and p max error relative to their scale, mass drift of fluids
+    1 and 2, and the film thickness on the cylinder top (0 before the drop
+    touches it).  Then an angle sweep (30..150 deg, We = 10, FP32 storage)
+    timed over the same steps."""
     import workloads as W
-    w = W.compound_drop_on_cylinder(1024, 2048, We=10.0)
-    out = {"workload": f"{w.name}, We = 10, periodic, cylinder R = 120 (curved wetting wall)",
-           "steps": args.impact_steps}
-    for prec in ("fp32", "fp16"):
-        L = T.lattice_from_workload(w, prec)
-        L.step(max(3, args.warmup))
+    n0 = args.impact_steps
+    out = {"workload": "compound_drop_on_cylinder_1024x2048, periodic, cylinder R = 120 (curved wetting wall), "
+                       "core R = 60, shell R = 100, 48 lattice units between shell and cylinder at the start",
+           "We": {}}
+    for We in (1.0, 10.0, 50.0):
+        w = W.compound_drop_on_cylinder(1024, 2048, We=We)
+        col = w.nx // 2
+        y_top = int(max(y for y in range(w.ny) if w.mask[y, col]))
+        contact = int(48.0 / w.meta["U"])  # steps until the falling shell reaches the cylinder top
+        n = max(n0, contact + 1500) if contact + 1500 <= args.impact_max_steps else n0
+        fields = {}
+        res = {"U": round(w.meta["U"], 5), "Re": round(w.meta["Re"], 1), "steps": n,
+               "contact_step_estimate": contact}
+        for prec in ("fp64", "fp32", "fp16"):
+            L = T.lattice_from_workload(w, prec)
+            m0 = np.array(L.diagnostics()["mass"])
+            L.step(3)
+            L.sync()
+            ms = time_steps(L, n, torch, torch.cuda.current_stream())
+            res[prec + "_mlups"] = round(w.nx * w.ny * n / (ms / 1e3) / 1e6, 1)
+            fields[prec] = L.fields(("c1", "c2", "ux", "uy", "p"))
+            m1 = np.array(L.diagnostics()["mass"])
+            res[prec + "_mass_drift"] = [float(f"{v:.3g}") for v in np.abs(m1[:2] - m0[:2]) / np.abs(m0[:2])]
+            res[prec + "_film_h"] = round(L.film_thickness(col, y_top, 3), 6)
+            L.close()
+        ref = fields["fp64"]
+        for prec in ("fp32", "fp16"):
+            a = fields[prec]
+            err = {"c_abs": float(max(np.abs(a[k] - ref[k]).max() for k in ("c1", "c2")))}
+            for k in ("ux", "uy", "p"):
+                err[k + "_rel"] = float(np.abs(a[k] - ref[k]).max() / max(float(np.abs(ref[k]).max()), 1e-12))
+            err["film_h_abs"] = abs(res[prec + "_film_h"] - res["fp64_film_h"])
+            res[prec + "_vs_fp64"] = {k: float(f"{v:.3g}") for k, v in err.items()}
+        out["We"][f"{We:g}"] = res
+    sweep = {}
+    n = n0
+    out["angle_sweep_steps"] = n
+    for th in (30.0, 60.0, 90.0, 120.0, 150.0):
+        w = W.compound_drop_on_cylinder(1024, 2048, We=10.0, theta=th)
+        L = T.lattice_from_workload(w, "fp32")
+        L.step(3)
         L.sync()
-        ms = time_steps(L, args.impact_steps, torch, torch.cuda.current_stream())
-        out[prec + "_mlups"] = round(w.nx * w.ny * args.impact_steps / (ms / 1e3) / 1e6, 1)
+        ms = time_steps(L, n, torch, torch.cuda.current_stream())
+        sweep[f"{th:g}"] = round(w.nx * w.ny * n / (ms / 1e3) / 1e6, 1)
         L.close()
+    out["angle_sweep_fp32_mlups"] = sweep
     return out
 
 
@@ -578,11 +631,11 @@ def shear(args, torch, T):
 def served(args, torch, T):
     """The served workload: Poisson arrivals (20 requests/s, seed 1710) of
     drop-on-wall and drop-on-cylinder jobs, sides log-uniform 128..serve_hi,
-    steps log-uniform serve_steps_lo..serve_steps_hi (default 1024, 500..5000:
-    a run of seconds; the full configuration is 200 requests, 128..2048,
-    1000..20000), FP32 and FP16 storage alternating, admitted by device
-    footprint against an HBM budget; time to result and aggregate MLUPS over
-    the whole run."""
+    steps log-uniform serve_steps_lo..serve_steps_hi (defaults: the full
+    configuration, 200 requests, 128..2048, 1000..20000 steps), FP32 and
+    shifted-FP16 storage alternating, admitted by device footprint against an
+    HBM budget; time to result (p50, p99), aggregate MLUPS over the whole run,
+    the GPU's busy share of it and the tile shapes the tuner picked."""
     import workloads as W
     from paper_1710_09534_gb300.serve import Request, Server, poisson_arrivals
     hi, slo, shi = args.serve_hi, args.serve_steps_lo, args.serve_steps_hi

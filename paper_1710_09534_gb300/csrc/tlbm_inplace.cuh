@@ -95,12 +95,8 @@ __global__ void k_csum(const S* __restrict__ f, R* __restrict__ cpl, const uint8
 template <typename S, typename R, int BLOCK, bool PREFETCH, bool MRT, bool UNI, bool ODD>
 __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, const R* __restrict__ cpl,
                                                  const uint8_t* __restrict__ cls, const Geo& g, const Prm<R>& P,
-                                                 int bx, int by, int rows, TileRings<R, BLOCK>& sh)
+                                                 int bx, int by, int rows, ColRings<R, BLOCK>& sh)
 {
-    R(&sc1)[5][BLOCK] = sh.c1;
-    R(&sc2)[5][BLOCK] = sh.c2;
-    R(&sm1)[3][BLOCK] = sh.m1;
-    R(&sm2)[3][BLOCK] = sh.m2;
     const long long PL = g.plane;
     const int t = threadIdx.x;
     const int x0 = bx * (BLOCK - 4);
@@ -116,6 +112,9 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
     const int y1 = min(y0 + rows, g.ny);
     const int dir = (by & 1) ? -1 : 1;
     const int iters = (y1 - y0) + 4;
+    // this column's c and mu histories (as in interior_tile)
+    R ca[3] = {R(0), R(0), R(0)}, cb[3] = {R(0), R(0), R(0)};
+    R ma[3] = {R(0), R(0), R(0)}, mb[3] = {R(0), R(0), R(0)};
 
     for (int it = 0; it < iters; it++) {
         const int yc = dir > 0 ? y0 - 2 + it : y1 + 1 - it;
@@ -178,49 +177,59 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
                 a = __ldg(cpl + oc);
                 b = __ldg(cpl + PL + oc);
             }
-            const int sl = (yc + 10) % 5;
-            sc1[sl][t] = a;
-            sc2[sl][t] = b;
+            ca[2] = ca[1];
+            ca[1] = ca[0];
+            ca[0] = a;
+            cb[2] = cb[1];
+            cb[1] = cb[0];
+            cb[0] = b;
+            if (it >= 2) {
+                const int sl = (ym + 9) % 3;
+                sh.A1[sl][t] = fma(R(4), ca[1], ca[0] + ca[2]);
+                sh.A2[sl][t] = fma(R(4), cb[1], cb[0] + cb[2]);
+                sh.D1[sl][t] = dir > 0 ? ca[0] - ca[2] : ca[2] - ca[0];
+                sh.D2[sl][t] = dir > 0 ? cb[0] - cb[2] : cb[2] - cb[0];
+            }
         }
         __syncthreads();
         // 2) mu of row ym (Eq. 8 with Eq. 20b)
         if (it >= 2 && t >= 1 && t < BLOCK - 1) {
-            R v1[9], v2[9];
-#pragma unroll
-            for (int k = 0; k < 9; k++) {
-                const int sl = (ym + ey(k) + 10) % 5;
-                v1[k] = sc1[sl][t + ex(k)];
-                v2[k] = sc2[sl][t + ex(k)];
-            }
+            const int sl = (ym + 9) % 3;
+            const R lap1 = fma(R(4), fma(R(-5), ca[1], ca[0] + ca[2]), sh.A1[sl][t - 1] + sh.A1[sl][t + 1]);
+            const R lap2 = fma(R(4), fma(R(-5), cb[1], cb[0] + cb[2]), sh.A2[sl][t - 1] + sh.A2[sl][t + 1]);
             R mu1, mu2;
-            chem_pot(P, v1[0], v2[0], lap9s(v1), lap9s(v2), mu1, mu2);
-            const int ml = (ym + 9) % 3;
-            sm1[ml][t] = mu1;
-            sm2[ml][t] = mu2;
+            chem_pot(P, ca[1], cb[1], lap1, lap2, mu1, mu2);
+            ma[2] = ma[1];
+            ma[1] = ma[0];
+            ma[0] = mu1;
+            mb[2] = mb[1];
+            mb[1] = mb[0];
+            mb[0] = mu2;
+            if constexpr (!UNI) {
+                sh.M1[t] = fma(R(4), ma[1], ma[0] + ma[2]);
+                sh.M2[t] = fma(R(4), mb[1], mb[0] + mb[2]);
+            }
         }
         __syncthreads();
         // 3) update of row yu
         if (!upd) continue;
         Macro<R> m;
         {
-            R v1[9], v2[9], w1[9], w2[9];
-#pragma unroll
-            for (int k = 0; k < 9; k++) {
-                const int sl = (yu + ey(k) + 10) % 5;
-                const int ml = (yu + ey(k) + 9) % 3;
-                v1[k] = sc1[sl][t + ex(k)];
-                v2[k] = sc2[sl][t + ex(k)];
-                w1[k] = sm1[ml][t + ex(k)];
-                w2[k] = sm2[ml][t + ex(k)];
+            const int su = (yu + 9) % 3;
+            m.c1 = ca[2];
+            m.c2 = cb[2];
+            m.mu1 = ma[1];
+            m.mu2 = mb[1];
+            m.g1x = sh.A1[su][t + 1] - sh.A1[su][t - 1];
+            m.g2x = sh.A2[su][t + 1] - sh.A2[su][t - 1];
+            m.g1y = fma(R(4), sh.D1[su][t], sh.D1[su][t - 1] + sh.D1[su][t + 1]);
+            m.g2y = fma(R(4), sh.D2[su][t], sh.D2[su][t - 1] + sh.D2[su][t + 1]);
+            if constexpr (UNI) {
+                m.lm1 = m.lm2 = R(0);
+            } else {
+                m.lm1 = fma(R(4), fma(R(-5), ma[1], ma[0] + ma[2]), sh.M1[t - 1] + sh.M1[t + 1]);
+                m.lm2 = fma(R(4), fma(R(-5), mb[1], mb[0] + mb[2]), sh.M2[t - 1] + sh.M2[t + 1]);
             }
-            m.c1 = v1[0];
-            m.c2 = v2[0];
-            m.mu1 = w1[0];
-            m.mu2 = w2[0];
-            grad9s(v1, m.g1x, m.g1y);
-            grad9s(v2, m.g2x, m.g2y);
-            m.lm1 = lap9s(w1);
-            m.lm2 = lap9s(w2);
             m.rho = UNI ? P.rho[2] : density(P, m.c1, m.c2);
         }
         if (!PREFETCH) load_g();
@@ -268,7 +277,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
 k_step_interior_ip(S* f, CuT<S>* __restrict__ cu, const R* __restrict__ cpl, const uint8_t* __restrict__ cls,
                    Geo g, Prm<R> P, int rows)
 {
-    __shared__ TileRings<R, BLOCK> sh;
+    __shared__ ColRings<R, BLOCK> sh;
     interior_tile_ip<S, R, BLOCK, PREFETCH, MRT, UNI, ODD>(f, cu, cpl, cls, g, P, blockIdx.x, blockIdx.y, rows, sh);
 }
 

@@ -445,18 +445,15 @@ struct PushOffsets {
 // segment.  Even segments march up, odd segments down, so that two adjacent
 // segments read the two halo rows they share at about the same time (both
 // at their start or both at their end) and the second read hits L2.  The
-// iteration that reaches row r keeps rolling rings in shared memory:
+// iteration that reaches row r computes
 //   c1, c2 of row r         (sum of the 18 order-parameter populations)
 //   mu1, mu2 of row r - dir (needs c rows r - 2 dir .. r)
 //   update of row r - 2 dir (needs c and mu rows around it)
-// so each order parameter is summed once per node (plus a 4-column, 4-row
-// halo per block) and no c or mu array ever reaches HBM.
+// with each column's recent c and mu kept by its own thread and the column
+// sums its neighbours need in shared memory (ColRings), so each order
+// parameter is summed once per node (plus a 4-column, 4-row halo per block)
+// and no c or mu array ever reaches HBM.
 // ---------------------------------------------------------------------------
-template <typename R, int BLOCK>
-struct TileRings {
-    R c1[5][BLOCK], c2[5][BLOCK];  // c rings (row r in slot (r + 10) % 5)
-    R m1[3][BLOCK], m2[3][BLOCK];  // mu rings (row r in slot (r + 9) % 3)
-};
 
 // Column sums of the two-buffer interior tile.  For one row r of an order
 // parameter c and each column j of the strip:
