@@ -8,9 +8,13 @@ the update, written from Sec. II of Liang et al., arXiv:1710.09534).  This
 module only compiles it with gcc, marshals arrays through ctypes and adds the
 contact-angle measurement of Sec. III.A in numpy.
 
-Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
-the figure values of Figs. 3, 5 and 14, which the paper text does not carry
-(parity unpinned for those; no function here reproduces them).
+The D3Q19 form of the same model (Sec. II.A states it for D dimensions) lives
+in ``tlb_oracle3d.c`` (``OracleLattice3D``), built into the same library.
+
+Parity status: every function is pinned by ``tests/test_oracle_*.py`` and
+``tests/test_oracle3d.py`` except the figure values of Figs. 3, 5 and 14,
+which the paper text does not carry (parity unpinned for those; no function
+here reproduces them).
 """
 from __future__ import annotations
 
@@ -23,6 +27,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tlb_oracle.c")
+_SRC3 = os.path.join(_HERE, "tlb_oracle3d.c")
+_HDR = os.path.join(_HERE, "tlb_oracle.h")
 _LIB = os.path.join(_HERE, "libtlb_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -44,10 +50,12 @@ class Params(ctypes.Structure):
 def build(force: bool = False) -> str:
     """Compile tlb_oracle.c into libtlb_oracle.so next to it (gcc -O2, OpenMP over nodes)."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f)
+                                                for f in (_SRC, _SRC3, _HDR))
+        if force or stale:
             tmp = _LIB + f".{os.getpid()}.tmp"
             subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC",
-                                   "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
+                                   "-shared", "-std=c11", "-o", tmp, _SRC, _SRC3, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -94,6 +102,39 @@ def lib() -> ctypes.CDLL:
         L.orc_mrt_relax.argtypes = [dp, dp, dp, dp, dp]
         L.orc_w.argtypes = [ctypes.c_int]
         L.orc_w.restype = ctypes.c_double
+        # D3Q19 form (tlb_oracle3d.c)
+        L.orc3_create.restype = ctypes.c_void_p
+        L.orc3_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.orc3_destroy.argtypes = [ctypes.c_void_p]
+        L.orc3_set_geometry.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ubyte)]
+        L.orc3_set_params.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params)]
+        L.orc3_set_fields.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp, dp]
+        L.orc3_set_fields.restype = ctypes.c_int
+        L.orc3_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+        L.orc3_step.restype = ctypes.c_int
+        L.orc3_read_fields.argtypes = [ctypes.c_void_p, dp]
+        L.orc3_read_fields.restype = ctypes.c_int
+        L.orc3_get_state.argtypes = [ctypes.c_void_p, dp]
+        L.orc3_set_state.argtypes = [ctypes.c_void_p, dp]
+        L.orc3_grad.argtypes = [dp, dp]
+        L.orc3_lap.argtypes = [dp]
+        L.orc3_lap.restype = ctypes.c_double
+        L.orc3_e.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.orc3_e.restype = ctypes.c_int
+        L.orc3_opp.argtypes = [ctypes.c_int]
+        L.orc3_opp.restype = ctypes.c_int
+        L.orc3_w.argtypes = [ctypes.c_int]
+        L.orc3_w.restype = ctypes.c_double
+        L.orc3_feq.argtypes = [ctypes.c_int] + [ctypes.c_double] * 6
+        L.orc3_feq.restype = ctypes.c_double
+        L.orc3_geq.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5
+        L.orc3_geq.restype = ctypes.c_double
+        L.orc3_sk.argtypes = [ctypes.c_int] + [ctypes.c_double] * 3
+        L.orc3_sk.restype = ctypes.c_double
+        L.orc3_src_f.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4
+        L.orc3_src_f.restype = ctypes.c_double
+        L.orc3_src_g.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp, dp]
+        L.orc3_src_g.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -183,6 +224,115 @@ class OracleLattice:
         f = self.fields()
         fl = self.mask == 0
         return np.array([f[k][fl].sum() for k in ("c1", "c2", "c3")])
+
+
+FIELDS3 = ("c1", "c2", "c3", "rho", "ux", "uy", "uz", "p", "mu1", "mu2", "mu3")
+
+
+class OracleLattice3D:
+    """One nx-by-ny-by-nz D3Q19 lattice advanced by the FP64 oracle (arrays are
+    [nz, ny, nx]; edges = (x-, x+, y-, y+, z-, z+), each periodic, wetting or
+    neutral)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, edges=(0, 0, 1, 2, 0, 0), mask=None, params=None):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.shape = (self.nz, self.ny, self.nx)
+        self.edges = tuple(int(e) for e in edges)
+        e = (ctypes.c_int * 6)(*self.edges)
+        self._h = lib().orc3_create(self.nx, self.ny, self.nz, e)
+        if not self._h:
+            raise ValueError("oracle: invalid lattice size")
+        m = np.zeros(self.shape, np.uint8) if mask is None else np.ascontiguousarray(mask, np.uint8)
+        assert m.shape == self.shape
+        self.mask = m.copy()
+        lib().orc3_set_geometry(self._h, self.mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        if params is not None:
+            self.set_params(params)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc3_destroy(h)
+            self._h = None
+
+    def set_params(self, params):
+        if not isinstance(params, Params):
+            params = make_params(**params)
+        self.params = params
+        lib().orc3_set_params(self._h, ctypes.byref(params))
+
+    def set_fields(self, c1, c2, ux, uy, uz, p=None):
+        arrs = [_f64(a).reshape(self.shape) for a in (c1, c2, ux, uy, uz)]
+        pp = _f64(p).reshape(self.shape) if p is not None else None
+        rc = lib().orc3_set_fields(self._h, *(_dp(a) for a in arrs), _dp(pp) if pp is not None else None)
+        if rc:
+            raise RuntimeError("oracle: set_params first")
+
+    def step(self, n: int = 1):
+        if lib().orc3_step(self._h, int(n)):
+            raise RuntimeError("oracle: set_params first")
+
+    def fields(self) -> dict:
+        out = np.zeros((11,) + self.shape)
+        lib().orc3_read_fields(self._h, _dp(out))
+        return {k: out[i] for i, k in enumerate(FIELDS3)}
+
+    def state(self) -> np.ndarray:
+        """Raw state [63, nz, ny, nx]: f1 k=0..18, f2 k=0..18, g k=0..18, then
+        c1 ux, c1 uy, c1 uz, c2 ux, c2 uy, c2 uz."""
+        out = np.zeros((63,) + self.shape)
+        lib().orc3_get_state(self._h, _dp(out))
+        return out
+
+    def set_state(self, s):
+        s = _f64(s).reshape((63,) + self.shape)
+        lib().orc3_set_state(self._h, _dp(s))
+
+    def mass(self) -> np.ndarray:
+        """sum over fluid nodes of c1, c2, c3."""
+        f = self.fields()
+        fl = self.mask == 0
+        return np.array([f[k][fl].sum() for k in ("c1", "c2", "c3")])
+
+
+def lattice3_vectors():
+    """D3Q19 velocities e_k (19 x 3), weights w_k and the opposite table of the 3D oracle."""
+    e = np.array([[lib().orc3_e(k, a) for a in range(3)] for k in range(19)])
+    w = np.array([lib().orc3_w(k) for k in range(19)])
+    opp = np.array([lib().orc3_opp(k) for k in range(19)])
+    return e, w, opp
+
+
+def feq3(k, c, mu, eta, u):
+    return lib().orc3_feq(k, c, mu, eta, *map(float, u))
+
+
+def geq3(k, p, rho, u):
+    return lib().orc3_geq(k, p, rho, *map(float, u))
+
+
+def sk3(k, u):
+    return lib().orc3_sk(k, *map(float, u))
+
+
+def src_f3(k, tau, dcu):
+    return lib().orc3_src_f(k, tau, *map(float, dcu))
+
+
+def src_g3(k, taug, u, gr, Ft, Fa):
+    a = [_f64(v) for v in (u, gr, Ft, Fa)]
+    return lib().orc3_src_g(k, taug, *(_dp(v) for v in a))
+
+
+def grad3(v):
+    v = _f64(v)
+    out = np.zeros(3)
+    lib().orc3_grad(_dp(v), _dp(out))
+    return out
+
+
+def lap3(v):
+    return lib().orc3_lap(_dp(_f64(v)))
 
 
 # ---- exported per-node formulas (the same C functions the step uses) --------

@@ -52,6 +52,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include "tlb_oracle.h"
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -67,21 +68,7 @@ static const double WK[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
 static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 #define CS2 (1.0 / 3.0) /* c_s^2 = c^2 / 3 with c = dx/dt = 1 */
 
-/* ---- parameters ---------------------------------------------------------- */
-typedef struct {
-    double sigma12, sigma13, sigma23;          /* surface tensions, Eq. 7 */
-    double theta12_deg, theta13_deg, theta23_deg; /* contact angles, Eq. 38 */
-    double rho1, rho2, rho3;                   /* densities, Eq. 14 */
-    double nu1, nu2, nu3;                      /* viscosities, Eq. 15 */
-    double M0;                                 /* M_i = M0 / lambda_i, Eq. 12 */
-    double D;                                  /* interface thickness, Eq. 8 */
-    double tau1, tau2;                         /* relaxation times, Eq. 1a */
-    double gx, gy;                             /* body force per unit mass (R7) */
-    double lid_u;                              /* U0 of the velocity lid, Eq. 53 */
-    double collision;                          /* 0 BGK (Eqs. 1a, 1b), 1 MRT (R8) */
-    double mrt_s_f;                            /* MRT rate of the non-flux moments of f^i */
-    double mrt_s_g;                            /* MRT rate of e, eps, q_x, q_y of g */
-} orc_params;
+/* ---- parameters: orc_params (tlb_oracle.h) ------------------------------- */
 
 enum { EDGE_PERIODIC = 0, EDGE_WETTING = 1, EDGE_NEUTRAL = 2, EDGE_LID = 3 };
 enum { SITE_FLUID = 0, SITE_LID = 1, SITE_WET = 2, SITE_NEUTRAL = 3, SITE_VOID = 4 };

@@ -428,3 +428,127 @@ def served_requests(count=200, seed=1710, lo=128, hi=2048, steps_lo=1000, steps_
         w = drops_on_wall(n, 0, rng) if rng.random() < 0.5 else drop_on_cylinder(n, rng)
         out.append((w, steps))
     return out
+
+
+# ---- three-dimensional (D3Q19) inputs ----------------------------------------
+
+@dataclass
+class Workload3:
+    """A D3Q19 problem: arrays are [nz, ny, nx]; edges = (x-, x+, y-, y+, z-,
+    z+), each PERIODIC, WETTING or NEUTRAL."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    edges: tuple
+    mask: np.ndarray
+    params: dict
+    c1: np.ndarray
+    c2: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    uz: np.ndarray
+    p: np.ndarray | None = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def grid3(nx, ny, nz):
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(np.float64)
+    return x, y, z
+
+
+def profile3(x, y, z, xc, yc, zc, R, D, periods=(None, None, None)):
+    """0.5 + 0.5 tanh(2 (R - r) / D) with r the Euclidean (minimum-image on
+    the periodic axes) distance to (xc, yc, zc)."""
+    d = []
+    for a, c, per in ((x, xc, periods[0]), (y, yc, periods[1]), (z, zc, periods[2])):
+        v = a - c
+        if per:
+            v = (v + per / 2) % per - per / 2
+        d.append(v)
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    return 0.5 + 0.5 * np.tanh(2.0 * (R - r) / D)
+
+
+def random_lattice3(nx, ny, nz, seed, edges=None, solids=("sphere",), u_amp=0.01, rho=(1.0, 3.0, 1.0)):
+    """Random drops of fluids 1 and 2, random solids (a sphere, a pillar, an
+    L-shaped concave corner), small random velocity, random admissible
+    tensions and angles: reaches every branch of the 3D wall rules."""
+    rng = np.random.default_rng(seed)
+    if edges is None:
+        edges = (PERIODIC, PERIODIC, WETTING, NEUTRAL, PERIODIC, PERIODIC)
+    x, y, z = grid3(nx, ny, nz)
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    for kind in solids:
+        kv = int(rng.integers(1, 3))
+        if kind == "sphere":
+            c = [rng.uniform(0.3 * n, 0.7 * n) for n in (nx, ny, nz)]
+            R = rng.uniform(2.5, max(3.0, min(nx, ny, nz) / 5))
+            mask[((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) <= R * R] = kv
+        elif kind == "pillar":
+            px, py = int(rng.integers(2, nx - 2)), int(rng.integers(2, ny - 2))
+            mask[:, py, px] = kv
+        elif kind == "corner":
+            px, py, pz = int(rng.integers(2, nx - 6)), int(rng.integers(2, ny - 6)), int(rng.integers(2, nz - 4))
+            mask[pz:pz + 3, py:py + 4, px:px + 2] = kv
+            mask[pz:pz + 3, py:py + 2, px:px + 4] = kv
+    per = tuple(n if edges[2 * a] == PERIODIC else None for a, n in enumerate((nx, ny, nz)))
+    c1 = np.zeros((nz, ny, nx))
+    c2 = np.zeros((nz, ny, nx))
+    for i in range(int(rng.integers(2, 5))):
+        c = [rng.uniform(0, n) for n in (nx, ny, nz)]
+        R = rng.uniform(2.5, max(3.0, min(nx, ny, nz) / 4))
+        prof = profile3(x, y, z, *c, R, 4.0, per)
+        if i % 2 == 0:
+            c1 = np.maximum(c1, prof)
+        else:
+            c2 = np.maximum(c2, prof)
+    s = c1 + c2
+    over = s > 1
+    c1[over] /= s[over]
+    c2[over] /= s[over]
+    c1[mask > 0] = 0
+    c2[mask > 0] = 0
+    u = [u_amp * rng.standard_normal((nz, ny, nx)) for _ in range(3)]
+    for a in u:
+        a[mask > 0] = 0
+    sigma = tuple(rng.uniform(0.8e-3, 1.5e-3, 3))
+    th13, th23 = rng.uniform(40, 140, 2)
+    try:
+        th12 = theta12_from(*sigma, th13, th23)
+    except ValueError:
+        th13, th23 = 90.0, 90.0
+        th12 = theta12_from(*sigma, th13, th23)
+    P = params(sigma=sigma, theta=(th12, th13, th23), rho=rho,
+               nu=tuple(rng.uniform(0.05, 0.15, 3)), mobility=float(rng.uniform(0.05, 0.15)),
+               D=float(rng.choice([3.0, 4.0, 5.0])), tau=tuple(rng.uniform(0.7, 1.0, 2)), g=(0.0, -1e-6))
+    return Workload3(f"random3_{nx}x{ny}x{nz}_s{seed}", nx, ny, nz, tuple(edges), mask, P, c1, c2, *u)
+
+
+def drops3d_on_wall(nx=128, ny=64, nz=128, R=16.0, theta=(60.0, 90.0, 120.0), sigma=1e-3, seed=1710):
+    """The 3D counterpart of the two-drop wetting case, tiled: hemispherical
+    drops of fluid 1 and fluid 2 (radius R) every 2.5 R along x and z on a
+    wetting bottom wall (y-), neutral top wall, periodic in x and z, in fluid
+    3; rho = 1, nu = 0.1, equal tensions, angles (theta_12, theta_13,
+    theta_23), mobility 0.1, D = 4."""
+    x, y, z = grid3(nx, ny, nz)
+    c1 = np.zeros((nz, ny, nx))
+    c2 = np.zeros((nz, ny, nx))
+    step = 2.5 * R
+    for iz, zc in enumerate(np.arange(step / 2, nz, step)):
+        for ix, xc in enumerate(np.arange(step / 2, nx, step)):
+            prof = profile3(x, y, z, xc, -0.5, zc, R, 4.0, (nx, None, nz))
+            if (ix + iz) % 2 == 0:
+                c1 = np.maximum(c1, prof)
+            else:
+                c2 = np.maximum(c2, prof)
+    P = params(sigma=(sigma, sigma, sigma), theta=theta, rho=(1.0, 1.0, 1.0), nu=(0.1, 0.1, 0.1),
+               mobility=0.1, D=4.0)
+    zero = np.zeros((nz, ny, nx))
+    return Workload3(f"drops3d_on_wall_{nx}x{ny}x{nz}", nx, ny, nz,
+                     (PERIODIC, PERIODIC, WETTING, NEUTRAL, PERIODIC, PERIODIC),
+                     np.zeros((nz, ny, nx), np.uint8), P, c1, c2, zero, zero.copy(), zero.copy())
