@@ -120,6 +120,9 @@ def parse():
     ap.add_argument("--batch-plain-steps", type=int, default=500,
                     help="steps timed on the plain path (one tlb_step per lattice), whose rate does not "
                          "depend on the step count")
+    ap.add_argument("--d3-steps", type=int, default=100,
+                    help="steps of the D3Q19 drops-on-wall lattice (0: skip)")
+    ap.add_argument("--d3-size", default="192,96,192", help="nx,ny,nz of the D3Q19 lattice")
     ap.add_argument("--serve-count", type=int, default=200, help="requests in the served workload (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--serve-hi", type=int, default=2048, help="largest side of a served lattice")
@@ -479,6 +482,8 @@ def run_ours(args):
             result["batched"] = batched(args, torch, T)
         if args.serve_count > 0:
             result["served"] = served(args, torch, T)
+        if args.d3_steps > 0:
+            result["d3q19"] = d3q19(args, torch, T)
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(result), flush=True)
@@ -650,6 +655,36 @@ def served(args, torch, T):
     out["workload"] = (f"{len(reqs)} requests, Poisson 20/s (seed 1710), sides 128..{hi}, steps {slo}..{shi}, "
                        f"FP32 and shifted-FP16 alternating, HBM budget {args.serve_budget_gb} GB")
     return out
+
+
+def d3q19(args, torch, T):
+    """The D3Q19 form (FP64): tiled hemispherical drops of fluids 1 and 2 on
+    a wetting wall, periodic in x and z; whole steps (three launches each)
+    timed with CUDA events on the lattice's stream, and the c_1, c_2 mass
+    drift over the timed steps."""
+    import workloads as W
+    nx, ny, nz = (int(v) for v in args.d3_size.split(","))
+    w = W.drops3d_on_wall(nx, ny, nz)
+    L = T.lattice3_from_workload(w)
+    stream = torch.cuda.current_stream()
+    L.step(max(args.warmup, 3))
+    L.sync()
+    m0 = np.array(L.diagnostics()["mass"])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    L.step(args.d3_steps)
+    ev[1].record(stream)
+    ev[1].synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    m1 = np.array(L.diagnostics()["mass"])
+    n = nx * ny * nz
+    L.close()
+    return {"workload": w.name, "nx": nx, "ny": ny, "nz": nz, "precision": "fp64", "steps": args.d3_steps,
+            "value": round(n * args.d3_steps / (ms / 1e3) / 1e6, 2), "unit": "MLUPS",
+            "ms_per_step": round(ms / args.d3_steps, 4),
+            "gpu_launches": 3 * args.d3_steps,
+            "mass_drift": [float(f"{v:.3g}") for v in np.abs(m1[:2] - m0[:2]) / np.abs(m0[:2])]}
 
 
 def e2e(L, w, args, torch, T):

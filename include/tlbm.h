@@ -324,6 +324,50 @@ int tlb_batch_tune(tlb_batch *batch, int trial_steps, void *dev_scratch, int64_t
                    int out_config[4], double *out_ms_per_step);
 void tlb_batch_destroy(tlb_batch *batch);
 
+/* ---- D3Q19: the same model on a three-dimensional lattice ---------------
+ * Sec. II.A states the model for D dimensions; these calls run it on the
+ * D3Q19 velocity set (e_0 = 0; e_1..6 = +x, -x, +y, -y, +z, -z; e_7..18 the 12
+ * face diagonals (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1),
+ * (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1); weights 1/3,
+ * 1/18, 1/36): Eqs. 1-20 with the Eq. 20 stencils over its 18 links, the
+ * Eq. 42 wetting ghost on every link into a wetting solid (Eq. 43 otherwise),
+ * half-way bounce-back (Eq. 44), FP64 storage and arithmetic, BGK collision.
+ * Body force G = rho (gx, gy, 0).  Node arrays are [nz][ny][nx], x fastest.
+ * edges[6] = {x-, x+, y-, y+, z-, z+}, each TLB_EDGE_PERIODIC, _WETTING or
+ * _NEUTRAL (no lid); a periodic edge needs a periodic opposite edge; at a
+ * site outside in several axes the first outside axis in x, y, z order
+ * whose edge is not periodic decides.  Mask values as for tlb_set_geometry.
+ * One step is three launches on the lattice's stream (order parameters into
+ * two planes, chemical potentials into two planes, then the fused update and
+ * push).  Ownership and errors as for the 2D calls; the library allocates no
+ * device memory (workspace from tlb3_workspace_bytes, 256-byte aligned).
+ *   tlb3_set_params: TLB_EINVAL as tlb_set_params, and for collision != 0 or
+ *     lid_u != 0.
+ *   tlb3_set_fields: host arrays of nx*ny*nz (p may be NULL); f = f^eq(c,
+ *     mu(c), u), g = g^eq(p, rho, u), c_i u stored; synchronizes.
+ *   tlb3_step: n steps, asynchronous.  tlb3_sync: waits for the stream.
+ *   tlb3_read_fields: field_mask bits 0..10 select c1, c2, c3, rho, ux, uy,
+ *     uz, p, mu1, mu2, mu3 (in that order) as FP64 planes of nx*ny*nz;
+ *     synchronizes.
+ *   tlb3_read_state: 63 FP64 planes: f^1_k, f^2_k, g_k (k = 0..18), then c1
+ *     ux, c1 uy, c1 uz, c2 ux, c2 uy, c2 uz of the previous step (Eq. 19); zero on solid nodes.
+ *   tlb3_diagnostics: FP64 mass totals of c1, c2, c3 over fluid nodes and
+ *     the non-finite count (TLB_EUNSTABLE if any). */
+typedef struct tlb3_lattice tlb3_lattice;
+int64_t tlb3_workspace_bytes(int nx, int ny, int nz);
+int tlb3_create(int nx, int ny, int nz, const int32_t edges[6], void *dev_workspace, int64_t ws_bytes,
+                void *cuda_stream, tlb3_lattice **out);
+int tlb3_set_geometry(tlb3_lattice *lat, const uint8_t *host_mask);
+int tlb3_set_params(tlb3_lattice *lat, const tlb_params *params);
+int tlb3_set_fields(tlb3_lattice *lat, const double *c1, const double *c2, const double *ux, const double *uy,
+                    const double *uz, const double *p);
+int tlb3_step(tlb3_lattice *lat, int64_t n);
+int tlb3_sync(tlb3_lattice *lat);
+int tlb3_read_fields(tlb3_lattice *lat, uint32_t field_mask, double *host_out);
+int tlb3_read_state(tlb3_lattice *lat, double *host_out);
+int tlb3_diagnostics(tlb3_lattice *lat, tlb_diag *out);
+void tlb3_destroy(tlb3_lattice *lat);
+
 /* Allocation-free variant of the tlb_diagnostics reduction.  The paper has
  * no counterpart: this exists for callers that cannot allocate device memory
  * where they need the totals (code living in a fixed arena it does not own,

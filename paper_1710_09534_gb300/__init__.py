@@ -103,6 +103,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tlb_batch_tune": (i32, [vp, i32, vp, i64, ctypes.POINTER(ctypes.c_int), dp]),
         "tlb_batch_destroy": (None, [vp]),
         "tlb_last_error": (ctypes.c_char_p, []),
+        "tlb3_workspace_bytes": (i64, [i32, i32, i32]),
+        "tlb3_create": (i32, [i32, i32, i32, ctypes.POINTER(ctypes.c_int32), vp, i64, vp, ctypes.POINTER(vp)]),
+        "tlb3_set_geometry": (i32, [vp, ctypes.POINTER(ctypes.c_uint8)]),
+        "tlb3_set_params": (i32, [vp, ctypes.POINTER(Params)]),
+        "tlb3_set_fields": (i32, [vp, dp, dp, dp, dp, dp, dp]),
+        "tlb3_step": (i32, [vp, i64]),
+        "tlb3_sync": (i32, [vp]),
+        "tlb3_read_fields": (i32, [vp, ctypes.c_uint32, dp]),
+        "tlb3_read_state": (i32, [vp, dp]),
+        "tlb3_diagnostics": (i32, [vp, ctypes.POINTER(Diag)]),
+        "tlb3_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -387,3 +398,95 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+FIELDS3 = ("c1", "c2", "c3", "rho", "ux", "uy", "uz", "p", "mu1", "mu2", "mu3")
+
+
+class Lattice3D:
+    """One D3Q19 lattice (FP64) on the current CUDA device, advanced on
+    ``stream`` (see the "D3Q19" section of include/tlbm.h).  Arrays are
+    [nz, ny, nx]; edges = (x-, x+, y-, y+, z-, z+)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, edges=(0, 0, 1, 2, 0, 0), stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("tlbm needs a CUDA device; there is no CPU fallback")
+        self.lib = load_library()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.shape = (self.nz, self.ny, self.nx)
+        self.edges = tuple(int(e) for e in edges)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            nbytes = _check(self.lib.tlb3_workspace_bytes(self.nx, self.ny, self.nz))
+            self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+            h = ctypes.c_void_p()
+            e = (ctypes.c_int32 * 6)(*self.edges)
+            _check(self.lib.tlb3_create(self.nx, self.ny, self.nz, e, ctypes.c_void_p(self.workspace.data_ptr()),
+                                        int(nbytes), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def n(self):
+        return self.nx * self.ny * self.nz
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.tlb3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, mask=None):
+        m = np.zeros(self.shape, np.uint8) if mask is None else np.ascontiguousarray(mask, np.uint8).reshape(self.shape)
+        _check(self.lib.tlb3_set_geometry(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+    def set_params(self, params):
+        p = params if isinstance(params, Params) else Params.from_dict(params)
+        _check(self.lib.tlb3_set_params(self._h, ctypes.byref(p)))
+
+    def set_fields(self, c1, c2, ux, uy, uz, p=None):
+        arrs = [_f64(a, self.n) for a in (c1, c2, ux, uy, uz)]
+        pp = _f64(p, self.n) if p is not None else None
+        _check(self.lib.tlb3_set_fields(self._h, *(_dp(a) for a in arrs), _dp(pp) if pp is not None else None))
+
+    def step(self, n: int = 1):
+        _check(self.lib.tlb3_step(self._h, int(n)))
+
+    def sync(self):
+        return _check(self.lib.tlb3_sync(self._h))
+
+    def fields(self, names=FIELDS3) -> dict:
+        mask = 0
+        for nm in names:
+            mask |= 1 << FIELDS3.index(nm)
+        order = [f for i, f in enumerate(FIELDS3) if mask & (1 << i)]
+        out = np.empty((len(order),) + self.shape)
+        _check(self.lib.tlb3_read_fields(self._h, mask, _dp(out)))
+        return {k: out[i] for i, k in enumerate(order)}
+
+    def state(self) -> np.ndarray:
+        out = np.empty((63,) + self.shape)
+        _check(self.lib.tlb3_read_state(self._h, _dp(out)))
+        return out
+
+    def diagnostics(self):
+        d = Diag()
+        rc = self.lib.tlb3_diagnostics(self._h, ctypes.byref(d))
+        if rc < 0 and rc != EUNSTABLE:
+            raise TlbError(rc, last_error())
+        return dict(mass=np.array(d.mass[:]), nonfinite=int(d.nonfinite), rc=rc)
+
+
+def lattice3_from_workload(w, stream=None) -> Lattice3D:
+    """Create and initialise a Lattice3D from a ``workloads.Workload3``."""
+    L = Lattice3D(w.nx, w.ny, w.nz, w.edges, stream=stream)
+    L.set_geometry(w.mask)
+    L.set_params(w.params)
+    L.set_fields(w.c1, w.c2, w.ux, w.uy, w.uz, w.p)
+    return L

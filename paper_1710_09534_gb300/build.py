@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libtlbm.so")
 BUILD = os.path.join(PKG, "_build")
-SOURCES = ["tlbm_api.cpp", "tlbm_batch.cpp", "tlbm_noalloc.cu", "tlbm_peak.cu",
+SOURCES = ["tlbm_api.cpp", "tlbm_batch.cpp", "tlbm_noalloc.cu", "tlbm_peak.cu", "tlbm3d.cu",
            "tlbm_f64.cu", "tlbm_f32.cu", "tlbm_f16.cu", "tlbm_bf16.cu",
            "tlbm_f64_mrt.cu", "tlbm_f32_mrt.cu", "tlbm_f16_mrt.cu", "tlbm_bf16_mrt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -29,17 +29,30 @@ tightly.
 import numpy as np
 
 FIELDS = ("c1", "c2", "c3", "rho", "ux", "uy", "p", "mu1", "mu2", "mu3")
-FLOOR = dict(c1=1.0, c2=1.0, c3=1.0, rho=1.0, ux=1e-4, uy=1e-4)
+FIELDS3 = ("c1", "c2", "c3", "rho", "ux", "uy", "uz", "p", "mu1", "mu2", "mu3")
+FLOOR = dict(c1=1.0, c2=1.0, c3=1.0, rho=1.0, ux=1e-4, uy=1e-4, uz=1e-4)
 TOL64 = 1e-12
 
 REST = (0, 9)
 MOVING = tuple(q for q in range(27) if q not in REST)
 CU = (27, 28, 29, 30)
+# the D3Q19 state: 57 distribution planes (rest populations at 0 and 19), 6 c_i u planes
+GROUPS3 = ((0, 19), tuple(q for q in range(57) if q not in (0, 19)), tuple(range(57, 63)))
 
 
 def floors(params):
     smax = max(params["sigma12"], params["sigma13"], params["sigma23"])
     return dict(FLOOR, p=smax / 32, mu1=smax / params["D"], mu2=smax / params["D"], mu3=smax / params["D"])
+
+
+def assert_oracle_parity3(L, O, params, tol=TOL64, what=""):
+    """FP64 D3Q19 lattice L against the 3D oracle O: every field and every
+    raw-state plane within `tol`."""
+    errs = field_errors(L.fields(), O.fields(), params, FIELDS3)
+    bad = {k: v for k, v in errs.items() if not v < tol}
+    assert not bad, f"{what} field errors above {tol}: {bad}"
+    se, q = state_error(L.state(), O.state(), False, GROUPS3)
+    assert se < tol, f"{what} raw state error {se:.3e} in plane {q}"
 
 
 def relnorm(a, b, floor):
@@ -51,22 +64,25 @@ def field_errors(fg, fo, params, names=FIELDS):
     return {k: relnorm(fg[k], fo[k], fl[k]) for k in names}
 
 
-def plane_errors(sg, so, mrt=False):
-    """Per-plane errors of two raw states [31][ny][nx] against their group
-    scales (see the module docstring); returns an array of 31 errors."""
-    scale = {g: max(float(np.abs(so[list(g)]).max()), 1e-300) for g in (REST, MOVING, CU)}
+def plane_errors(sg, so, mrt=False, groups=(REST, MOVING, CU)):
+    """Per-plane errors of two raw states [planes][...] against their group
+    scales (see the module docstring; `groups` = rest, moving, c_i u planes,
+    the D2Q9 layout by default, GROUPS3 for D3Q19); returns one error per
+    plane."""
+    rest, moving, cu = groups
+    scale = {g: max(float(np.abs(so[list(g)]).max()), 1e-300) for g in (rest, moving, cu)}
     if mrt:
-        scale[MOVING] = max(scale[MOVING], scale[REST])
-    err = np.zeros(31)
+        scale[moving] = max(scale[moving], scale[rest])
+    err = np.zeros(len(rest) + len(moving) + len(cu))
     for g, s_g in scale.items():
         for q in g:
             err[q] = float(np.abs(sg[q] - so[q]).max()) / s_g
     return err
 
 
-def state_error(sg, so, mrt=False):
+def state_error(sg, so, mrt=False, groups=(REST, MOVING, CU)):
     """Largest per-plane error and the plane it occurs in."""
-    e = plane_errors(sg, so, mrt)
+    e = plane_errors(sg, so, mrt, groups)
     q = int(np.argmax(e))
     return float(e[q]), q
 

@@ -1,0 +1,101 @@
+"""The D3Q19 form on the GPU (through the C ABI) against the 3D FP64 oracle:
+every field and every raw-state plane within 1e-12 (the norms of parity.py,
+with the D3Q19 plane groups), on random lattices with every kind of edge and
+solid, drops on a wetting wall, the smallest lattices, a state that reaches
+a ragged tail of blocks in x, and a full-size lattice of the benchmark."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import OracleLattice3D
+from parity import assert_oracle_parity3
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_09534_gb300 import build
+    build.build()
+    import paper_1710_09534_gb300 as T
+    return T
+
+
+def pair(T, w):
+    L = T.lattice3_from_workload(w)
+    O = OracleLattice3D(w.nx, w.ny, w.nz, w.edges, w.mask, w.params)
+    O.set_fields(w.c1, w.c2, w.ux, w.uy, w.uz, w.p)
+    return L, O
+
+
+@pytest.mark.parametrize("shape,seed,edges,solids", [
+    ((20, 18, 16), 1, (0, 0, 1, 2, 0, 0), ("sphere",)),
+    ((17, 13, 11), 2, (1, 2, 1, 1, 2, 1), ("pillar", "corner")),
+    ((24, 12, 14), 3, (0, 0, 0, 0, 0, 0), ("sphere", "corner")),
+    ((131, 9, 7), 4, (2, 1, 0, 0, 1, 2), ("pillar",)),       # a ragged second block in x
+    ((12, 20, 9), 5, (0, 0, 2, 1, 0, 0), ("sphere", "sphere")),
+])
+def test_random_lattices_fp64(T, shape, seed, edges, solids):
+    w = W.random_lattice3(*shape, seed, edges=edges, solids=solids)
+    L, O = pair(T, w)
+    for n in (1, 30):
+        L.step(n)
+        O.step(n)
+        assert_oracle_parity3(L, O, w.params, what=f"{w.name} after {n}")
+
+
+def test_drops_on_a_wetting_wall_300_steps(T):
+    w = W.drops3d_on_wall(48, 24, 40, R=10.0)
+    L, O = pair(T, w)
+    L.step(300)
+    O.step(300)
+    assert_oracle_parity3(L, O, w.params, what=w.name)
+
+
+def test_zero_steps_and_smallest_lattices(T):
+    for shape, edges in (((3, 3, 3), (0,) * 6), ((4, 5, 3), (1, 2, 0, 0, 2, 2)), ((3, 4, 6), (0, 0, 1, 2, 0, 0))):
+        w = W.random_lattice3(*shape, 7, edges=edges, solids=())
+        L, O = pair(T, w)
+        assert_oracle_parity3(L, O, w.params, what=f"{shape} init")
+        L.step(12)
+        O.step(12)
+        assert_oracle_parity3(L, O, w.params, what=f"{shape}")
+
+
+def test_mass_diagnostics_fp64(T):
+    w = W.random_lattice3(22, 16, 14, 8, edges=(0, 0, 1, 2, 1, 1), solids=("sphere", "corner"))
+    L, O = pair(T, w)
+    d0 = L.diagnostics()
+    L.step(60)
+    O.step(60)
+    d1 = L.diagnostics()
+    assert d1["nonfinite"] == 0 and d1["rc"] == 0
+    assert np.allclose(d1["mass"], O.mass(), rtol=1e-13, atol=1e-11)
+    assert np.allclose(d1["mass"][:2], d0["mass"][:2], rtol=1e-12)
+
+
+def test_error_codes(T):
+    w = W.random_lattice3(8, 8, 8, 9, solids=())
+    L = T.Lattice3D(8, 8, 8, w.edges)
+    with pytest.raises(T.TlbError) as e:
+        L.step(1)
+    assert e.value.code == T.ESTATE
+    for bad in (dict(collision=1.0), dict(lid_u=0.01), dict(theta12_deg=w.params["theta12_deg"] + 20)):
+        with pytest.raises(T.TlbError) as e:
+            L.set_params(dict(w.params, **bad))
+        assert e.value.code == T.EINVAL
+    with pytest.raises(T.TlbError) as e:
+        T.Lattice3D(8, 8, 8, (0, 1, 0, 0, 0, 0))  # periodic edge paired with a wall
+    assert e.value.code == T.EINVAL
+
+
+def test_full_size_benchmark_lattice_fp64(T):
+    """The benchmark's 3D lattice, two steps, every node compared."""
+    w = W.drops3d_on_wall(192, 96, 192)
+    L, O = pair(T, w)
+    L.step(2)
+    O.step(2)
+    assert_oracle_parity3(L, O, w.params, what=w.name)
