@@ -332,14 +332,16 @@ void tlb_batch_destroy(tlb_batch *batch);
  * 1/18, 1/36): Eqs. 1-20 with the Eq. 20 stencils over its 18 links, the
  * Eq. 42 wetting ghost on every link into a wetting solid (Eq. 43 otherwise),
  * half-way bounce-back (Eq. 44), FP64 storage and arithmetic, BGK collision.
- * Body force G = rho (gx, gy, 0).  Node arrays are [nz][ny][nx], x fastest.
+ * Body force G = rho (gx, gy, 0).  Node arrays are [nz][ny][nx], x fastest;
+ * nx, ny, nz >= 3 and nx*ny*nz < 2^31 (TLB_EINVAL otherwise).
  * edges[6] = {x-, x+, y-, y+, z-, z+}, each TLB_EDGE_PERIODIC, _WETTING or
  * _NEUTRAL (no lid); a periodic edge needs a periodic opposite edge; at a
  * site outside in several axes the first outside axis in x, y, z order
  * whose edge is not periodic decides.  Mask values as for tlb_set_geometry.
  * One step is three launches on the lattice's stream (order parameters into
  * two planes, chemical potentials into two planes, then the fused update and
- * push).  Ownership and errors as for the 2D calls; the library allocates no
+ * push; equal densities and viscosities in the three fluids select an update
+ * without the terms that then vanish).  Ownership and errors as for the 2D calls; the library allocates no
  * device memory (workspace from tlb3_workspace_bytes, 256-byte aligned).
  *   tlb3_set_params: TLB_EINVAL as tlb_set_params, and for collision != 0 or
  *     lid_u != 0.

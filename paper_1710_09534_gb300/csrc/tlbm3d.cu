@@ -26,6 +26,7 @@
 
 #include "tlbm.h"
 #include "tlbm_internal.h"
+#include "tlbm_device.cuh"
 
 namespace tlb3 {
 
@@ -57,15 +58,37 @@ struct Geo3 {
     long long plane;  // elements per plane = nz * ny * pitch
 };
 
-// Derived constants (host-computed from tlb_params).
+// Derived constants (host-computed from tlb_params).  Stencils are formed
+// scaled so that their weights are small integers: G = 12 grad (weights 2 on
+// the axis links, 1 on the diagonal ones), L6 = 6 lap (the same weights, minus
+// 24 times the centre); the factors 1/12 and 1/6 sit in these constants.
 struct Prm3 {
-    double lam[3], lamT, two_lamT, k12D, k34Dlam[2], k4D;
-    double eta[2], tau[2];
-    double rho[3], nu[3], M[2];
+    double eta[2], rho[3], nu[3];
     double l3_l1, l3_l2;
+    double k4D;                    // 4 / D (Eq. 42)
     double cos12, cos13, cos23;
-    double gx, gy;
+    double kl[2], kT, kd6[2];      // Eq. 8: 12 lambda_i / D, 24 lambda_T / D, (3/4) D lambda_i / 6
+    double qa[2][2];               // (mu_i - mu_3) / 12 = qa[i][0] mu_1 + qa[i][1] mu_2
+    double drho12[2];              // (rho_i - rho_3) / 12
+    double aM6[2];                 // (rho_i - rho_3) M_i / 6 (Eq. 12 from L6 mu_i)
+    double nu3, dnu[2];            // nu_3, nu_i - nu_3 (Eq. 15)
+    double gx, gy;                 // G = rho (gx, gy, 0)
+    // order parameters (Eqs. 1a, 2a, 11a)
+    double omt[2];                 // 1 - 1/tau_i
+    double e0[2], itau[2];         // (w_0 - 1) eta_i / tau_i, 1 / tau_i
+    double aw[2][2];               // w eta_i / tau_i (axis, diagonal)
+    double kq[2], sq[2];           // 3 w36 / tau_i, 3 w36 (1 - 1/(2 tau_i))
+    // uniform properties (rho, nu equal in the three fluids)
+    double rho0, irho, hirho, prho;  // rho, 1/rho, 1/(2 rho), -rho/4
+    double itg0, omtg0, kG0, Kw0[2], Rw0[2], p3tg0, Gc[2];
 };
+
+// Per-node link word: bit k-1 (k = 1..18) set when x + e_k is a fluid node
+// (inside the lattice or across a periodic edge); bits 18..22 the wetting
+// weight n_w = sum of 36 w_k over the links into wetting solids; bit 31 set
+// on solid nodes.
+constexpr uint32_t LNK_SOLID = 1u << 31;
+constexpr int LNK_NW = 18;
 
 __device__ __forceinline__ long long node_off(const Geo3& g, int x, int y, int z)
 {
@@ -92,24 +115,77 @@ __device__ __forceinline__ int site(const Geo3& g, const uint8_t* __restrict__ k
     return kind[off];
 }
 
-// Eq. 8 for i = 1, 2 from c_1, c_2 and their Laplacians.
-__device__ __forceinline__ void chem_pot(const Prm3& P, double c1, double c2, double lap1, double lap2, double& mu1,
+// Eq. 8 for i = 1, 2 from c_1, c_2 and L6 = 6 lap c_i; c (1 - c)(1 - 2c) in
+// Horner form c (1 + c (2c - 3)).
+__device__ __forceinline__ void chem_pot(const Prm3& P, double c1, double c2, double l6c1, double l6c2, double& mu1,
                                          double& mu2)
 {
     const double c3 = 1.0 - c1 - c2;
-    const double t = P.two_lamT * c1 * c2 * c3;
-    mu1 = P.k12D * (P.lam[0] * c1 * (1.0 - c1) * (1.0 - 2.0 * c1) - t) - P.k34Dlam[0] * lap1;
-    mu2 = P.k12D * (P.lam[1] * c2 * (1.0 - c2) * (1.0 - 2.0 * c2) - t) - P.k34Dlam[1] * lap2;
+    const double t = P.kT * (c1 * c2) * c3;
+    const double h1 = c1 * fma(c1, fma(2.0, c1, -3.0), 1.0);
+    const double h2 = c2 * fma(c2, fma(2.0, c2, -3.0), 1.0);
+    mu1 = fma(-P.kd6[0], l6c1, fma(P.kl[0], h1, -t));
+    mu2 = fma(-P.kd6[1], l6c2, fma(P.kl[1], h2, -t));
 }
+
+// Element offsets of the 18 neighbours of node (x, y, z), periodic wrap
+// included (the wrapped offset is in range on every edge; a link into a
+// solid or a wall is never followed).
+struct Nb3 {
+    long long dx[3], dy[3], dz[3];
+    __device__ __forceinline__ Nb3(const Geo3& g, int x, int y, int z)
+    {
+        const long long P = g.pitch, R = (long long)g.ny * g.pitch;
+        dx[0] = x == 0 ? g.nx - 1 : -1;
+        dx[1] = 0;
+        dx[2] = x == g.nx - 1 ? -(long long)(g.nx - 1) : 1;
+        dy[0] = y == 0 ? (g.ny - 1) * P : -P;
+        dy[1] = 0;
+        dy[2] = y == g.ny - 1 ? -(g.ny - 1) * P : P;
+        dz[0] = z == 0 ? (g.nz - 1) * R : -R;
+        dz[1] = 0;
+        dz[2] = z == g.nz - 1 ? -(g.nz - 1) * R : R;
+    }
+    __device__ __forceinline__ long long off(int k) const { return dx[ex(k) + 1] + dy[ey(k) + 1] + dz[ez(k) + 1]; }
+    // the neighbour's element offset when link k is fluid, else the node's own
+    // (Eq. 43: a solid neighbour takes the centre's value)
+    __device__ __forceinline__ long long at(uint32_t L, long long o, int k) const
+    {
+        return (L >> (k - 1)) & 1u ? o + off(k) : o;
+    }
+};
 
 // ---- kernels --------------------------------------------------------------
 
-// Node (x, y, z) of a launch over the whole lattice: grid (ceil(nx/128), ny, nz).
-#define NODE_OF_THREAD                                           \
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;         \
-    const int y = blockIdx.y, z = blockIdx.z;                    \
-    if (x >= g.nx) return;                                       \
+// Node (x, y, z) of a launch over the whole lattice, one thread per node in
+// x-fastest order (no idle threads at the row ends): grid ceil(nodes / 128).
+#define NODE_OF_THREAD                                                         \
+    const unsigned i_ = blockIdx.x * blockDim.x + threadIdx.x;                 \
+    if (i_ >= (unsigned)g.nx * (unsigned)g.ny * (unsigned)g.nz) return;        \
+    const unsigned r_ = i_ / (unsigned)g.nx;                                   \
+    const int x = (int)(i_ - r_ * (unsigned)g.nx);                             \
+    const int y = (int)(r_ % (unsigned)g.ny), z = (int)(r_ / (unsigned)g.ny);  \
     const long long o = node_off(g, x, y, z);
+
+// Link words of every node (from the node kinds and the edges).
+__global__ void k3_links(const uint8_t* __restrict__ kind, uint32_t* __restrict__ lnk, Geo3 g)
+{
+    NODE_OF_THREAD
+    uint32_t w = LNK_SOLID;
+    if (kind[o] == K_FLUID) {
+        w = 0;
+        uint32_t nw = 0;
+#pragma unroll
+        for (int k = 1; k < Q; k++) {
+            long long nb = 0;
+            const int s = site(g, kind, x + ex(k), y + ey(k), z + ez(k), nb);
+            if (s == K_FLUID) w |= 1u << (k - 1);
+            else if (s == K_WET) nw += k <= 6 ? 2u : 1u;
+        }
+        w |= nw << LNK_NW;
+    }
+    lnk[o] = w;
+}
 
 // c_1, c_2 of every node (Eq. 13a); zero on solids.
 __global__ void k3_csum(const double* __restrict__ f, double* __restrict__ cpl, const uint8_t* __restrict__ kind,
@@ -129,190 +205,305 @@ __global__ void k3_csum(const double* __restrict__ f, double* __restrict__ cpl, 
     cpl[PL + o] = b;
 }
 
-// mu_1, mu_2 of every fluid node (Eq. 8, Eq. 20b with the Eq. 42 ghosts).
-__global__ void k3_mu(const double* __restrict__ cpl, double* __restrict__ mpl, const uint8_t* __restrict__ kind,
+// Sum over the 9 opposite pairs of a pair-wise quantity: axis pairs weighted
+// 2, diagonal pairs 1 (the integer weights 36 w_k).
+#define W36_SUM(S) fma(2.0, ((S)[0] + (S)[1]) + (S)[2], (((S)[3] + (S)[4]) + ((S)[5] + (S)[6])) + ((S)[7] + (S)[8]))
+
+// mu_1, mu_2 of every fluid node: Eq. 8 with the Eq. 20b Laplacian, whose
+// links into wetting solids take the Eq. 42 ghost c + o_i (with the wall
+// value of c taken as the node's own, dx = 1) and into neutral solids c.
+__global__ void k3_mu(const double* __restrict__ cpl, double* __restrict__ mpl, const uint32_t* __restrict__ lnk,
                       Geo3 g, Prm3 P)
 {
     NODE_OF_THREAD
     const long long PL = g.plane;
+    const uint32_t L = lnk[o];
     double mu1 = 0.0, mu2 = 0.0;
-    if (kind[o] == K_FLUID) {
+    if (!(L & LNK_SOLID)) {
+        const Nb3 nb(g, x, y, z);
         const double c1 = cpl[o], c2 = cpl[PL + o];
-        const double c3 = 1.0 - c1 - c2;
-        // Eq. 42 with the wall value of c taken as the node's own (dx = 1)
-        const double o1 = P.k4D * (P.cos13 * c1 * c3 + P.cos12 * c1 * c2);
-        const double o2 = P.k4D * (-P.cos12 * c1 * c2 + P.cos23 * c2 * c3);
-        double l1 = 0.0, l2 = 0.0;
+        double s1[9], s2[9];
 #pragma unroll
-        for (int k = 1; k < Q; k++) {
-            long long nb = 0;
-            const int s = site(g, kind, x + ex(k), y + ey(k), z + ez(k), nb);
-            double v1, v2;
-            if (s == K_FLUID) {
-                v1 = cpl[nb];
-                v2 = cpl[PL + nb];
-            } else if (s == K_WET) {
-                v1 = c1 + o1;
-                v2 = c2 + o2;
-            } else {
-                v1 = c1;
-                v2 = c2;
-            }
-            // 2 w_k / cs^2 = 6 w_k
-            l1 += 6.0 * wk(k) * (v1 - c1);
-            l2 += 6.0 * wk(k) * (v2 - c2);
+        for (int p = 0; p < 9; p++) {
+            const long long ap = nb.at(L, o, 2 * p + 1), am = nb.at(L, o, 2 * p + 2);
+            s1[p] = cpl[ap] + cpl[am];
+            s2[p] = cpl[PL + ap] + cpl[PL + am];
         }
+        const double c3 = 1.0 - c1 - c2;
+        const double nw = (double)(int)((L >> LNK_NW) & 31u);
+        const double o1 = P.k4D * fma(P.cos13, c1 * c3, P.cos12 * (c1 * c2));
+        const double o2 = P.k4D * fma(-P.cos12, c1 * c2, P.cos23 * (c2 * c3));
+        const double l1 = fma(nw, o1, fma(-24.0, c1, W36_SUM(s1)));
+        const double l2 = fma(nw, o2, fma(-24.0, c2, W36_SUM(s2)));
         chem_pot(P, c1, c2, l1, l2, mu1, mu2);
     }
     mpl[o] = mu1;
     mpl[PL + o] = mu2;
 }
 
+// X . e_k of the direction k = 2p + 1 of opposite pair p (the odd member),
+// and the same weighted by 36 w_k (x 2 on the axis pairs).
+template <int p>
+__device__ __forceinline__ double edot(const double X[3])
+{
+    if constexpr (p < 3) return X[p];
+    else if constexpr (p == 3) return X[0] + X[1];
+    else if constexpr (p == 4) return X[0] - X[1];
+    else if constexpr (p == 5) return X[0] + X[2];
+    else if constexpr (p == 6) return X[0] - X[2];
+    else if constexpr (p == 7) return X[1] + X[2];
+    else return X[1] - X[2];
+}
+template <int p>
+__device__ __forceinline__ double wdot(const double X[3])
+{
+    if constexpr (p < 3) return 2.0 * X[p];
+    else return edot<p>(X);
+}
+
 // Macroscopic state of a fluid node: c, mu (from the planes), rho (Eq. 14),
-// the Eq. 20 gradients with the Eq. 43 symmetric ghosts, F_s + G, u and p
-// (Eqs. 13b, 13c), the F_a factor of Eq. 12 and 1/tau_g (Eqs. 15, 18b).
-struct Mac3 {
-    double c1, c2, rho, mu1, mu2;
+// 12 grad c_i (Eq. 20a with the Eq. 43 ghosts), u and p (Eqs. 13b, 13c),
+// F_s + G, and in the general case grad rho, the F_a factor of Eq. 12 (Eq.
+// 20b on mu_i, Eq. 43 ghosts) and 1/tau_g (Eqs. 15, 18b); the g populations.
+struct Node3 {
+    double c1, c2, mu1, mu2, rho;
     double u[3], usq, p;
-    double gr[3], Ft[3];
-    double a, itg;
+    double T[3];  // 3 (F_s + G)
+    double H[3];  // grad rho + T
+    double aF, itg;
+    double g[Q];
 };
 
-__device__ __forceinline__ void macros(const Geo3& g, const uint8_t* __restrict__ kind, const double* __restrict__ f,
-                                       const double* __restrict__ cpl, const double* __restrict__ mpl,
-                                       const Prm3& P, int x, int y, int z, long long o, Mac3& m)
+template <bool UNI>
+__device__ __forceinline__ void node3(const Geo3& g, const Prm3& P, const double* __restrict__ f,
+                                      const double* __restrict__ cpl, const double* __restrict__ mpl, uint32_t L,
+                                      const Nb3& nb, long long o, Node3& n)
 {
     const long long PL = g.plane;
-    m.c1 = cpl[o];
-    m.c2 = cpl[PL + o];
-    m.mu1 = mpl[o];
-    m.mu2 = mpl[PL + o];
-    m.rho = m.c1 * P.rho[0] + m.c2 * P.rho[1] + (1.0 - m.c1 - m.c2) * P.rho[2];
-    double g1[3] = {0, 0, 0}, g2[3] = {0, 0, 0}, lm1 = 0.0, lm2 = 0.0;
+    n.c1 = cpl[o];
+    n.c2 = cpl[PL + o];
+    n.mu1 = mpl[o];
+    n.mu2 = mpl[PL + o];
+    double d1[9], d2[9], s1[9], s2[9];
 #pragma unroll
-    for (int k = 1; k < Q; k++) {
-        long long nb = 0;
-        const int s = site(g, kind, x + ex(k), y + ey(k), z + ez(k), nb);
-        double v1 = m.c1, v2 = m.c2, w1 = m.mu1, w2 = m.mu2;  // Eq. 43: a solid neighbour takes the centre's value
-        if (s == K_FLUID) {
-            v1 = cpl[nb];
-            v2 = cpl[PL + nb];
-            w1 = mpl[nb];
-            w2 = mpl[PL + nb];
+    for (int p = 0; p < 9; p++) {
+        const long long ap = nb.at(L, o, 2 * p + 1), am = nb.at(L, o, 2 * p + 2);
+        d1[p] = cpl[ap] - cpl[am];
+        d2[p] = cpl[PL + ap] - cpl[PL + am];
+        if constexpr (!UNI) {
+            s1[p] = mpl[ap] + mpl[am];
+            s2[p] = mpl[PL + ap] + mpl[PL + am];
         }
-        const double w3 = 3.0 * wk(k);  // w_k / cs^2
-        const int e[3] = {ex(k), ey(k), ez(k)};
+    }
+    double G1[3], G2[3];
+    G1[0] = fma(2.0, d1[0], (d1[3] + d1[4]) + (d1[5] + d1[6]));
+    G1[1] = fma(2.0, d1[1], (d1[3] - d1[4]) + (d1[7] + d1[8]));
+    G1[2] = fma(2.0, d1[2], (d1[5] - d1[6]) + (d1[7] - d1[8]));
+    G2[0] = fma(2.0, d2[0], (d2[3] + d2[4]) + (d2[5] + d2[6]));
+    G2[1] = fma(2.0, d2[1], (d2[3] - d2[4]) + (d2[7] + d2[8]));
+    G2[2] = fma(2.0, d2[2], (d2[5] - d2[6]) + (d2[7] - d2[8]));
+    // g moments from the sums and differences of opposite pairs
+    const double* gq = f + 2 * Q * PL;
+    n.g[0] = gq[o];
+    double gs[9], gd[9];
+#pragma unroll
+    for (int p = 0; p < 9; p++) {
+        n.g[2 * p + 1] = gq[(2 * p + 1) * PL + o];
+        n.g[2 * p + 2] = gq[(2 * p + 2) * PL + o];
+        gs[p] = n.g[2 * p + 1] + n.g[2 * p + 2];
+        gd[p] = n.g[2 * p + 1] - n.g[2 * p + 2];
+    }
+    const double sum = (((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7]))) + gs[8];
+    double mom[3];
+    mom[0] = gd[0] + ((gd[3] + gd[4]) + (gd[5] + gd[6]));
+    mom[1] = gd[1] + ((gd[3] - gd[4]) + (gd[7] + gd[8]));
+    mom[2] = gd[2] + ((gd[5] - gd[6]) + (gd[7] - gd[8]));
+    // F_s = sum_i mu_i grad c_i with grad c_3 = -grad c_1 - grad c_2 and
+    // mu_3 from sum_i mu_i / lambda_i = 0
+    const double m1 = fma(P.qa[0][0], n.mu1, P.qa[0][1] * n.mu2);
+    const double m2 = fma(P.qa[1][0], n.mu1, P.qa[1][1] * n.mu2);
+    double F[3];
+    if constexpr (UNI) {
+        n.rho = P.rho0;
+        F[0] = fma(m1, G1[0], fma(m2, G2[0], P.Gc[0]));
+        F[1] = fma(m1, G1[1], fma(m2, G2[1], P.Gc[1]));
+        F[2] = fma(m1, G1[2], m2 * G2[2]);
+#pragma unroll
+        for (int a = 0; a < 3; a++) n.u[a] = fma(P.hirho, F[a], P.irho * mom[a]);
+        n.usq = fma(n.u[0], n.u[0], fma(n.u[1], n.u[1], n.u[2] * n.u[2]));
+        // Eq. 13c: p = (1/2) [sum_{k != 0} g_k + rho w_0 (-3/2) u.u] (grad rho = 0)
+        n.p = fma(0.5, sum, P.prho * n.usq);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            if (e[a] != 0) {
-                g1[a] += e[a] * w3 * v1;
-                g2[a] += e[a] * w3 * v2;
-            }
+            n.T[a] = 3.0 * F[a];
+            n.H[a] = n.T[a];
         }
-        lm1 += 2.0 * w3 * (w1 - m.mu1);
-        lm2 += 2.0 * w3 * (w2 - m.mu2);
-    }
-    // mu_3 from sum_i mu_i / lambda_i = 0; F_s = sum_i mu_i grad c_i with grad c3 = -grad c1 - grad c2
-    const double mu3 = -(P.l3_l1 * m.mu1 + P.l3_l2 * m.mu2);
-    const double G[3] = {m.rho * P.gx, m.rho * P.gy, 0.0};
-    double mom[3] = {0, 0, 0}, sum = 0.0;
-    const double* gq = f + 2 * Q * PL;
+        n.aF = 0.0;
+        n.itg = P.itg0;
+    } else {
+        n.rho = fma(n.c1, P.rho[0] - P.rho[2], fma(n.c2, P.rho[1] - P.rho[2], P.rho[2]));
+        double gr[3];
 #pragma unroll
-    for (int k = 0; k < Q; k++) {
-        const double gk = gq[k * PL + o];
-        if (ex(k)) mom[0] += ex(k) * gk;
-        if (ey(k)) mom[1] += ey(k) * gk;
-        if (ez(k)) mom[2] += ez(k) * gk;
-        if (k) sum += gk;
-    }
-    double ug = 0.0;
-    m.usq = 0.0;
+        for (int a = 0; a < 3; a++) gr[a] = fma(P.drho12[0], G1[a], P.drho12[1] * G2[a]);
+        F[0] = fma(m1, G1[0], fma(m2, G2[0], n.rho * P.gx));
+        F[1] = fma(m1, G1[1], fma(m2, G2[1], n.rho * P.gy));
+        F[2] = fma(m1, G1[2], m2 * G2[2]);
+        const double ir = tlb::rcp(n.rho);
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        m.gr[a] = (P.rho[0] - P.rho[2]) * g1[a] + (P.rho[1] - P.rho[2]) * g2[a];
-        m.Ft[a] = m.mu1 * g1[a] + m.mu2 * g2[a] - mu3 * (g1[a] + g2[a]) + G[a];
-        m.u[a] = (mom[a] + 0.5 * m.Ft[a]) / m.rho;
-        ug += m.u[a] * m.gr[a];
-        m.usq += m.u[a] * m.u[a];
+        for (int a = 0; a < 3; a++) n.u[a] = fma(0.5, F[a], mom[a]) * ir;
+        n.usq = fma(n.u[0], n.u[0], fma(n.u[1], n.u[1], n.u[2] * n.u[2]));
+        const double ug = fma(n.u[0], gr[0], fma(n.u[1], gr[1], n.u[2] * gr[2]));
+        // Eq. 13c: p = (1/2) [sum_{k != 0} g_k + u.grad rho / 2 + rho w_0 (-3/2) u.u]
+        n.p = fma(0.5, sum, fma(0.25, ug, (-0.25 * n.rho) * n.usq));
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            n.T[a] = 3.0 * F[a];
+            n.H[a] = gr[a] + n.T[a];
+        }
+        const double l1 = fma(-24.0, n.mu1, W36_SUM(s1));
+        const double l2 = fma(-24.0, n.mu2, W36_SUM(s2));
+        n.aF = fma(P.aM6[0], l1, P.aM6[1] * l2);
+        const double nu = fma(n.c1, P.dnu[0], fma(n.c2, P.dnu[1], P.nu3));
+        n.itg = tlb::rcp(fma(3.0, nu, 0.5));
     }
-    // Eq. 13c: p = cs^2 / (1 - w_0) [sum_{k != 0} g_k + u.grad rho / 2 + rho s_0(u)], cs^2 / (1 - w_0) = 1/2
-    m.p = 0.5 * (sum + 0.5 * ug + m.rho * (wk(0) * (-1.5 * m.usq)));
-    m.a = (P.rho[0] - P.rho[2]) * P.M[0] * lm1 + (P.rho[1] - P.rho[2]) * P.M[1] * lm2;
-    const double nu = m.c1 * P.nu[0] + m.c2 * P.nu[1] + (1.0 - m.c1 - m.c2) * P.nu[2];
-    m.itg = 1.0 / (3.0 * nu + 0.5);
+}
+
+// Collision and push of opposite pair p (directions k = 2p + 1 and k + 1).
+// With beta = 3 e_k.u and a = beta^2/2 - (3/2) u.u the BGK updates of Eqs. 1a,
+// 1b with Eqs. 2a, 2b, 4, 11a, 11b take the form
+//   f'_{k, k+1} = (1 - 1/tau) f + A_w +- V,
+//   g'_{k, k+1} = (1 - 1/tau_g) g + Sym +- Anti,
+//   Sym = beta K_X + a R_X + P_X,  Anti = a K_X + beta R_X + A_X,
+// K_X = K_w e.H, R_X = w rho/tau_g - K_w u.H, P_X = 3 w p/tau_g - K_w u.T,
+// A_X = K_w e.T + w a_F beta, K_w = w (1 - 1/(2 tau_g)).
+struct Coll3 {
+    double omt1, omt2, omtg, t0;
+    double A1[2], A2[2], RX[2], PX[2];
+    double b3[3], Q1[3], Q2[3], Hs[3], Ts[3];
+    double wa36;
+};
+
+template <bool UNI, int p>
+__device__ __forceinline__ void pair3(const Coll3& C, const double* __restrict__ fA, double* __restrict__ fB,
+                                      const Node3& n, const Nb3& nb, uint32_t L, long long o, long long PL)
+{
+    constexpr int kp = 2 * p + 1, km = 2 * p + 2, c = p < 3 ? 0 : 1;
+    const double beta = edot<p>(C.b3);
+    const double V1 = wdot<p>(C.Q1), V2 = wdot<p>(C.Q2);
+    const double KX = wdot<p>(C.Hs);
+    double AX;
+    if constexpr (UNI) AX = KX;
+    else AX = fma(p < 3 ? 2.0 * C.wa36 : C.wa36, beta, wdot<p>(C.Ts));
+    const double a = fma(beta, 0.5 * beta, C.t0);
+    const double sym = fma(beta, KX, fma(a, C.RX[c], C.PX[c]));
+    const double anti = fma(a, KX, fma(beta, C.RX[c], AX));
+    const double o1p = fma(C.omt1, fA[kp * PL + o], C.A1[c] + V1);
+    const double o1m = fma(C.omt1, fA[km * PL + o], C.A1[c] - V1);
+    const double o2p = fma(C.omt2, fA[(Q + kp) * PL + o], C.A2[c] + V2);
+    const double o2m = fma(C.omt2, fA[(Q + km) * PL + o], C.A2[c] - V2);
+    const double ogp = fma(C.omtg, n.g[kp], sym + anti);
+    const double ogm = fma(C.omtg, n.g[km], sym - anti);
+    // push to x + e_k, or back into slot k-bar of this node (Eq. 44)
+    const long long dp = (L >> (kp - 1)) & 1u ? kp * PL + o + nb.off(kp) : km * PL + o;
+    const long long dm = (L >> (km - 1)) & 1u ? km * PL + o + nb.off(km) : kp * PL + o;
+    fB[dp] = o1p;
+    fB[Q * PL + dp] = o2p;
+    fB[2 * Q * PL + dp] = ogp;
+    fB[dm] = o1m;
+    fB[Q * PL + dm] = o2m;
+    fB[2 * Q * PL + dm] = ogm;
 }
 
 // One BGK time step of every fluid node: collision (Eqs. 1a, 1b, 2a, 2b, 4,
-// 11a, 11b, 19) and the push to x + e_k, or back into slot k-bar of the node
-// itself on a link into a solid (Eq. 44).
+// 11a, 11b, 19) and the push to x + e_k.  UNI: equal densities and
+// viscosities (grad rho = 0, F_a = 0, tau_g constant).
+template <bool UNI>
 __global__ void __launch_bounds__(128)
 k3_update(const double* __restrict__ fA, double* __restrict__ fB, double* __restrict__ cu,
-          const double* __restrict__ cpl, const double* __restrict__ mpl, const uint8_t* __restrict__ kind, Geo3 g,
+          const double* __restrict__ cpl, const double* __restrict__ mpl, const uint32_t* __restrict__ lnk, Geo3 g,
           Prm3 P)
 {
     NODE_OF_THREAD
-    if (kind[o] != K_FLUID) return;
+    const uint32_t L = lnk[o];
+    if (L & LNK_SOLID) return;
     const long long PL = g.plane;
-    Mac3 m;
-    macros(g, kind, fA, cpl, mpl, P, x, y, z, o, m);
-    const double c[2] = {m.c1, m.c2};
-    const double mu[2] = {m.mu1, m.mu2};
-    double dcu[2][3];
+    const Nb3 nb(g, x, y, z);
+    Node3 n;
+    node3<UNI>(g, P, fA, cpl, mpl, L, nb, o, n);
+    constexpr double w0 = 1.0 / 3.0, w36 = 1.0 / 36.0;
+    Coll3 C;
+    // order parameters: Q_i = 3 w36 [c_i u / tau_i + (1 - 1/(2 tau_i)) d(c_i u)],
+    // d(c_i u) against the previous step's (Eq. 19), which is replaced
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const double cua = c[q] * m.u[a];
-            dcu[q][a] = cua - cu[(3 * q + a) * PL + o];
-            cu[(3 * q + a) * PL + o] = cua;
-        }
+    for (int a = 0; a < 3; a++) {
+        const double cu1 = n.c1 * n.u[a], cu2 = n.c2 * n.u[a];
+        const double d1 = cu1 - cu[a * PL + o], d2 = cu2 - cu[(3 + a) * PL + o];
+        cu[a * PL + o] = cu1;
+        cu[(3 + a) * PL + o] = cu2;
+        C.Q1[a] = fma(P.kq[0], cu1, P.sq[0] * d1);
+        C.Q2[a] = fma(P.kq[1], cu2, P.sq[1] * d2);
     }
-    const double Fa[3] = {m.u[0] * m.a, m.u[1] * m.a, m.u[2] * m.a};
-    const double kg = 1.0 - 0.5 * m.itg;
+    C.omt1 = P.omt[0];
+    C.omt2 = P.omt[1];
+    const double E1 = fma(P.e0[0], n.mu1, P.itau[0] * n.c1);
+    const double E2 = fma(P.e0[1], n.mu2, P.itau[1] * n.c2);
 #pragma unroll
-    for (int k = 0; k < Q; k++) {
-        const double w = wk(k);
-        const int e[3] = {ex(k), ey(k), ez(k)};
-        const double eu = e[0] * m.u[0] + e[1] * m.u[1] + e[2] * m.u[2];
-        const double s = w * (3.0 * eu + 4.5 * eu * eu - 1.5 * m.usq);  // Eq. 4
-        double o1, o2, og;
-        {
-            double post[2];
-#pragma unroll
-            for (int q = 0; q < 2; q++) {
-                const double em = P.eta[q] * mu[q];
-                const double feq = k == 0 ? c[q] + (w - 1.0) * em : w * (em + 3.0 * c[q] * eu);  // Eq. 2a
-                const double ed = e[0] * dcu[q][0] + e[1] * dcu[q][1] + e[2] * dcu[q][2];
-                const double src = (1.0 - 0.5 / P.tau[q]) * 3.0 * w * ed;                            // Eq. 11a
-                const double fk = fA[(Q * q + k) * PL + o];
-                post[q] = fk - (fk - feq) / P.tau[q] + src;                                          // Eq. 1a
-            }
-            o1 = post[0];
-            o2 = post[1];
-        }
-        {
-            const double geq = k == 0 ? 3.0 * m.p * (w - 1.0) + m.rho * s : 3.0 * m.p * w + m.rho * s;  // Eq. 2b
-            double br = 0.0, efa = 0.0;
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                br += (e[a] - m.u[a]) * (s * m.gr[a] + 3.0 * (s + w) * m.Ft[a]);
-                efa += e[a] * Fa[a];
-            }
-            const double src = kg * br + 3.0 * w * efa;  // Eq. 11b
-            const double gk = fA[(2 * Q + k) * PL + o];
-            og = gk - (gk - geq) * m.itg + src;          // Eq. 1b
-        }
-        long long d = o;
-        int slot = k;
-        if (k != 0) {
-            long long nb = 0;
-            if (site(g, kind, x + e[0], y + e[1], z + e[2], nb) == K_FLUID) d = nb;
-            else slot = opp(k);
-        }
-        fB[slot * PL + d] = o1;
-        fB[(Q + slot) * PL + d] = o2;
-        fB[(2 * Q + slot) * PL + d] = og;
+    for (int c = 0; c < 2; c++) {
+        C.A1[c] = P.aw[0][c] * n.mu1;
+        C.A2[c] = P.aw[1][c] * n.mu2;
     }
+    // hydrodynamics
+#pragma unroll
+    for (int a = 0; a < 3; a++) C.b3[a] = 3.0 * n.u[a];
+    C.t0 = -1.5 * n.usq;
+    double kG, Kw[2], Rw[2], p3;
+    if constexpr (UNI) {
+        C.omtg = P.omtg0;
+        kG = P.kG0;
+        Kw[0] = P.Kw0[0];
+        Kw[1] = P.Kw0[1];
+        Rw[0] = P.Rw0[0];
+        Rw[1] = P.Rw0[1];
+        p3 = n.p * P.p3tg0;
+    } else {
+        C.omtg = 1.0 - n.itg;
+        kG = fma(-0.5, n.itg, 1.0);
+        Kw[0] = (2.0 * w36) * kG;
+        Kw[1] = w36 * kG;
+        const double ri = n.rho * n.itg;
+        Rw[0] = (2.0 * w36) * ri;
+        Rw[1] = w36 * ri;
+        p3 = 3.0 * n.p * n.itg;
+    }
+    const double uT = fma(n.u[0], n.T[0], fma(n.u[1], n.T[1], n.u[2] * n.T[2]));
+    double uH = uT;
+    if constexpr (!UNI) uH = fma(n.u[0], n.H[0], fma(n.u[1], n.H[1], n.u[2] * n.H[2]));
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        C.RX[c] = fma(-Kw[c], uH, Rw[c]);
+        C.PX[c] = fma(-Kw[c], uT, (c == 0 ? 2.0 * w36 : w36) * p3);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        C.Hs[a] = Kw[1] * n.H[a];
+        C.Ts[a] = UNI ? C.Hs[a] : Kw[1] * n.T[a];
+    }
+    C.wa36 = w36 * n.aF;
+    // rest direction: g^eq_0 = 3p (w_0 - 1) + rho w_0 t0, G_0 = -w_0 K_G (t0 u.H + u.T)
+    const double geq0 = fma(n.rho * w0, C.t0, (3.0 * (w0 - 1.0)) * n.p);
+    const double P0 = fma(geq0, n.itg, -(w0 * kG) * fma(C.t0, uH, uT));
+    fB[o] = fma(C.omt1, fA[o], E1);
+    fB[Q * PL + o] = fma(C.omt2, fA[Q * PL + o], E2);
+    fB[2 * Q * PL + o] = fma(C.omtg, n.g[0], P0);
+    pair3<UNI, 0>(C, fA, fB, n, nb, L, o, PL);
+    pair3<UNI, 1>(C, fA, fB, n, nb, L, o, PL);
+    pair3<UNI, 2>(C, fA, fB, n, nb, L, o, PL);
+    pair3<UNI, 3>(C, fA, fB, n, nb, L, o, PL);
+    pair3<UNI, 4>(C, fA, fB, n, nb, L, o, PL);
+    pair3<UNI, 5>(C, fA, fB, n, nb, L, o, PL);
+    pair3<UNI, 6>(C, fA, fB, n, nb, L, o, PL);
+    pair3<UNI, 7>(C, fA, fB, n, nb, L, o, PL);
+    pair3<UNI, 8>(C, fA, fB, n, nb, L, o, PL);
 }
 
 // c of every node from dense host-order arrays (c1 then c2, nx*ny*nz each).
@@ -360,16 +551,19 @@ __global__ void k3_init(double* __restrict__ f, double* __restrict__ cu, const d
 }
 
 // The 11 macroscopic fields c1 c2 c3 rho ux uy uz p mu1 mu2 mu3 as dense
-// planes of nx*ny*nz (zero on solids).
+// planes of nx*ny*nz (zero on solids), from the same node3 as the update.
+template <bool UNI>
 __global__ void k3_read(const double* __restrict__ f, const double* __restrict__ cpl, const double* __restrict__ mpl,
-                        const uint8_t* __restrict__ kind, double* __restrict__ out, Geo3 g, Prm3 P)
+                        const uint32_t* __restrict__ lnk, double* __restrict__ out, Geo3 g, Prm3 P)
 {
     NODE_OF_THREAD
     const long long n = ((long long)z * g.ny + y) * g.nx + x, N = (long long)g.nx * g.ny * g.nz;
     double v[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (kind[o] == K_FLUID) {
-        Mac3 m;
-        macros(g, kind, f, cpl, mpl, P, x, y, z, o, m);
+    const uint32_t L = lnk[o];
+    if (!(L & LNK_SOLID)) {
+        const Nb3 nb(g, x, y, z);
+        Node3 m;
+        node3<UNI>(g, P, f, cpl, mpl, L, nb, o, m);
         v[0] = m.c1;
         v[1] = m.c2;
         v[2] = 1.0 - m.c1 - m.c2;
@@ -464,10 +658,14 @@ int err3(int code, const char* fmt, ...)
 struct Layout3 {
     int pitch = 0;
     int64_t plane = 0;
-    int64_t fA = 0, fB = 0, cu = 0, cpl = 0, mpl = 0, kind = 0, part = 0, diag = 0, total = 0;
+    int64_t fA = 0, fB = 0, cu = 0, cpl = 0, mpl = 0, lnk = 0, kind = 0, part = 0, diag = 0, total = 0;
 };
 
-bool size_ok(int nx, int ny, int nz) { return nx >= 3 && ny >= 3 && nz >= 3 && nx <= 65536 && ny <= 65535 && nz <= 65535; }
+// at least 3 nodes per axis; fewer than 2^31 nodes (one 32-bit thread index per node)
+bool size_ok(int nx, int ny, int nz)
+{
+    return nx >= 3 && ny >= 3 && nz >= 3 && (int64_t)nx * ny * nz < ((int64_t)1 << 31);
+}
 
 Layout3 layout3(int nx, int ny, int nz)
 {
@@ -485,6 +683,7 @@ Layout3 layout3(int nx, int ny, int nz)
     L.cu = take(6 * L.plane * 8);
     L.cpl = take(2 * L.plane * 8);
     L.mpl = take(2 * L.plane * 8);
+    L.lnk = take(L.plane * 4);
     L.kind = take(L.plane);
     L.part = take((int64_t)kMassParts3 * 4 * 8);
     L.diag = take(4 * 8);
@@ -503,7 +702,7 @@ struct tlb3_lattice {
     tlb3::Geo3 geo{};
     tlb3::Prm3 prm{};
     int cur = 0;
-    bool have_params = false, have_fields = false;
+    bool have_params = false, have_fields = false, uni = false;
     std::vector<uint8_t> mask;
 
     double* buf(int which) { return (double*)(ws + (which == 0 ? lay.fA : lay.fB)); }
@@ -513,6 +712,7 @@ struct tlb3_lattice {
     double* cpl() { return (double*)(ws + lay.cpl); }
     double* mpl() { return (double*)(ws + lay.mpl); }
     uint8_t* kind() { return (uint8_t*)(ws + lay.kind); }
+    uint32_t* lnk() { return (uint32_t*)(ws + lay.lnk); }
     int64_t n() const { return (int64_t)nx * ny * nz; }
 };
 
@@ -525,13 +725,21 @@ int check3(tlb3_lattice* L)
     return TLB_OK;
 }
 
-dim3 grid3(const tlb3_lattice* L) { return dim3((unsigned)((L->nx + 127) / 128), (unsigned)L->ny, (unsigned)L->nz); }
+dim3 grid3(const tlb3_lattice* L) { return dim3((unsigned)((L->n() + 127) / 128)); }
 
 // c and mu planes of the current state (the first two launches of a step)
 int order_params3(tlb3_lattice* L)
 {
     tlb3::k3_csum<<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cpl(), L->kind(), L->geo);
-    tlb3::k3_mu<<<grid3(L), 128, 0, L->stream>>>(L->cpl(), L->mpl(), L->kind(), L->geo, L->prm);
+    tlb3::k3_mu<<<grid3(L), 128, 0, L->stream>>>(L->cpl(), L->mpl(), L->lnk(), L->geo, L->prm);
+    T3_CUDA(cudaGetLastError());
+    return TLB_OK;
+}
+
+// link words from the node kinds (after every change of the geometry)
+int links3(tlb3_lattice* L)
+{
+    tlb3::k3_links<<<grid3(L), 128, 0, L->stream>>>(L->kind(), L->lnk(), L->geo);
     T3_CUDA(cudaGetLastError());
     return TLB_OK;
 }
@@ -583,7 +791,7 @@ int tlb3_create(int nx, int ny, int nz, const int32_t edges[6], void* dev_worksp
     L->geo.plane = lay.plane;
     for (int e = 0; e < 6; e++) L->geo.edge[e] = edges[e];
     L->mask.assign((size_t)L->n(), 0);
-    if (cudaMemsetAsync(L->ws + lay.kind, 0, (size_t)lay.plane, L->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(L->ws + lay.kind, 0, (size_t)lay.plane, L->stream) != cudaSuccess || links3(L) != TLB_OK ||
         cudaStreamSynchronize(L->stream) != cudaSuccess) {
         delete L;
         return err3(TLB_ECUDA, "clearing the node kinds failed");
@@ -606,6 +814,7 @@ int tlb3_set_geometry(tlb3_lattice* L, const uint8_t* host_mask)
         L->mask[(size_t)i] = m;
     }
     T3_CUDA(cudaMemcpyAsync(L->kind(), kind.data(), kind.size(), cudaMemcpyHostToDevice, L->stream));
+    if ((rc = links3(L))) return rc;
     T3_CUDA(cudaStreamSynchronize(L->stream));
     L->have_fields = false;
     return tlb::clear_error();
@@ -637,34 +846,62 @@ int tlb3_set_params(tlb3_lattice* L, const tlb_params* p)
     const double resid = p->sigma12 * c12 - p->sigma13 * c13 + p->sigma23 * c23;
     if (std::fabs(resid) > 1e-6 * smax) return err3(TLB_EINVAL, "contact angles violate Eq. 39 (residual %g)", resid);
     const double den = l1 * l2 + l1 * l3 + l2 * l3;
-    tlb3::Prm3& P = L->prm;
-    P.lam[0] = l1;
-    P.lam[1] = l2;
-    P.lam[2] = l3;
-    P.lamT = den != 0 ? 3.0 * l1 * l2 * l3 / den : 0.0;  // Eq. 9, continuous form
-    P.two_lamT = 2.0 * P.lamT;
-    P.k12D = 12.0 / p->D;
-    P.k4D = 4.0 / p->D;
-    const double tau[2] = {p->tau1, p->tau2};
-    for (int i = 0; i < 2; i++) {
-        P.k34Dlam[i] = 0.75 * p->D * P.lam[i];
-        P.M[i] = p->M0 / P.lam[i];                       // Eq. 12
-        P.eta[i] = P.M[i] / ((1.0 / 3.0) * (tau[i] - 0.5));  // Eq. 18a, per component
-        P.tau[i] = tau[i];
+    const double lamT = den != 0 ? 3.0 * l1 * l2 * l3 / den : 0.0;  // Eq. 9, continuous form
+    const double lam[2] = {l1, l2}, tau[2] = {p->tau1, p->tau2};
+    const double rho[3] = {p->rho1, p->rho2, p->rho3}, nu[3] = {p->nu1, p->nu2, p->nu3};
+    constexpr double w0 = 1.0 / 3.0, w18 = 1.0 / 18.0, w36 = 1.0 / 36.0;
+    tlb3::Prm3 P{};
+    for (int i = 0; i < 3; i++) {
+        P.rho[i] = rho[i];
+        P.nu[i] = nu[i];
     }
-    P.rho[0] = p->rho1;
-    P.rho[1] = p->rho2;
-    P.rho[2] = p->rho3;
-    P.nu[0] = p->nu1;
-    P.nu[1] = p->nu2;
-    P.nu[2] = p->nu3;
     P.l3_l1 = l3 / l1;
     P.l3_l2 = l3 / l2;
+    P.k4D = 4.0 / p->D;
     P.cos12 = c12;
     P.cos13 = c13;
     P.cos23 = c23;
+    P.kT = 24.0 * lamT / p->D;
+    P.qa[0][0] = (1.0 + P.l3_l1) / 12.0;
+    P.qa[0][1] = P.l3_l2 / 12.0;
+    P.qa[1][0] = P.l3_l1 / 12.0;
+    P.qa[1][1] = (1.0 + P.l3_l2) / 12.0;
+    P.nu3 = nu[2];
     P.gx = p->gx;
     P.gy = p->gy;
+    for (int i = 0; i < 2; i++) {
+        const double M = p->M0 / lam[i];                       // Eq. 12
+        P.eta[i] = M / ((1.0 / 3.0) * (tau[i] - 0.5));         // Eq. 18a, per component
+        P.kl[i] = 12.0 * lam[i] / p->D;
+        P.kd6[i] = 0.75 * p->D * lam[i] / 6.0;
+        P.drho12[i] = (rho[i] - rho[2]) / 12.0;
+        P.aM6[i] = (rho[i] - rho[2]) * M / 6.0;
+        P.dnu[i] = nu[i] - nu[2];
+        P.omt[i] = 1.0 - 1.0 / tau[i];
+        P.itau[i] = 1.0 / tau[i];
+        P.e0[i] = (w0 - 1.0) * P.eta[i] / tau[i];
+        P.aw[i][0] = w18 * P.eta[i] / tau[i];
+        P.aw[i][1] = w36 * P.eta[i] / tau[i];
+        P.kq[i] = 3.0 * w36 / tau[i];
+        P.sq[i] = 3.0 * w36 * (1.0 - 0.5 / tau[i]);
+    }
+    // uniform properties: the constants of the UNI update
+    P.rho0 = rho[0];
+    P.irho = 1.0 / rho[0];
+    P.hirho = 0.5 / rho[0];
+    P.prho = -0.25 * rho[0];
+    P.itg0 = 1.0 / (3.0 * nu[0] + 0.5);
+    P.omtg0 = 1.0 - P.itg0;
+    P.kG0 = 1.0 - 0.5 * P.itg0;
+    P.Kw0[0] = w18 * P.kG0;
+    P.Kw0[1] = w36 * P.kG0;
+    P.Rw0[0] = w18 * rho[0] * P.itg0;
+    P.Rw0[1] = w36 * rho[0] * P.itg0;
+    P.p3tg0 = 3.0 * P.itg0;
+    P.Gc[0] = rho[0] * p->gx;
+    P.Gc[1] = rho[0] * p->gy;
+    L->prm = P;
+    L->uni = rho[0] == rho[1] && rho[1] == rho[2] && nu[0] == nu[1] && nu[1] == nu[2];
     L->have_params = true;
     return tlb::clear_error();
 }
@@ -681,7 +918,7 @@ int tlb3_set_fields(tlb3_lattice* L, const double* c1, const double* c2, const d
     T3_CUDA(cudaMemcpyAsync(stage, c1, bytes, cudaMemcpyHostToDevice, L->stream));
     T3_CUDA(cudaMemcpyAsync(stage + N, c2, bytes, cudaMemcpyHostToDevice, L->stream));
     tlb3::k3_load_c<<<grid3(L), 128, 0, L->stream>>>(stage, L->cpl(), L->kind(), L->geo);
-    tlb3::k3_mu<<<grid3(L), 128, 0, L->stream>>>(L->cpl(), L->mpl(), L->kind(), L->geo, L->prm);
+    tlb3::k3_mu<<<grid3(L), 128, 0, L->stream>>>(L->cpl(), L->mpl(), L->lnk(), L->geo, L->prm);
     T3_CUDA(cudaGetLastError());
     // u, p after the c staging has been consumed (same stream)
     double* in = stage + 2 * N;
@@ -705,8 +942,12 @@ int tlb3_step(tlb3_lattice* L, int64_t n)
     if (!L->have_params || !L->have_fields) return err3(TLB_ESTATE, "set_params and set_fields first");
     for (int64_t s = 0; s < n; s++) {
         if ((rc = order_params3(L))) return rc;
-        tlb3::k3_update<<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->fspare(), L->cu(), L->cpl(), L->mpl(), L->kind(),
-                                                         L->geo, L->prm);
+        if (L->uni)
+            tlb3::k3_update<true><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->fspare(), L->cu(), L->cpl(), L->mpl(),
+                                                                   L->lnk(), L->geo, L->prm);
+        else
+            tlb3::k3_update<false><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->fspare(), L->cu(), L->cpl(), L->mpl(),
+                                                                    L->lnk(), L->geo, L->prm);
         T3_CUDA(cudaGetLastError());
         L->cur ^= 1;
     }
@@ -730,7 +971,10 @@ int tlb3_read_fields(tlb3_lattice* L, uint32_t mask, double* host_out)
     if ((rc = order_params3(L))) return rc;
     const size_t N = (size_t)L->n();
     double* stage = L->fspare();
-    tlb3::k3_read<<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cpl(), L->mpl(), L->kind(), stage, L->geo, L->prm);
+    if (L->uni)
+        tlb3::k3_read<true><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cpl(), L->mpl(), L->lnk(), stage, L->geo, L->prm);
+    else
+        tlb3::k3_read<false><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cpl(), L->mpl(), L->lnk(), stage, L->geo, L->prm);
     T3_CUDA(cudaGetLastError());
     size_t done = 0;
     for (int q = 0; q < 11; q++) {
