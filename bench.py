@@ -68,6 +68,10 @@ KERNEL = {"fp64": "k_step_interior<double>", "fp32": "k_step_interior<float>",
 # and viscosity (the tiled-drops workload); "general": any densities and
 # viscosities (the same lattice with rho_2 = 3).
 FP64_DP = {"uniform": (226.6, 332.1), "general": (290.1, 426.0)}
+# The same counts for the D3Q19 update kernel k3_update (ncu, 128x64x128
+# drops on a wetting wall, uniform properties: 174.0 DFMA + 131.0 DADD + 49.0
+# DMUL per node).
+FP64_DP3 = {"uniform": (354.0, 528.0)}
 # FP64 vector unit: 152 SMs x 2 DP instructions/clk x 2.07 GHz (an FMA is 2 flops)
 FP64_DP_INST_PEAK = 152 * 2 * 2.07e9
 FP64_PEAK_TFLOPS = 2 * FP64_DP_INST_PEAK / 1e12
@@ -483,7 +487,7 @@ def run_ours(args):
         if args.serve_count > 0:
             result["served"] = served(args, torch, T)
         if args.d3_steps > 0:
-            result["d3q19"] = d3q19(args, torch, T)
+            result["d3q19"] = d3q19(args, torch, T, fp64_peak)
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(result), flush=True)
@@ -657,11 +661,12 @@ def served(args, torch, T):
     return out
 
 
-def d3q19(args, torch, T):
+def d3q19(args, torch, T, fp64_peak=None):
     """The D3Q19 form (FP64): tiled hemispherical drops of fluids 1 and 2 on
     a wetting wall, periodic in x and z; whole steps (three launches each)
-    timed with CUDA events on the lattice's stream, and the c_1, c_2 mass
-    drift over the timed steps."""
+    timed with CUDA events on the lattice's stream, each launch timed apart
+    (tlb3_profile) for the roofline of the update kernel, which is bound by
+    the FP64 unit; and the c_1, c_2 mass drift over the timed steps."""
     import workloads as W
     nx, ny, nz = (int(v) for v in args.d3_size.split(","))
     w = W.drops3d_on_wall(nx, ny, nz)
@@ -678,11 +683,29 @@ def d3q19(args, torch, T):
     ev[1].synchronize()
     ms = ev[0].elapsed_time(ev[1])
     m1 = np.array(L.diagnostics()["mass"])
+    # the same number of steps again with each launch bracketed by events
+    L.profile(True)
+    L.step(args.d3_steps)
+    kms, kn = L.profile_read()
+    L.profile(False)
     n = nx * ny * nz
+    fluid = n  # drops3d_on_wall has no solid nodes (the wall is an edge)
     L.close()
+    upd_ms = kms[2] / max(kn[2], 1)
+    dp_inst, flops = FP64_DP3["uniform"]
+    ach = fluid * flops / (upd_ms / 1e3) / 1e12
+    peak, src = fp64_peak if fp64_peak else measured_fp64_peak(T)
     return {"workload": w.name, "nx": nx, "ny": ny, "nz": nz, "precision": "fp64", "steps": args.d3_steps,
             "value": round(n * args.d3_steps / (ms / 1e3) / 1e6, 2), "unit": "MLUPS",
             "ms_per_step": round(ms / args.d3_steps, 4),
+            "kernel_ms": {"k3_csum": round(kms[0] / max(kn[0], 1), 4), "k3_mu": round(kms[1] / max(kn[1], 1), 4),
+                          "k3_update": round(upd_ms, 4)},
+            "roofline": {"bound": "alu", "kernel": "k3_update<uniform>", "achieved": round(ach, 4),
+                         "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                         "peak_source": src, "dp_inst_per_node": dp_inst, "flops_per_node": flops,
+                         "dp_issue_frac": round(fluid * dp_inst / (upd_ms / 1e3) / FP64_DP_INST_PEAK, 4),
+                         "algorithmic_bytes_per_node": 2 * (57 + 6) * 8,
+                         "hbm_achieved_gbs": round(fluid * 2 * (57 + 6) * 8 / (upd_ms / 1e3) / 1e9, 1)},
             "gpu_launches": 3 * args.d3_steps,
             "mass_drift": [float(f"{v:.3g}") for v in np.abs(m1[:2] - m0[:2]) / np.abs(m0[:2])]}
 

@@ -368,6 +368,11 @@ int tlb3_sync(tlb3_lattice *lat);
 int tlb3_read_fields(tlb3_lattice *lat, uint32_t field_mask, double *host_out);
 int tlb3_read_state(tlb3_lattice *lat, double *host_out);
 int tlb3_diagnostics(tlb3_lattice *lat, tlb_diag *out);
+/* Per-kernel timing with CUDA events on the lattice's stream, as tlb_profile:
+ * ms[0..2] and launches[0..2] for the order-parameter, chemical-potential and
+ * update launches of the steps run since tlb3_profile(lat, 1). */
+int tlb3_profile(tlb3_lattice *lat, int enable);
+int tlb3_profile_read(tlb3_lattice *lat, double ms[3], int64_t launches[3]);
 void tlb3_destroy(tlb3_lattice *lat);
 
 /* Allocation-free variant of the tlb_diagnostics reduction.  The paper has

@@ -113,6 +113,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tlb3_read_fields": (i32, [vp, ctypes.c_uint32, dp]),
         "tlb3_read_state": (i32, [vp, dp]),
         "tlb3_diagnostics": (i32, [vp, ctypes.POINTER(Diag)]),
+        "tlb3_profile": (i32, [vp, i32]),
+        "tlb3_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "tlb3_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -474,6 +476,16 @@ class Lattice3D:
         out = np.empty((63,) + self.shape)
         _check(self.lib.tlb3_read_state(self._h, _dp(out)))
         return out
+
+    def profile(self, enable: bool = True):
+        _check(self.lib.tlb3_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """((csum_ms, mu_ms, update_ms), (launches...)) since profile(True)."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        _check(self.lib.tlb3_profile_read(self._h, ms, n))
+        return tuple(ms), tuple(n)
 
     def diagnostics(self):
         d = Diag()

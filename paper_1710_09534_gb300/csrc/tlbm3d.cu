@@ -229,12 +229,16 @@ __global__ void k3_mu(const double* __restrict__ cpl, double* __restrict__ mpl, 
             s1[p] = cpl[ap] + cpl[am];
             s2[p] = cpl[PL + ap] + cpl[PL + am];
         }
-        const double c3 = 1.0 - c1 - c2;
-        const double nw = (double)(int)((L >> LNK_NW) & 31u);
-        const double o1 = P.k4D * fma(P.cos13, c1 * c3, P.cos12 * (c1 * c2));
-        const double o2 = P.k4D * fma(-P.cos12, c1 * c2, P.cos23 * (c2 * c3));
-        const double l1 = fma(nw, o1, fma(-24.0, c1, W36_SUM(s1)));
-        const double l2 = fma(nw, o2, fma(-24.0, c2, W36_SUM(s2)));
+        double l1 = fma(-24.0, c1, W36_SUM(s1));
+        double l2 = fma(-24.0, c2, W36_SUM(s2));
+        const unsigned nwi = (L >> LNK_NW) & 31u;
+        if (nwi) {
+            const double c3 = 1.0 - c1 - c2, nw = (double)(int)nwi;
+            const double o1 = P.k4D * fma(P.cos13, c1 * c3, P.cos12 * (c1 * c2));
+            const double o2 = P.k4D * fma(-P.cos12, c1 * c2, P.cos23 * (c2 * c3));
+            l1 = fma(nw, o1, l1);
+            l2 = fma(nw, o2, l2);
+        }
         chem_pot(P, c1, c2, l1, l2, mu1, mu2);
     }
     mpl[o] = mu1;
@@ -704,6 +708,12 @@ struct tlb3_lattice {
     int cur = 0;
     bool have_params = false, have_fields = false, uni = false;
     std::vector<uint8_t> mask;
+    // per-kernel timing (tlb3_profile): 4 events per step around the three launches
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    double prof_ms[3] = {0, 0, 0};
+    int64_t prof_n[3] = {0, 0, 0};
 
     double* buf(int which) { return (double*)(ws + (which == 0 ? lay.fA : lay.fB)); }
     double* fcur() { return buf(cur); }
@@ -727,10 +737,39 @@ int check3(tlb3_lattice* L)
 
 dim3 grid3(const tlb3_lattice* L) { return dim3((unsigned)((L->n() + 127) / 128)); }
 
+constexpr int kProfSteps3 = 256;
+
+// Adds the recorded intervals to the totals (synchronizes on the last event).
+int prof_fold3(tlb3_lattice* L)
+{
+    if (L->ev_used == 0) return TLB_OK;
+    T3_CUDA(cudaEventSynchronize(L->ev[4 * (L->ev_used - 1) + 3]));
+    for (int u = 0; u < L->ev_used; u++)
+        for (int j = 0; j < 3; j++) {
+            float ms = 0.0f;
+            T3_CUDA(cudaEventElapsedTime(&ms, L->ev[4 * u + j], L->ev[4 * u + j + 1]));
+            L->prof_ms[j] += ms;
+            L->prof_n[j]++;
+        }
+    L->ev_used = 0;
+    return TLB_OK;
+}
+
+// event j (0..3) of the current profiled step
+int prof_mark3(tlb3_lattice* L, int j)
+{
+    if (!L->prof) return TLB_OK;
+    T3_CUDA(cudaEventRecord(L->ev[4 * L->ev_used + j], L->stream));
+    if (j == 3) L->ev_used++;
+    return TLB_OK;
+}
+
 // c and mu planes of the current state (the first two launches of a step)
 int order_params3(tlb3_lattice* L)
 {
     tlb3::k3_csum<<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cpl(), L->kind(), L->geo);
+    int rc = prof_mark3(L, 1);
+    if (rc) return rc;
     tlb3::k3_mu<<<grid3(L), 128, 0, L->stream>>>(L->cpl(), L->mpl(), L->lnk(), L->geo, L->prm);
     T3_CUDA(cudaGetLastError());
     return TLB_OK;
@@ -941,7 +980,10 @@ int tlb3_step(tlb3_lattice* L, int64_t n)
     if (n < 0) return err3(TLB_EINVAL, "negative step count");
     if (!L->have_params || !L->have_fields) return err3(TLB_ESTATE, "set_params and set_fields first");
     for (int64_t s = 0; s < n; s++) {
+        if (L->prof && L->ev_used == kProfSteps3 && (rc = prof_fold3(L))) return rc;
+        if ((rc = prof_mark3(L, 0))) return rc;
         if ((rc = order_params3(L))) return rc;
+        if ((rc = prof_mark3(L, 2))) return rc;
         if (L->uni)
             tlb3::k3_update<true><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->fspare(), L->cu(), L->cpl(), L->mpl(),
                                                                    L->lnk(), L->geo, L->prm);
@@ -949,7 +991,39 @@ int tlb3_step(tlb3_lattice* L, int64_t n)
             tlb3::k3_update<false><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->fspare(), L->cu(), L->cpl(), L->mpl(),
                                                                     L->lnk(), L->geo, L->prm);
         T3_CUDA(cudaGetLastError());
+        if ((rc = prof_mark3(L, 3))) return rc;
         L->cur ^= 1;
+    }
+    return tlb::clear_error();
+}
+
+int tlb3_profile(tlb3_lattice* L, int enable)
+{
+    int rc = check3(L);
+    if (rc) return rc;
+    if (enable && L->ev.empty()) {
+        L->ev.resize(4 * kProfSteps3);
+        for (auto& e : L->ev) T3_CUDA(cudaEventCreate(&e));
+    }
+    if (!enable && (rc = prof_fold3(L))) return rc;
+    L->prof = enable != 0;
+    for (int j = 0; j < 3; j++) {
+        L->prof_ms[j] = 0.0;
+        L->prof_n[j] = 0;
+    }
+    L->ev_used = 0;
+    return tlb::clear_error();
+}
+
+int tlb3_profile_read(tlb3_lattice* L, double ms[3], int64_t launches[3])
+{
+    int rc = check3(L);
+    if (rc) return rc;
+    if (!ms || !launches) return err3(TLB_EINVAL, "null output");
+    if ((rc = prof_fold3(L))) return rc;
+    for (int j = 0; j < 3; j++) {
+        ms[j] = L->prof_ms[j];
+        launches[j] = L->prof_n[j];
     }
     return tlb::clear_error();
 }
@@ -1035,6 +1109,7 @@ void tlb3_destroy(tlb3_lattice* L)
     if (!L) return;
     cudaSetDevice(L->device);
     cudaStreamSynchronize(L->stream);
+    for (auto e : L->ev) cudaEventDestroy(e);
     delete L;
 }
 
