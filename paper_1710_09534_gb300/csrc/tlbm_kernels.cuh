@@ -505,6 +505,19 @@ constexpr bool kPipeRows = TLB_PIPE32 != 0;
 #define TLB_PIPE16R 1
 #endif
 constexpr bool kPipeRows16 = TLB_PIPE16R != 0;
+// With the one-row-ahead loads, the g populations and c_i u of the next
+// iteration's update row are loaded one iteration ahead as well (as stored,
+// 13 registers): 16-bit storage, GB300, 2048^2, 5 blocks per SM: FP16 25.3 ->
+// 26.1, BF16 26.6 -> 27.2 G node updates/s.
+#ifndef TLB_PIPEG16
+#define TLB_PIPEG16 1
+#endif
+constexpr bool kPipeG16 = TLB_PIPEG16 != 0;
+// (FP32 storage, at 4 blocks per SM: 19.9 -> 19.4, so off there)
+#ifndef TLB_PIPEG32
+#define TLB_PIPEG32 0
+#endif
+constexpr bool kPipeG32 = TLB_PIPEG32 != 0;
 
 // One row of the order-parameter populations of a 16-bit buffer as loaded.
 struct Raw16Row {
@@ -598,6 +611,9 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
     };
     Raw16Row nq;
     if constexpr (PIPE16) load_raw_row(dir > 0 ? y0 - 2 : y1 + 1, nq);
+    constexpr bool PIPEG = ((PIPE16 && kPipeG16) || (PIPE && kPipeG32)) && PREFETCH;
+    typename std::conditional<Store<S>::k16, unsigned short, S>::type ngr[9];
+    CuT<S> ncp[4];
 
     for (int it = 0; it < iters; it++) {
         const int yc = dir > 0 ? y0 - 2 + it : y1 + 1 - it;  // c row of this iteration
@@ -636,7 +652,32 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
         const long long ou = in_rows ? (long long)yu * g.pitch + xs : 0;
         const bool upd = in_rows && (cls[ou] & CLS_INTERIOR) != 0;
         R gv[9], cp[4];
-        if (PREFETCH && in_rows) {
+        if constexpr (PIPEG) {
+            if constexpr (Store<S>::k16) {
+                constexpr float inv = SE != 0 ? 1.0f : 1.0f / float(1 << Store<S>::kScaleExp);
+#pragma unroll
+                for (int k = 0; k < 9; k++) gv[k] = R(dec16(S{}, ngr[k]) * inv);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 9; k++) gv[k] = R(ngr[k]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) cp[q] = R(ncp[q]);
+            // the next iteration's update row (yu + dir), if it has one
+            if (updater && it + 1 >= 4 && it + 1 < iters) {
+                const long long on = (long long)(yu + dir) * g.pitch + xs;
+                if constexpr (Store<S>::k16) {
+                    const unsigned short* gp = reinterpret_cast<const unsigned short*>(fA);
+#pragma unroll
+                    for (int k = 0; k < 9; k++) ngr[k] = __ldg(gp + idx16(18 + k, PL, on));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 9; k++) ngr[k] = __ldg(fA + (18 + k) * PL + on);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) ncp[q] = __ldg(&cu[q * PL + on]);
+            }
+        } else if (PREFETCH && in_rows) {
 #pragma unroll
             for (int k = 0; k < 9; k++) gv[k] = ld_pop<R, true, SE != 0>(fA, 18 + k, PL, ou);
 #pragma unroll
