@@ -549,6 +549,24 @@ def batched(args, torch, T):
     return out
 
 
+def cushion_gap(f, col, y_top):
+    """Thickness of the layer of fluid 3 between the cylinder top and the drop
+    on column `col`: distance from the half-way wall above solid row y_top to
+    the first crossing of c1 + c2 = 1/2 (linear interpolation); NaN if the
+    column holds no drop.  0 once the drop touches the wall (the film
+    thickness of `tlb_film_thickness` then measures the drop's own layer)."""
+    s = f["c1"][:, col] + f["c2"][:, col]
+    above = s[y_top + 1:]
+    if above[0] >= 0.5:
+        return 0.0
+    idx = np.nonzero(above >= 0.5)[0]
+    if not len(idx):
+        return float("nan")
+    j = int(idx[0])
+    t = (0.5 - above[j - 1]) / (above[j] - above[j - 1])
+    return float(j - 1 + t + 0.5)
+
+
 def impact(args, torch, T):
     """Compound drop falling onto a wetting cylinder at full size (1024 x 2048,
     R_cyl = 120, core R = 60, shell R = 100, fully periodic), for We = 1, 10,
@@ -556,8 +574,9 @@ def impact(args, torch, T):
     shifted-FP16 storage.  MLUPS of each; the FP32 and FP16 results' errors
     against the FP64 one (which equals the oracle to 1e-12): order-parameter
     max error, u and p max error relative to their scale, mass drift of fluids
-    1 and 2, and the film thickness on the cylinder top (0 before the drop
-    touches it).  Then an angle sweep (30..150 deg, We = 10, FP32 storage)
+    1 and 2, the film thickness on the cylinder top (0 before the drop
+    touches it) and the thickness of the fluid-3 cushion between drop and
+    cylinder top (`cushion_gap`).  Then an angle sweep (30..150 deg, We = 10, FP32 storage)
     timed over the same steps."""
     import workloads as W
     n0 = args.impact_steps
@@ -581,6 +600,7 @@ def impact(args, torch, T):
             ms = time_steps(L, n, torch, torch.cuda.current_stream())
             res[prec + "_mlups"] = round(w.nx * w.ny * n / (ms / 1e3) / 1e6, 1)
             fields[prec] = L.fields(("c1", "c2", "ux", "uy", "p"))
+            res[prec + "_gap"] = round(cushion_gap(fields[prec], col, y_top), 4)
             m1 = np.array(L.diagnostics()["mass"])
             res[prec + "_mass_drift"] = [float(f"{v:.3g}") for v in np.abs(m1[:2] - m0[:2]) / np.abs(m0[:2])]
             res[prec + "_film_h"] = round(L.film_thickness(col, y_top, 3), 6)
@@ -592,6 +612,7 @@ def impact(args, torch, T):
             for k in ("ux", "uy", "p"):
                 err[k + "_rel"] = float(np.abs(a[k] - ref[k]).max() / max(float(np.abs(ref[k]).max()), 1e-12))
             err["film_h_abs"] = abs(res[prec + "_film_h"] - res["fp64_film_h"])
+            err["gap_abs"] = abs(res[prec + "_gap"] - res["fp64_gap"])
             res[prec + "_vs_fp64"] = {k: float(f"{v:.3g}") for k, v in err.items()}
         out["We"][f"{We:g}"] = res
     sweep = {}

@@ -87,6 +87,21 @@ __global__ void k_csum(const S* __restrict__ f, R* __restrict__ cpl, const uint8
     cpl[PL + o] = c2;
 }
 
+// 16-bit storage: the whole read set of the next iteration's update node (8
+// pair words, 4 FP32 rest parts, 9 g values, 4 c_i u values) loaded one
+// iteration ahead, as stored, and decoded when consumed.  Safe in place: a
+// node's read set is written by that node's own update only.
+#ifndef TLB_PIPE_IP16
+#define TLB_PIPE_IP16 1
+#endif
+constexpr bool kPipeIp16 = TLB_PIPE_IP16 != 0;
+
+struct RawIpNode {
+    unsigned w[8];
+    float r[2], l[2], cu[4];
+    unsigned short gq[9];
+};
+
 // ---------------------------------------------------------------------------
 // Interior tile, in place: the marching scheme of interior_tile with c read
 // from the planes and the parity's addressing.  Interior nodes have no wall
@@ -115,6 +130,34 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
     // this column's c and mu histories (as in interior_tile)
     R ca[3] = {R(0), R(0), R(0)}, cb[3] = {R(0), R(0), R(0)};
     R ma[3] = {R(0), R(0), R(0)}, mb[3] = {R(0), R(0), R(0)};
+    constexpr bool PIP = kPipeIp16 && Store<S>::k16 && PREFETCH && !MRT;
+    RawIpNode nr;
+    // the read set of node (xs, yr) in this parity's layout, as stored
+    auto load_raw = [&](int yr) {
+        const long long o2 = (long long)yr * g.pitch + xs;
+        const PushOffsets p2(g, xs, yr);
+        const unsigned* wp = reinterpret_cast<const unsigned*>(f);
+        const unsigned short* hp = reinterpret_cast<const unsigned short*>(f);
+        const float* rp = rest_region(f, PL);
+        static_for<1, 9>([&](auto kc) {
+            constexpr int K = decltype(kc)::value;
+            constexpr int q = ODD ? opp(K) : K;
+            const long long sK = ODD ? p2.template dest<opp(K)>() : o2;
+            nr.w[K - 1] = ld_any<false>(wp + (long long)(q - 1) * PL + sK);
+        });
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            nr.r[i] = ld_any<false>(rp + i * PL + o2);
+            nr.l[i] = ld_any<false>(rp + (2 + i) * PL + o2);
+        }
+        static_for<0, 9>([&](auto kc) {
+            constexpr int K = decltype(kc)::value;
+            const long long sK = (ODD && K != 0) ? p2.template dest<opp(K)>() : o2;
+            nr.gq[K] = ld_any<false>(hp + idx16(18 + (ODD ? opp(K) : K), PL, sK));
+        });
+#pragma unroll
+        for (int q = 0; q < 4; q++) nr.cu[q] = float(cu[q * PL + o2]);
+    };
 
     for (int it = 0; it < iters; it++) {
         const int yc = dir > 0 ? y0 - 2 + it : y1 + 1 - it;
@@ -159,7 +202,27 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
         auto load_all_f = [&]() {
             static_for<0, 9>([&](auto kc) { load_f(kc, f1[decltype(kc)::value], f2[decltype(kc)::value]); });
         };
-        if (PREFETCH && in_rows) {
+        R pl[2] = {R(0), R(0)};
+        if constexpr (PIP) {
+            if constexpr (Store<S>::k16) {
+                // decode this iteration's read set, then issue the next one's
+                constexpr float inv = 1.0f / float(1 << Store<S>::kScaleExp);
+#pragma unroll
+                for (int k = 1; k < 9; k++) {
+                    f1[k] = R(dec16(S{}, (unsigned short)(nr.w[k - 1] & 0xffffu)) * inv);
+                    f2[k] = R(dec16(S{}, (unsigned short)(nr.w[k - 1] >> 16)) * inv);
+                }
+                f1[0] = R(nr.r[0]);
+                f2[0] = R(nr.r[1]);
+                pl[0] = R(nr.l[0]);
+                pl[1] = R(nr.l[1]);
+#pragma unroll
+                for (int k = 0; k < 9; k++) gv[k] = R(dec16(S{}, nr.gq[k]) * inv);
+#pragma unroll
+                for (int q = 0; q < 4; q++) cp[q] = R(nr.cu[q]);
+                if (updater && it + 1 >= 4 && it + 1 < iters) load_raw(yu + dir);
+            }
+        } else if (PREFETCH && in_rows) {
             load_g();
             if constexpr (kPre) load_all_f();
         }
@@ -256,8 +319,13 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
                 }
             },
             [&](R& l1, R& l2) {
-                l1 = ld_lo<R, false>(f, 0, PL, ou);
-                l2 = ld_lo<R, false>(f, 1, PL, ou);
+                if constexpr (PIP) {
+                    l1 = pl[0];
+                    l2 = pl[1];
+                } else {
+                    l1 = ld_lo<R, false>(f, 0, PL, ou);
+                    l2 = ld_lo<R, false>(f, 1, PL, ou);
+                }
             },
             [&](auto kc, auto o1, auto o2, auto og) {
                 constexpr int K = decltype(kc)::value;

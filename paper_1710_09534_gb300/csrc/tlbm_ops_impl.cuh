@@ -246,8 +246,16 @@ struct OpsImpl {
 #ifndef TLB_IP_MINB_ODD
 #define TLB_IP_MINB_ODD 5
 #endif
-    static constexpr int kMinBIpEven = std::is_same<R, float>::value ? TLB_IP_MINB_EVEN : MINB;
-    static constexpr int kMinBIpOdd = std::is_same<R, float>::value ? TLB_IP_MINB_ODD : MINB;
+    // 16-bit storage with the whole next read set loaded one iteration ahead
+    // (TLB_PIPE_IP16) runs at 4 blocks (GB300, 2048^2: 16.3 -> 17.2 G node
+    // updates/s; at 5 blocks it spills and gains 1%)
+#ifndef TLB_IP_MINB16
+#define TLB_IP_MINB16 4
+#endif
+    static constexpr int kMinBIpEven =
+        Store<S>::k16 && kPipeIp16 ? TLB_IP_MINB16 : (std::is_same<R, float>::value ? TLB_IP_MINB_EVEN : MINB);
+    static constexpr int kMinBIpOdd =
+        Store<S>::k16 && kPipeIp16 ? TLB_IP_MINB16 : (std::is_same<R, float>::value ? TLB_IP_MINB_ODD : MINB);
     template <bool UNI, bool ODD>
     static void launch_interior_ip(void* f, void* cu, const void* cpl, const uint8_t* cls, const Geo& g,
                                    const Prm<R>& P, cudaStream_t s)

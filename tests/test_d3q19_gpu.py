@@ -47,6 +47,19 @@ def test_random_lattices_fp64(T, shape, seed, edges, solids):
         assert_oracle_parity3(L, O, w.params, what=f"{w.name} after {n}")
 
 
+@pytest.mark.parametrize("seed,edges", [(11, (0, 0, 1, 2, 1, 1)), (12, (2, 2, 0, 0, 1, 2))])
+def test_uniform_property_update_with_solids_and_body_force(T, seed, edges):
+    """Equal densities and viscosities select the update without grad rho,
+    F_a and lap mu; walls on several faces, a sphere, a corner, gx and gy."""
+    w = W.random_lattice3(19, 15, 13, seed, edges=edges, solids=("sphere", "corner"))
+    w.params.update(rho1=1.0, rho2=1.0, rho3=1.0, nu1=0.1, nu2=0.1, nu3=0.1, gx=3e-6, gy=-2e-6)
+    L, O = pair(T, w)
+    for n in (1, 40):
+        L.step(n)
+        O.step(n)
+        assert_oracle_parity3(L, O, w.params, what=f"{w.name} uniform after {n}")
+
+
 def test_drops_on_a_wetting_wall_300_steps(T):
     w = W.drops3d_on_wall(48, 24, 40, R=10.0)
     L, O = pair(T, w)
