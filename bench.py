@@ -67,7 +67,7 @@ KERNEL = {"fp64": "k_step_interior<double>", "fp32": "k_step_interior<float>",
 # FMA as 2).  "uniform": the update taken when all three fluids share density
 # and viscosity (the tiled-drops workload); "general": any densities and
 # viscosities (the same lattice with rho_2 = 3).
-FP64_DP = {"uniform": (226.6, 332.1), "general": (290.1, 426.0)}
+FP64_DP = {"uniform": (219.9, 323.9), "general": (290.1, 426.0)}
 # The same counts for the D3Q19 update kernel k3_update (ncu, 128x64x128
 # drops on a wetting wall, uniform properties: 174.0 DFMA + 131.0 DADD + 49.0
 # DMUL per node).

@@ -196,17 +196,19 @@ int step_launches(tlb_lattice* L, Pre pre, Interior interior, Wall wall, Post po
     }
     TLB_CUDA(pre());
     const bool two = L->nlist > 0;
+    // the near-wall launch goes first, so that its few blocks are resident
+    // before the interior grid takes the SMs
     if (two) {
         TLB_CUDA(cudaEventRecord(L->fork, L->stream));
         TLB_CUDA(cudaStreamWaitEvent(L->side, L->fork, 0));
-    }
-    TLB_CUDA(interior());
-    if (ev) TLB_CUDA(cudaEventRecord(ev[1], L->stream));
-    if (two) {
         if (ev) TLB_CUDA(cudaEventRecord(ev[2], L->side));
         TLB_CUDA(wall(L->side));
         if (ev) TLB_CUDA(cudaEventRecord(ev[3], L->side));
         TLB_CUDA(cudaEventRecord(L->join, L->side));
+    }
+    TLB_CUDA(interior());
+    if (ev) TLB_CUDA(cudaEventRecord(ev[1], L->stream));
+    if (two) {
         TLB_CUDA(cudaStreamWaitEvent(L->stream, L->join, 0));
     } else if (ev) {
         TLB_CUDA(cudaEventRecord(ev[2], L->stream));

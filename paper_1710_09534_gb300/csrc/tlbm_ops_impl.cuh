@@ -93,11 +93,14 @@ inline int sm_count()
 #ifndef TLB_ADAPTIVE_ROWS
 #define TLB_ADAPTIVE_ROWS 1
 #endif
-// one_wave (the two-buffer interior kernel): a lattice large enough for more
-// than one wave of blocks gets segments long enough that the whole grid is
-// resident at once (fewer halo rows per updated row, no partial last wave):
-// GB300, 2048^2, interior kernel FP64 1.929 -> 1.911 ms, FP32 0.208 -> 0.202
-// ms; the in-place kernels measured slower with it.
+// one_wave (the FP64 two-buffer interior kernel): a lattice large enough for
+// more than one wave of blocks gets segments long enough that the whole grid
+// is resident at once, so that the halo rows' c sums and chemical potentials
+// (FP64 arithmetic, the kernel's bound) are repeated on fewer rows.  GB300:
+// FP64 2048^2 interior kernel 1.929 -> 1.911 ms, 1024x2048 cylinder impact
+// within +-3%.  FP32 and 16-bit storage (latency-bound) lose the dynamic
+// balancing of several waves: the cylinder impact ran 12% (FP32) and 10%
+// (FP16) slower, so they keep short segments; the in-place kernels too.
 #ifndef TLB_ONE_WAVE
 #define TLB_ONE_WAVE 1
 #endif
@@ -123,7 +126,7 @@ struct OpsImpl {
     {
         const Prm<R> P = cast_prm<R>(Pd);
         constexpr int TX = BLOCK - 4;
-        const int rows = rows_for(g, TX, ROWS, MINB, true);
+        const int rows = rows_for(g, TX, ROWS, MINB, std::is_same<R, double>::value);
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
         // equal densities and viscosities: the uniform-property update
         if (Pd.uni != 0.0)
