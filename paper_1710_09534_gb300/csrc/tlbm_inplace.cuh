@@ -209,8 +209,9 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
                 constexpr float inv = 1.0f / float(1 << Store<S>::kScaleExp);
 #pragma unroll
                 for (int k = 1; k < 9; k++) {
-                    f1[k] = R(dec16(S{}, (unsigned short)(nr.w[k - 1] & 0xffffu)) * inv);
-                    f2[k] = R(dec16(S{}, (unsigned short)(nr.w[k - 1] >> 16)) * inv);
+                    const float2 v = dec16x2(S{}, nr.w[k - 1]);
+                    f1[k] = R(v.x * inv);
+                    f2[k] = R(v.y * inv);
                 }
                 f1[0] = R(nr.r[0]);
                 f2[0] = R(nr.r[1]);

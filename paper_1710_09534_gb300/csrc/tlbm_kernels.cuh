@@ -89,6 +89,35 @@ __device__ __forceinline__ unsigned short enc16(__nv_bfloat16, float v)
 {
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
+// A 32-bit pair word (low half, high half) decoded to two floats, and two
+// floats encoded into one, by the packed conversions (one rounding per value,
+// the same as enc16 of each).
+__device__ __forceinline__ float2 dec16x2(__half, unsigned w)
+{
+    __half2 h;
+    memcpy(&h, &w, sizeof w);
+    return __half22float2(h);
+}
+__device__ __forceinline__ float2 dec16x2(__nv_bfloat16, unsigned w)
+{
+    __nv_bfloat162 h;
+    memcpy(&h, &w, sizeof w);
+    return __bfloat1622float2(h);
+}
+__device__ __forceinline__ unsigned enc16x2(__half, float lo, float hi)
+{
+    const __half2 h = __floats2half2_rn(lo, hi);
+    unsigned w;
+    memcpy(&w, &h, sizeof w);
+    return w;
+}
+__device__ __forceinline__ unsigned enc16x2(__nv_bfloat16, float lo, float hi)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    unsigned w;
+    memcpy(&w, &h, sizeof w);
+    return w;
+}
 
 // FP32 region of a 16-bit buffer (after the 16 + 9 16-bit planes)
 template <typename S>
@@ -141,6 +170,11 @@ __device__ __forceinline__ R ld_pop(const S* __restrict__ f, int q, long long PL
 struct Bits16 {
     unsigned short b;
 };
+// f^1_k (low half) and f^2_k (high half) of a node already encoded into the
+// 32-bit word of a 16-bit buffer.
+struct Pair16 {
+    unsigned w;
+};
 // lo part of rest population i (0: f^1_0, 1: f^2_0); zero for FP64
 template <typename R, bool NC = true, typename S>
 __device__ __forceinline__ R ld_lo(const S* __restrict__ f, int i, long long PL, long long o)
@@ -192,8 +226,9 @@ __device__ __forceinline__ void ld_pair(const S* __restrict__ f, int k, long lon
     if constexpr (Store<S>::k16) {
         const unsigned w = ld_any<NC>(reinterpret_cast<const unsigned*>(f) + (long long)(k - 1) * PL + o);
         constexpr float inv = RAW ? 1.0f : 1.0f / float(1 << Store<S>::kScaleExp);
-        f1k = R(dec16(S{}, (unsigned short)(w & 0xffffu)) * inv);
-        f2k = R(dec16(S{}, (unsigned short)(w >> 16)) * inv);
+        const float2 v = dec16x2(S{}, w);
+        f1k = R(v.x * inv);
+        f2k = R(v.y * inv);
     } else {
         f1k = ld_pop<R, NC>(f, k, PL, o);
         f2k = ld_pop<R, NC>(f, 9 + k, PL, o);
@@ -205,16 +240,22 @@ __device__ __forceinline__ void ld_pair(const S* __restrict__ f, int k, long lon
 template <typename S, typename V1, typename V2, typename VG>
 __device__ __forceinline__ void st_three(S* __restrict__ f, int k, long long PL, long long d, V1 o1, V2 o2, VG og)
 {
-    if constexpr (Store<S>::k16 && std::is_same<V1, Bits16>::value && std::is_same<V2, Bits16>::value) {
-        if (k != 0) {
-            reinterpret_cast<unsigned*>(f)[(long long)(k - 1) * PL + d] = (unsigned)o1.b | ((unsigned)o2.b << 16);
-            st_pop(f, 18 + k, PL, d, og);
-            return;
+    if constexpr (std::is_same<V1, Pair16>::value) {
+        static_assert(Store<S>::k16 && std::is_same<V2, Pair16>::value, "a pair word goes to a 16-bit buffer");
+        reinterpret_cast<unsigned*>(f)[(long long)(k - 1) * PL + d] = o1.w;  // k != 0: rest values are not pairs
+        st_pop(f, 18 + k, PL, d, og);
+    } else {
+        if constexpr (Store<S>::k16 && std::is_same<V1, Bits16>::value && std::is_same<V2, Bits16>::value) {
+            if (k != 0) {
+                reinterpret_cast<unsigned*>(f)[(long long)(k - 1) * PL + d] = (unsigned)o1.b | ((unsigned)o2.b << 16);
+                st_pop(f, 18 + k, PL, d, og);
+                return;
+            }
         }
+        st_pop(f, k, PL, d, o1);
+        st_pop(f, 9 + k, PL, d, o2);
+        st_pop(f, 18 + k, PL, d, og);
     }
-    st_pop(f, k, PL, d, o1);
-    st_pop(f, 9 + k, PL, d, o2);
-    st_pop(f, 18 + k, PL, d, og);
 }
 
 // c_i = sum_k f^i_k of node o for i = 1, 2 (rest population hi + lo)
@@ -277,21 +318,13 @@ __device__ __forceinline__ void collide_all(const Collider<R, UNI>& col, const R
     constexpr bool ff = Store<S>::kLo;
     constexpr bool k16 = Store<S>::k16;
     static_assert(SE == 0 || (k16 && SE == Store<S>::kScaleExp), "scaled units are those of FP16 storage");
-    // encode a value for 16-bit storage and decode it back (in the units of the values)
+    // encode a value for 16-bit storage (in the units of the values)
     auto enc = [](R v) -> Bits16 {
         if constexpr (k16) {
             constexpr float sc = SE ? 1.0f : float(1 << Store<S>::kScaleExp);
             return Bits16{enc16(S{}, float(v) * sc)};
         } else {
             return Bits16{0};
-        }
-    };
-    auto dec = [](Bits16 h) -> R {
-        if constexpr (k16) {
-            constexpr float inv = SE ? 1.0f : 1.0f / float(1 << Store<S>::kScaleExp);
-            return R(dec16(S{}, h.b) * inv);
-        } else {
-            return R(0);
         }
     };
     R d1 = R(0), d2 = R(0);  // sum_k (f_k - o'_k) over the moving directions
@@ -308,11 +341,16 @@ __device__ __forceinline__ void collide_all(const Collider<R, UNI>& col, const R
         load(kbc, b1, b2);
         col.template pair<K>(a1, a2, gv[K], b1, b2, gv[KB], oa1, oa2, oag, ob1, ob2, obg);
         if constexpr (k16) {
-            const Bits16 ha1 = enc(oa1), ha2 = enc(oa2), hb1 = enc(ob1), hb2 = enc(ob2);
-            d1 += (a1 - dec(ha1)) + (b1 - dec(hb1));
-            d2 += (a2 - dec(ha2)) + (b2 - dec(hb2));
-            store(kc, ha1, ha2, enc(oag));
-            store(kbc, hb1, hb2, enc(obg));
+            // f^1_k, f^2_k of each direction encoded into their pair word at once
+            constexpr float sc = SE ? 1.0f : float(1 << Store<S>::kScaleExp);
+            constexpr float inv = SE ? 1.0f : 1.0f / float(1 << Store<S>::kScaleExp);
+            const Pair16 pa{enc16x2(S{}, float(oa1) * sc, float(oa2) * sc)};
+            const Pair16 pb{enc16x2(S{}, float(ob1) * sc, float(ob2) * sc)};
+            const float2 da = dec16x2(S{}, pa.w), db = dec16x2(S{}, pb.w);
+            d1 += (a1 - R(da.x * inv)) + (b1 - R(db.x * inv));
+            d2 += (a2 - R(da.y * inv)) + (b2 - R(db.y * inv));
+            store(kc, pa, pa, enc(oag));
+            store(kbc, pb, pb, enc(obg));
         } else {
             if constexpr (ff) {
                 d1 += (a1 - oa1) + (b1 - ob1);
@@ -635,8 +673,9 @@ __device__ __forceinline__ void interior_tile(const S* __restrict__ fA, S* __res
                 cv[9] = R(nq.r[1]);
 #pragma unroll
                 for (int k = 1; k < 9; k++) {
-                    cv[k] = R(dec16(S{}, (unsigned short)(nq.w[k - 1] & 0xffffu)) * inv);
-                    cv[9 + k] = R(dec16(S{}, (unsigned short)(nq.w[k - 1] >> 16)) * inv);
+                    const float2 v = dec16x2(S{}, nq.w[k - 1]);
+                    cv[k] = R(v.x * inv);
+                    cv[9 + k] = R(v.y * inv);
                 }
                 cl[0] = R(nq.l[0]);
                 cl[1] = R(nq.l[1]);
@@ -999,7 +1038,7 @@ __device__ __forceinline__ void push_wall(const Geo& g, const uint8_t* __restric
                                           int x, int y, long long o, V1 o1, V2 o2, VG og)
 {
     const long long PL = g.plane;
-    if (K == 0) {
+    if constexpr (K == 0) {
         st_pop(fB, 0, PL, o, o1);
         st_pop(fB, 9, PL, o, o2);
         st_pop(fB, 18, PL, o, og);
