@@ -421,8 +421,17 @@ __device__ __forceinline__ void pair3(const Coll3& C, const double* __restrict__
 // One BGK time step of every fluid node: collision (Eqs. 1a, 1b, 2a, 2b, 4,
 // 11a, 11b, 19) and the push to x + e_k.  UNI: equal densities and
 // viscosities (grad rho = 0, F_a = 0, tau_g constant).
+// resident blocks per SM the update is compiled for: the uniform-property
+// update at 3 (168 registers, 16 bytes spilled; GB300, 192x96x192: 2.447 ->
+// 2.348 ms per launch; 2.344 at 4); the general update gains nothing at 2 or 3
+#ifndef TLB3_MINB
+#define TLB3_MINB 3
+#endif
+#ifndef TLB3_MINB_GEN
+#define TLB3_MINB_GEN 1
+#endif
 template <bool UNI>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, UNI ? TLB3_MINB : TLB3_MINB_GEN)
 k3_update(const double* __restrict__ fA, double* __restrict__ fB, double* __restrict__ cu,
           const double* __restrict__ cpl, const double* __restrict__ mpl, const uint32_t* __restrict__ lnk, Geo3 g,
           Prm3 P)

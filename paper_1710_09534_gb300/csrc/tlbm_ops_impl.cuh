@@ -119,22 +119,34 @@ inline int rows_for(const Geo& g, int tx, int rows, int per_sm, bool one_wave = 
     return rows;
 }
 
+// Resident blocks per SM of the FP64 BGK uniform-property interior kernel,
+// which needs fewer registers than the general one: at 4 (128 registers, no
+// spills) it measured slower than at 3 (GB300, 2048^2: 1.913 -> 1.947 ms).
+#ifndef TLB_MINB64_UNI
+#define TLB_MINB64_UNI 3
+#endif
+
 template <typename S, typename R, int BLOCK, int ROWS, bool PREFETCH, int MINB, bool MRT>
 struct OpsImpl {
+    static constexpr int kMinBUni = std::is_same<R, double>::value && !MRT ? TLB_MINB64_UNI : MINB;
     static cudaError_t interior(const void* fA, void* fB, void* cu, const uint8_t* cls, const Geo& g,
                                 const Prm<double>& Pd, cudaStream_t s)
     {
         const Prm<R> P = cast_prm<R>(Pd);
         constexpr int TX = BLOCK - 4;
-        const int rows = rows_for(g, TX, ROWS, MINB, std::is_same<R, double>::value);
-        dim3 grid((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
+        constexpr bool kOneWave = std::is_same<R, double>::value;
         // equal densities and viscosities: the uniform-property update
-        if (Pd.uni != 0.0)
-            k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT, true><<<grid, BLOCK, 0, s>>>(
+        if (Pd.uni != 0.0) {
+            const int rows = rows_for(g, TX, ROWS, kMinBUni, kOneWave);
+            dim3 grid((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
+            k_step_interior<S, R, BLOCK, ROWS, PREFETCH, kMinBUni, MRT, true><<<grid, BLOCK, 0, s>>>(
                 (const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P, rows);
-        else
+        } else {
+            const int rows = rows_for(g, TX, ROWS, MINB, kOneWave);
+            dim3 grid((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
             k_step_interior<S, R, BLOCK, ROWS, PREFETCH, MINB, MRT, false><<<grid, BLOCK, 0, s>>>(
                 (const S*)fA, (S*)fB, (CuT<S>*)cu, cls, g, P, rows);
+        }
         return cudaGetLastError();
     }
     static cudaError_t wall(const void* fA, void* fB, void* cu, const uint8_t* cls, const uint32_t* list,

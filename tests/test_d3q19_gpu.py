@@ -68,6 +68,17 @@ def test_drops_on_a_wetting_wall_300_steps(T):
     assert_oracle_parity3(L, O, w.params, what=w.name)
 
 
+def test_drops_1000_steps_with_density_contrast(T):
+    """1000 steps of a small drops-on-wall lattice with fluid 2 three times as
+    dense and the viscosities apart (the general update), against the oracle."""
+    w = W.drops3d_on_wall(40, 20, 40, R=8.0)
+    w.params.update(rho2=3.0, nu1=0.08, nu2=0.12, nu3=0.1, gy=-1e-6)
+    L, O = pair(T, w)
+    L.step(1000)
+    O.step(1000)
+    assert_oracle_parity3(L, O, w.params, what=f"{w.name} general, 1000 steps")
+
+
 def test_zero_steps_and_smallest_lattices(T):
     for shape, edges in (((3, 3, 3), (0,) * 6), ((4, 5, 3), (1, 2, 0, 0, 2, 2)), ((3, 4, 6), (0, 0, 1, 2, 0, 0))):
         w = W.random_lattice3(*shape, 7, edges=edges, solids=())
