@@ -264,6 +264,21 @@ def oracle_run(w, steps, warmup=0):
     return w.nx * w.ny * steps / dt / 1e6, dt, oracle.threads()
 
 
+def cpu_model():
+    """The host CPU as lscpu names it (machine type if lscpu is missing)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return f"{name} ({platform.machine()})"
+    except Exception:
+        pass
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(w, budget_s=12.0, single_s=5.0):
     """The oracle on a bounded sample (~budget_s seconds of host work on all
     cores), and the same sample on one core (~single_s seconds) beside it."""
@@ -273,6 +288,7 @@ def cpu_baseline(w, budget_s=12.0, single_s=5.0):
     steps = max(1, min(5000, int(budget_s / max(t1 / 2, 1e-3))))
     mlups, dt, thr = oracle_run(s, steps)
     out = {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
+           "cpu": cpu_model(), "nproc": os.cpu_count(),
            "sample": f"{s.nx}x{s.ny} bottom strip of the {w.nx}x{w.ny} lattice, {steps} steps, "
                      f"{dt:.1f} s, FP64 C oracle with OpenMP over nodes"}
     oracle.set_threads(1)
@@ -317,7 +333,8 @@ def run_reference(args):
                        "storage": "f64", "parallelism": "host cores (OpenMP)",
                        "sample": f"bottom {w.ny} rows ({w.nx}x{w.ny}) per step"},
             "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": oracle.threads(),
-                             "kind": "oracle", "sample": f"{w.name}, {args.steps} steps per run"},
+                             "kind": "oracle", "cpu": cpu_model(), "nproc": os.cpu_count(),
+                             "sample": f"{w.name}, {args.steps} steps per run"},
             "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -590,8 +607,9 @@ def impact(args, torch, T):
         contact = int(48.0 / w.meta["U"])  # steps until the falling shell reaches the cylinder top
         n = max(n0, contact + 1500) if contact + 1500 <= args.impact_max_steps else n0
         fields = {}
+        fluid = float((w.mask == 0).sum()) / (w.nx * w.ny)
         res = {"U": round(w.meta["U"], 5), "Re": round(w.meta["Re"], 1), "steps": n,
-               "contact_step_estimate": contact}
+               "contact_step_estimate": contact, "fluid_fraction": round(fluid, 5)}
         for prec in ("fp64", "fp32", "fp16"):
             L = T.lattice_from_workload(w, prec)
             m0 = np.array(L.diagnostics()["mass"])
@@ -599,6 +617,7 @@ def impact(args, torch, T):
             L.sync()
             ms = time_steps(L, n, torch, torch.cuda.current_stream())
             res[prec + "_mlups"] = round(w.nx * w.ny * n / (ms / 1e3) / 1e6, 1)
+            res[prec + "_fluid_mlups"] = round(fluid * w.nx * w.ny * n / (ms / 1e3) / 1e6, 1)
             fields[prec] = L.fields(("c1", "c2", "ux", "uy", "p"))
             res[prec + "_gap"] = round(cushion_gap(fields[prec], col, y_top), 4)
             m1 = np.array(L.diagnostics()["mass"])
