@@ -24,8 +24,12 @@ def nvcc() -> str:
     return "nvcc"
 
 
+# -fmad=false: no multiply-add is contracted behind the source's back (every
+# fused multiply-add is an explicit fma), so the kernels that share the update
+# code (single lattices, batch members, in place) round identically and give
+# bit-identical results for the same lattice.
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
 
 

@@ -393,18 +393,31 @@ __device__ __forceinline__ void pair3(const Coll3& C, const double* __restrict__
 {
     constexpr int kp = 2 * p + 1, km = 2 * p + 2, c = p < 3 ? 0 : 1;
     const double beta = edot<p>(C.b3);
-    const double V1 = wdot<p>(C.Q1), V2 = wdot<p>(C.Q2);
     const double KX = wdot<p>(C.Hs);
+    // A_i +- V_i with V_i = 36 w_k e_k.Q'_i (on the axis pairs one fma each)
+    double s1p, s1m, s2p, s2m;
+    if constexpr (p < 3) {
+        s1p = fma(2.0, C.Q1[p], C.A1[c]);
+        s1m = fma(-2.0, C.Q1[p], C.A1[c]);
+        s2p = fma(2.0, C.Q2[p], C.A2[c]);
+        s2m = fma(-2.0, C.Q2[p], C.A2[c]);
+    } else {
+        const double V1 = edot<p>(C.Q1), V2 = edot<p>(C.Q2);
+        s1p = C.A1[c] + V1;
+        s1m = C.A1[c] - V1;
+        s2p = C.A2[c] + V2;
+        s2m = C.A2[c] - V2;
+    }
     double AX;
     if constexpr (UNI) AX = KX;
     else AX = fma(p < 3 ? 2.0 * C.wa36 : C.wa36, beta, wdot<p>(C.Ts));
     const double a = fma(beta, 0.5 * beta, C.t0);
     const double sym = fma(beta, KX, fma(a, C.RX[c], C.PX[c]));
     const double anti = fma(a, KX, fma(beta, C.RX[c], AX));
-    const double o1p = fma(C.omt1, fA[kp * PL + o], C.A1[c] + V1);
-    const double o1m = fma(C.omt1, fA[km * PL + o], C.A1[c] - V1);
-    const double o2p = fma(C.omt2, fA[(Q + kp) * PL + o], C.A2[c] + V2);
-    const double o2m = fma(C.omt2, fA[(Q + km) * PL + o], C.A2[c] - V2);
+    const double o1p = fma(C.omt1, fA[kp * PL + o], s1p);
+    const double o1m = fma(C.omt1, fA[km * PL + o], s1m);
+    const double o2p = fma(C.omt2, fA[(Q + kp) * PL + o], s2p);
+    const double o2m = fma(C.omt2, fA[(Q + km) * PL + o], s2m);
     const double ogp = fma(C.omtg, n.g[kp], sym + anti);
     const double ogm = fma(C.omtg, n.g[km], sym - anti);
     // push to x + e_k, or back into slot k-bar of this node (Eq. 44)

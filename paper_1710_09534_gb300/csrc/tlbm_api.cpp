@@ -435,6 +435,9 @@ int tlb_set_params(tlb_lattice* L, const tlb_params* p)
         P.drho12[i] = P.drho[i] / 12.0;
         P.aM6[i] = P.aM[i] / 6.0;
         P.k3tau[i] = 3.0 / tau[i];
+        P.kq[i] = 3.0 / 36.0 / tau[i];
+        P.ks[i] = P.src_f[i] / 36.0;
+        P.K3w3[i] = 3.0 * P.Kw3[i];
     }
     P.Kt = P.k12D * P.two_lamT;
     // mu_1 - mu_3 = (1 + l3/l1) mu_1 + (l3/l2) mu_2, mu_2 - mu_3 = (l3/l1) mu_1 + (1 + l3/l2) mu_2

@@ -82,6 +82,8 @@ struct Prm {
     R drho12[2];      // (rho_i - rho_3) / 12
     R aM6[2];         // (rho_i - rho_3) M_i / 6
     R k3tau[2];       // 3 / tau_i
+    R kq[2], ks[2];   // 3 w36 / tau_i, w36 src_f_i (the order-parameter sources per w36)
+    R K3w3[2];        // 3 Kw3 (uniform properties: K_w T = K3w3 (F_s + G))
 };
 
 // Site of (x, y), possibly outside the lattice; on an inside site sets the
@@ -257,10 +259,13 @@ __device__ __forceinline__ void hydro_from_g(const Prm<R>& P, const Macro<R>& m,
 //   AX = Kw e.T + 3 w a_F e.u   (= KX with equal densities, where H = T).
 // Every term is small (of the size of the populations themselves): the O(1)
 // parts of Rw and of (q + 1) never meet in a difference.
+// V_i is formed per pair from Q'_i = w36 Q_i: 4 Q'_x or 4 Q'_y on the axis
+// links (w_axis = 4 w36, folded into one fma with A_i), Q'_x +- Q'_y on the
+// diagonal ones.
 template <typename R, bool UNI = false>
 struct Collider {
     R A1[2], A2[2];     // per class (0 axis, 1 diagonal)
-    R V1[4], V2[4];     // per component: +x, +y, (1,1), (1,-1)
+    R Q1[2], Q2[2];     // w36 Q_i (x, y)
     R E1, E2;           // f^{i,eq}_0 / tau_i
     R b[4];             // beta = 3 e.u per component
     R t0;               // -1.5 u.u
@@ -285,17 +290,12 @@ struct Collider {
             A1[c] = P.aw[0][c] * m.mu1;
             A2[c] = P.aw[1][c] * m.mu2;
         }
-        const R k1 = P.k3tau[0] * m.c1, k2 = P.k3tau[1] * m.c2;
-        const R Q1x = fma(k1, h.ux, P.src_f[0] * d1x), Q1y = fma(k1, h.uy, P.src_f[0] * d1y);
-        const R Q2x = fma(k2, h.ux, P.src_f[1] * d2x), Q2y = fma(k2, h.uy, P.src_f[1] * d2y);
-        V1[0] = w9 * Q1x;
-        V1[1] = w9 * Q1y;
-        V1[2] = w36 * (Q1x + Q1y);
-        V1[3] = w36 * (Q1x - Q1y);
-        V2[0] = w9 * Q2x;
-        V2[1] = w9 * Q2y;
-        V2[2] = w36 * (Q2x + Q2y);
-        V2[3] = w36 * (Q2x - Q2y);
+        // w36 Q_i = (3 w36 / tau_i) c_i u + w36 src_f_i d(c_i u); the products
+        // c_i u are the ones the caller stores for Eq. 19
+        Q1[0] = fma(P.kq[0], m.c1 * h.ux, P.ks[0] * d1x);
+        Q1[1] = fma(P.kq[0], m.c1 * h.uy, P.ks[0] * d1y);
+        Q2[0] = fma(P.kq[1], m.c2 * h.ux, P.ks[1] * d2x);
+        Q2[1] = fma(P.kq[1], m.c2 * h.uy, P.ks[1] * d2y);
         // hydrodynamics
         b[0] = R(3) * h.ux;
         b[1] = R(3) * h.uy;
@@ -303,29 +303,32 @@ struct Collider {
         b[3] = b[0] - b[1];
         t0 = R(-1.5) * h.usq;
         const R itg = h.inv_taug;
-        const R Tx = R(3) * h.Ftx, Ty = R(3) * h.Fty;
-        const R uT = fma(h.ux, Tx, h.uy * Ty);
-        R uH, kG, Kw[2];
+        R uT, uH, kG, Kw[2];
         if constexpr (UNI) {
-            // H = T (grad rho = 0), F_a = 0; tau_g and rho are constants
+            // H = T = 3 (F_s + G) (grad rho = 0), F_a = 0; tau_g and rho are
+            // constants; the factor 3 of T sits in the constants K3w
             omtg = P.omtg3;
             kG = P.kG3;
-            Kw[0] = P.Kw3[0];
-            Kw[1] = P.Kw3[1];
-            uH = uT;
-            KX[0] = Kw[0] * Tx;
-            KX[1] = Kw[0] * Ty;
-            KX[2] = Kw[1] * (Tx + Ty);
-            KX[3] = Kw[1] * (Tx - Ty);
+            const R uF = fma(h.ux, h.Ftx, h.uy * h.Fty);
+            // K_w e.T: products of sums only, so that no instantiation of the
+            // kernels can contract a product into an add differently
+            KX[0] = P.K3w3[0] * h.Ftx;
+            KX[1] = P.K3w3[0] * h.Fty;
+            KX[2] = P.K3w3[1] * (h.Ftx + h.Fty);
+            KX[3] = P.K3w3[1] * (h.Ftx - h.Fty);
             const R p3 = h.p * P.p3tg3;
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                RX[c] = fma(-Kw[c], uT, P.Rw3[c]);
-                PX[c] = fma(-Kw[c], uT, (c == 0 ? w9 : w36) * p3);
+                RX[c] = fma(-P.K3w3[c], uF, P.Rw3[c]);
+                PX[c] = fma(-P.K3w3[c], uF, (c == 0 ? w9 : w36) * p3);
             }
 #pragma unroll
             for (int c = 0; c < 4; c++) AX[c] = KX[c];
+            uT = R(3) * uF;
+            uH = uT;
         } else {
+            const R Tx = R(3) * h.Ftx, Ty = R(3) * h.Fty;
+            uT = fma(h.ux, Tx, h.uy * Ty);
             omtg = R(1) - itg;
             kG = fma(R(-0.5), itg, R(1));
             Kw[0] = w9 * kG;
@@ -362,11 +365,11 @@ struct Collider {
                 A2[c] *= sc;
                 RX[c] *= sc;
                 PX[c] *= sc;
+                Q1[c] *= sc;
+                Q2[c] *= sc;
             }
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-                V1[c] *= sc;
-                V2[c] *= sc;
                 KX[c] *= sc;
                 AX[c] *= sc;
             }
@@ -389,10 +392,24 @@ struct Collider {
     {
         static_assert(K == 1 || K == 2 || K == 5 || K == 8, "pair<K> takes the direction with s = +1");
         constexpr int C = comp(K), W = wclass(K);
-        o1p = fma(omt1, f1p, A1[W] + V1[C]);
-        o1m = fma(omt1, f1m, A1[W] - V1[C]);
-        o2p = fma(omt2, f2p, A2[W] + V2[C]);
-        o2m = fma(omt2, f2m, A2[W] - V2[C]);
+        R s1p, s1m, s2p, s2m;  // A_i +- V_i
+        if constexpr (C < 2) {
+            s1p = fma(R(4), Q1[C], A1[W]);
+            s1m = fma(R(-4), Q1[C], A1[W]);
+            s2p = fma(R(4), Q2[C], A2[W]);
+            s2m = fma(R(-4), Q2[C], A2[W]);
+        } else {
+            const R V1 = C == 2 ? Q1[0] + Q1[1] : Q1[0] - Q1[1];
+            const R V2 = C == 2 ? Q2[0] + Q2[1] : Q2[0] - Q2[1];
+            s1p = A1[W] + V1;
+            s1m = A1[W] - V1;
+            s2p = A2[W] + V2;
+            s2m = A2[W] - V2;
+        }
+        o1p = fma(omt1, f1p, s1p);
+        o1m = fma(omt1, f1m, s1m);
+        o2p = fma(omt2, f2p, s2p);
+        o2m = fma(omt2, f2m, s2m);
         const R beta = b[C];
         const R a = fma(beta, R(0.5) * beta, t0);
         const R sym = fma(beta, KX[C], fma(a, RX[W], PX[W]));

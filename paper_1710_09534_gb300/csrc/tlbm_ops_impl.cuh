@@ -66,6 +66,9 @@ inline Prm<R> cast_prm(const Prm<double>& d)
         r.drho12[i] = R(d.drho12[i]);
         r.aM6[i] = R(d.aM6[i]);
         r.k3tau[i] = R(d.k3tau[i]);
+        r.kq[i] = R(d.kq[i]);
+        r.ks[i] = R(d.ks[i]);
+        r.K3w3[i] = R(d.K3w3[i]);
         r.qa[i][0] = R(d.qa[i][0]);
         r.qa[i][1] = R(d.qa[i][1]);
     }

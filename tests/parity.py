@@ -103,15 +103,17 @@ def assert_oracle_parity(L, O, params, tol=TOL64, what=""):
 
 # Bounds of the reduced-precision paths against the oracle: field ->
 # (kind, bound), "abs" absolute, "rel" relative to max|oracle| (about ten times
-# what was measured on GB300 for FP32 and FP16, three times for BF16).  The
-# density error is taken relative to the largest density, since it is the
-# order-parameter error scaled by the density contrast (Eq. 14).
+# what was measured on GB300 for FP32 and FP16, three times for BF16; the BF16
+# order-parameter bound is the FP16 one times 2^3, the ratio of the two
+# formats' unit roundoffs, 8 against 11 significand bits).  The density error
+# is taken relative to the largest density, since it is the order-parameter
+# error scaled by the density contrast (Eq. 14).
 BOUNDS = {
     "fp32": dict(c1=("abs", 2e-4), c2=("abs", 2e-4), c3=("abs", 2e-4), rho=("rel", 1e-3),
                  ux=("rel", 1e-3), uy=("rel", 1e-3), p=("rel", 1e-3), mu1=("rel", 2e-2), mu2=("rel", 2e-2)),
     "fp16": dict(c1=("abs", 2e-4), c2=("abs", 2e-4), c3=("abs", 2e-4), rho=("rel", 2e-4),
                  ux=("rel", 3e-2), uy=("rel", 3e-2), p=("rel", 6e-2), mu1=("rel", 6e-3), mu2=("rel", 6e-3)),
-    "bf16": dict(c1=("abs", 1e-3), c2=("abs", 1e-3), c3=("abs", 1e-3), rho=("rel", 1e-3),
+    "bf16": dict(c1=("abs", 1.6e-3), c2=("abs", 1.6e-3), c3=("abs", 1.6e-3), rho=("rel", 1e-3),
                  ux=("rel", 6e-2), uy=("rel", 6e-2), p=("rel", 0.16), mu1=("rel", 5e-2), mu2=("rel", 5e-2)),
 }
 
