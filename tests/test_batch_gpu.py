@@ -3,13 +3,11 @@ result is the same alone and in a batch.
 
 The batch runs the same per-tile and per-node device code as tlb_step, with
 the member's parameters read from its device descriptor instead of kernel
-arguments; the compiler may fuse multiply-adds differently in the two
-kernels, so results agree to rounding, not bit for bit.  Every member must
-match the same lattice stepped alone within the FP64 parity tolerance
-(1e-12 relative max-norm of the raw state) or, in FP32, within 1e-5 of the
-state's scale (a few FP32 roundings amplified over tens of steps), whatever
-else is in the batch, across odd and even step counts, membership changes
-and tuning.
+arguments; the library is built with every fused multiply-add explicit
+(-fmad=false), so both kernels round identically.  Every member's raw state
+must equal that of the same lattice stepped alone bit for bit, whatever else
+is in the batch, across odd and even step counts, membership changes and
+tuning.
 """
 import numpy as np
 import pytest
@@ -17,17 +15,16 @@ import pytest
 import oracle
 import workloads as W
 from oracle import OracleLattice
-from parity import assert_bounded, assert_oracle_parity, plane_errors
+from parity import assert_bounded, assert_oracle_parity
 
 pytestmark = pytest.mark.gpu
 
 
-TOL = dict(fp64=1e-12, fp32=1e-5)
-
-
 def same(a, m, precision):
-    """Per-plane relative max-norm (parity.plane_errors) of two raw states."""
-    return float(plane_errors(m.state(), a.state()).max()) < TOL[precision]
+    """The raw states of two lattices are equal bit for bit (`precision` names
+    the storage in failure messages)."""
+    sa, sm = a.state(), m.state()
+    return bool(np.array_equal(sa, sm))
 
 
 def oracle_of(w):

@@ -62,10 +62,10 @@ def test_served_results_equal_runs_alone(T):
         L = T.lattice_from_workload(r.workload, r.precision)
         L.step(r.steps)
         ref = L.fields()
-        tol = 1e-12 if r.precision == "fp64" else 1e-5
-        for k in ("c1", "c2", "ux", "uy", "p"):
-            scale = max(float(np.abs(ref[k]).max()), 1e-6)
-            assert np.abs(r.fields[k] - ref[k]).max() <= tol * scale, (r.rid, k)
+        # the batch kernel and the single-lattice kernel share the update code
+        # and round identically: the results are equal bit for bit
+        for k in ("c1", "c2", "ux", "uy", "p", "mu1", "mu2"):
+            assert np.array_equal(r.fields[k], ref[k]), (r.rid, r.precision, k, float(np.abs(r.fields[k] - ref[k]).max()))
 
 
 def test_request_larger_than_budget_is_rejected(T):
