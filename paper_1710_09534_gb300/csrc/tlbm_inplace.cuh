@@ -311,10 +311,9 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
         col.build(P, m, h, c1ux - cp[0], c1uy - cp[1], c2ux - cp[2], c2uy - cp[3]);
         collide_all_inplace<S, R>(col, gv,
             [&](auto kc, R& f1k, R& f2k) {
-                constexpr int K = decltype(kc)::value;
                 if constexpr (kPre) {
-                    f1k = f1[K];
-                    f2k = f2[K];
+                    f1k = f1[decltype(kc)::value];
+                    f2k = f2[decltype(kc)::value];
                 } else {
                     load_f(kc, f1k, f2k);
                 }
