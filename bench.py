@@ -705,11 +705,12 @@ def served(args, torch, T):
 
 
 def d3q19(args, torch, T, fp64_peak=None):
-    """The D3Q19 form (FP64): tiled hemispherical drops of fluids 1 and 2 on
-    a wetting wall, periodic in x and z; whole steps (three launches each)
+    """The D3Q19 form: tiled hemispherical drops of fluids 1 and 2 on a
+    wetting wall, periodic in x and z; whole steps (three launches each)
     timed with CUDA events on the lattice's stream, each launch timed apart
-    (tlb3_profile) for the roofline of the update kernel, which is bound by
-    the FP64 unit; and the c_1, c_2 mass drift over the timed steps."""
+    (tlb3_profile) for the roofline of the update kernel (FP64: bound by the
+    FP64 unit; FP32 storage: by HBM, on 2 (57 + 6) 4 B per node); and the
+    c_1, c_2 mass drift over the timed steps."""
     import workloads as W
     nx, ny, nz = (int(v) for v in args.d3_size.split(","))
     w = W.drops3d_on_wall(nx, ny, nz)
@@ -747,6 +748,23 @@ def d3q19(args, torch, T, fp64_peak=None):
     ev[1].synchronize()
     gms = ev[0].elapsed_time(ev[1])
     G.close()
+    # FP32 storage and arithmetic (rest populations as float pairs), the same lattice
+    F = T.lattice3_from_workload(w, precision="fp32")
+    F.step(3)
+    F.sync()
+    fm0 = np.array(F.diagnostics()["mass"])
+    F.profile(True)
+    ev[0].record(stream)
+    F.step(args.d3_steps)
+    ev[1].record(stream)
+    ev[1].synchronize()
+    fms = ev[0].elapsed_time(ev[1])
+    fk, fn = F.profile_read()
+    F.profile(False)
+    fm1 = np.array(F.diagnostics()["mass"])
+    F.close()
+    fupd = fk[2] / max(fn[2], 1)
+    f32_bytes = 2 * (57 + 6) * 4
     upd_ms = kms[2] / max(kn[2], 1)
     dp_inst, flops = FP64_DP3["uniform"]
     ach = fluid * flops / (upd_ms / 1e3) / 1e12
@@ -765,7 +783,19 @@ def d3q19(args, torch, T, fp64_peak=None):
             "gpu_launches": 3 * args.d3_steps,
             "mass_drift": [float(f"{v:.3g}") for v in np.abs(m1[:2] - m0[:2]) / np.abs(m0[:2])],
             "general": {"value": round(n * ng / (gms / 1e3) / 1e6, 2), "unit": "MLUPS", "steps": ng,
-                        "update": "general (rho = 1, 3, 1; nu = 0.08, 0.12, 0.1)"}}
+                        "update": "general (rho = 1, 3, 1; nu = 0.08, 0.12, 0.1)"},
+            "fp32": {"value": round(n * args.d3_steps / (fms / 1e3) / 1e6, 2), "unit": "MLUPS",
+                     "steps": args.d3_steps, "ms_per_step": round(fms / args.d3_steps, 4),
+                     "kernel_ms": {"k3_csum": round(fk[0] / max(fn[0], 1), 4),
+                                   "k3_mu": round(fk[1] / max(fn[1], 1), 4), "k3_update": round(fupd, 4)},
+                     "roofline": {"bound": "hbm", "kernel": "k3_update<float, uniform>",
+                                  "algorithmic_bytes_per_node": f32_bytes,
+                                  "achieved": round(fluid * f32_bytes / (fupd / 1e3) / 1e9, 1),
+                                  "peak": peaks()[0], "unit": "GB/s",
+                                  "frac": round(fluid * f32_bytes / (fupd / 1e3) / 1e9 / peaks()[0], 4)},
+                     "hbm_roofline_pct_whole_step": round(100 * n * args.d3_steps / (fms / 1e3) * f32_bytes
+                                                          / (peaks()[0] * 1e9), 2),
+                     "mass_drift": [float(f"{v:.3g}") for v in np.abs(fm1[:2] - fm0[:2]) / np.abs(fm0[:2])]}}
 
 
 def e2e(L, w, args, torch, T):

@@ -331,7 +331,10 @@ void tlb_batch_destroy(tlb_batch *batch);
  * (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1); weights 1/3,
  * 1/18, 1/36): Eqs. 1-20 with the Eq. 20 stencils over its 18 links, the
  * Eq. 42 wetting ghost on every link into a wetting solid (Eq. 43 otherwise),
- * half-way bounce-back (Eq. 44), FP64 storage and arithmetic, BGK collision.
+ * half-way bounce-back (Eq. 44), BGK collision.  precision: TLB_FP64 (FP64
+ * storage and arithmetic) or TLB_FP32 (FP32 storage and arithmetic, the rest
+ * populations as float pairs hi + lo so that each component's mass is
+ * conserved to round-off, as for the 2D FP32 storage); TLB_EINVAL otherwise.
  * Body force G = rho (gx, gy, 0).  Node arrays are [nz][ny][nx], x fastest;
  * nx, ny, nz >= 3 and nx*ny*nz < 2^31 (TLB_EINVAL otherwise).
  * edges[6] = {x-, x+, y-, y+, z-, z+}, each TLB_EDGE_PERIODIC, _WETTING or
@@ -356,8 +359,8 @@ void tlb_batch_destroy(tlb_batch *batch);
  *   tlb3_diagnostics: FP64 mass totals of c1, c2, c3 over fluid nodes and
  *     the non-finite count (TLB_EUNSTABLE if any). */
 typedef struct tlb3_lattice tlb3_lattice;
-int64_t tlb3_workspace_bytes(int nx, int ny, int nz);
-int tlb3_create(int nx, int ny, int nz, const int32_t edges[6], void *dev_workspace, int64_t ws_bytes,
+int64_t tlb3_workspace_bytes(int nx, int ny, int nz, int precision);
+int tlb3_create(int nx, int ny, int nz, int precision, const int32_t edges[6], void *dev_workspace, int64_t ws_bytes,
                 void *cuda_stream, tlb3_lattice **out);
 int tlb3_set_geometry(tlb3_lattice *lat, const uint8_t *host_mask);
 int tlb3_set_params(tlb3_lattice *lat, const tlb_params *params);

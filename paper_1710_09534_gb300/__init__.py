@@ -103,8 +103,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tlb_batch_tune": (i32, [vp, i32, vp, i64, ctypes.POINTER(ctypes.c_int), dp]),
         "tlb_batch_destroy": (None, [vp]),
         "tlb_last_error": (ctypes.c_char_p, []),
-        "tlb3_workspace_bytes": (i64, [i32, i32, i32]),
-        "tlb3_create": (i32, [i32, i32, i32, ctypes.POINTER(ctypes.c_int32), vp, i64, vp, ctypes.POINTER(vp)]),
+        "tlb3_workspace_bytes": (i64, [i32, i32, i32, i32]),
+        "tlb3_create": (i32, [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), vp, i64, vp, ctypes.POINTER(vp)]),
         "tlb3_set_geometry": (i32, [vp, ctypes.POINTER(ctypes.c_uint8)]),
         "tlb3_set_params": (i32, [vp, ctypes.POINTER(Params)]),
         "tlb3_set_fields": (i32, [vp, dp, dp, dp, dp, dp, dp]),
@@ -406,11 +406,12 @@ FIELDS3 = ("c1", "c2", "c3", "rho", "ux", "uy", "uz", "p", "mu1", "mu2", "mu3")
 
 
 class Lattice3D:
-    """One D3Q19 lattice (FP64) on the current CUDA device, advanced on
+    """One D3Q19 lattice (FP64 or FP32 storage and arithmetic) on the current CUDA device, advanced on
     ``stream`` (see the "D3Q19" section of include/tlbm.h).  Arrays are
     [nz, ny, nx]; edges = (x-, x+, y-, y+, z-, z+)."""
 
-    def __init__(self, nx: int, ny: int, nz: int, edges=(0, 0, 1, 2, 0, 0), stream=None, device=None):
+    def __init__(self, nx: int, ny: int, nz: int, edges=(0, 0, 1, 2, 0, 0), stream=None, device=None,
+                 precision="fp64"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("tlbm needs a CUDA device; there is no CPU fallback")
@@ -421,11 +422,13 @@ class Lattice3D:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            nbytes = _check(self.lib.tlb3_workspace_bytes(self.nx, self.ny, self.nz))
+            self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+            nbytes = _check(self.lib.tlb3_workspace_bytes(self.nx, self.ny, self.nz, self.precision))
             self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
             h = ctypes.c_void_p()
             e = (ctypes.c_int32 * 6)(*self.edges)
-            _check(self.lib.tlb3_create(self.nx, self.ny, self.nz, e, ctypes.c_void_p(self.workspace.data_ptr()),
+            _check(self.lib.tlb3_create(self.nx, self.ny, self.nz, self.precision, e,
+                                        ctypes.c_void_p(self.workspace.data_ptr()),
                                         int(nbytes), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self._h = h
 
@@ -495,9 +498,10 @@ class Lattice3D:
         return dict(mass=np.array(d.mass[:]), nonfinite=int(d.nonfinite), rc=rc)
 
 
-def lattice3_from_workload(w, stream=None) -> Lattice3D:
-    """Create and initialise a Lattice3D from a ``workloads.Workload3``."""
-    L = Lattice3D(w.nx, w.ny, w.nz, w.edges, stream=stream)
+def lattice3_from_workload(w, stream=None, precision="fp64") -> Lattice3D:
+    """Create and initialise a Lattice3D from a ``workloads.Workload3``
+    (precision "fp64" or "fp32")."""
+    L = Lattice3D(w.nx, w.ny, w.nz, w.edges, stream=stream, precision=precision)
     L.set_geometry(w.mask)
     L.set_params(w.params)
     L.set_fields(w.c1, w.c2, w.ux, w.uy, w.uz, w.p)

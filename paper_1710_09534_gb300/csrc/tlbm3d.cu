@@ -22,6 +22,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "tlbm.h"
@@ -62,25 +63,26 @@ struct Geo3 {
 // scaled so that their weights are small integers: G = 12 grad (weights 2 on
 // the axis links, 1 on the diagonal ones), L6 = 6 lap (the same weights, minus
 // 24 times the centre); the factors 1/12 and 1/6 sit in these constants.
+template <typename R>
 struct Prm3 {
-    double eta[2], rho[3], nu[3];
-    double l3_l1, l3_l2;
-    double k4D;                    // 4 / D (Eq. 42)
-    double cos12, cos13, cos23;
-    double kl[2], kT, kd6[2];      // Eq. 8: 12 lambda_i / D, 24 lambda_T / D, (3/4) D lambda_i / 6
-    double qa[2][2];               // (mu_i - mu_3) / 12 = qa[i][0] mu_1 + qa[i][1] mu_2
-    double drho12[2];              // (rho_i - rho_3) / 12
-    double aM6[2];                 // (rho_i - rho_3) M_i / 6 (Eq. 12 from L6 mu_i)
-    double nu3, dnu[2];            // nu_3, nu_i - nu_3 (Eq. 15)
-    double gx, gy;                 // G = rho (gx, gy, 0)
+    R eta[2], rho[3], nu[3];
+    R l3_l1, l3_l2;
+    R k4D;                    // 4 / D (Eq. 42)
+    R cos12, cos13, cos23;
+    R kl[2], kT, kd6[2];      // Eq. 8: 12 lambda_i / D, 24 lambda_T / D, (3/4) D lambda_i / 6
+    R qa[2][2];               // (mu_i - mu_3) / 12 = qa[i][0] mu_1 + qa[i][1] mu_2
+    R drho12[2];              // (rho_i - rho_3) / 12
+    R aM6[2];                 // (rho_i - rho_3) M_i / 6 (Eq. 12 from L6 mu_i)
+    R nu3, dnu[2];            // nu_3, nu_i - nu_3 (Eq. 15)
+    R gx, gy;                 // G = rho (gx, gy, 0)
     // order parameters (Eqs. 1a, 2a, 11a)
-    double omt[2];                 // 1 - 1/tau_i
-    double e0[2], itau[2];         // (w_0 - 1) eta_i / tau_i, 1 / tau_i
-    double aw[2][2];               // w eta_i / tau_i (axis, diagonal)
-    double kq[2], sq[2];           // 3 w36 / tau_i, 3 w36 (1 - 1/(2 tau_i))
+    R omt[2];                 // 1 - 1/tau_i
+    R e0[2], itau[2];         // (w_0 - 1) eta_i / tau_i, 1 / tau_i
+    R aw[2][2];               // w eta_i / tau_i (axis, diagonal)
+    R kq[2], sq[2];           // 3 w36 / tau_i, 3 w36 (1 - 1/(2 tau_i))
     // uniform properties (rho, nu equal in the three fluids)
-    double rho0, irho, hirho, prho;  // rho, 1/rho, 1/(2 rho), -rho/4
-    double itg0, omtg0, kG0, Kw0[2], Rw0[2], p3tg0, Gc[2];
+    R rho0, irho, hirho, prho;  // rho, 1/rho, 1/(2 rho), -rho/4
+    R itg0, omtg0, kG0, Kw0[2], Rw0[2], p3tg0, Gc[2];
 };
 
 // Per-node link word: bit k-1 (k = 1..18) set when x + e_k is a fluid node
@@ -89,6 +91,29 @@ struct Prm3 {
 // on solid nodes.
 constexpr uint32_t LNK_SOLID = 1u << 31;
 constexpr int LNK_NW = 18;
+
+// FP32 storage keeps the rest populations f^1_0, f^2_0 as float pairs hi + lo
+// (the lo parts in planes 57, 58 of a distribution buffer) and sets them after
+// the collision to the old pair plus sum_k (f_k - f'_k) over the moving
+// directions, so that each component's mass changes only by the rounding of
+// those small differences (Eq. 1a conserves c_i).
+template <typename R>
+constexpr bool kLo3 = std::is_same<R, float>::value;
+template <typename R>
+constexpr int kPlanes3 = kLo3<R> ? NPLANES + 2 : NPLANES;
+constexpr int kLoPlane = NPLANES;  // f^1_0 lo; f^2_0 lo follows
+
+// hi + lo plus a small increment d, renormalised (Knuth's TwoSum keeps the
+// rounding of hi + d, which joins lo)
+__device__ __forceinline__ void rest_add3(float hi, float lo, float d, float& nhi, float& nlo)
+{
+    const float s = hi + d;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (d - bb);
+    const float t = e + lo;
+    nhi = s + t;
+    nlo = t - (nhi - s);
+}
 
 __device__ __forceinline__ long long node_off(const Geo3& g, int x, int y, int z)
 {
@@ -117,13 +142,14 @@ __device__ __forceinline__ int site(const Geo3& g, const uint8_t* __restrict__ k
 
 // Eq. 8 for i = 1, 2 from c_1, c_2 and L6 = 6 lap c_i; c (1 - c)(1 - 2c) in
 // Horner form c (1 + c (2c - 3)).
-__device__ __forceinline__ void chem_pot(const Prm3& P, double c1, double c2, double l6c1, double l6c2, double& mu1,
-                                         double& mu2)
+template <typename R>
+__device__ __forceinline__ void chem_pot(const Prm3<R>& P, R c1, R c2, R l6c1, R l6c2, R& mu1,
+                                         R& mu2)
 {
-    const double c3 = 1.0 - c1 - c2;
-    const double t = P.kT * (c1 * c2) * c3;
-    const double h1 = c1 * fma(c1, fma(2.0, c1, -3.0), 1.0);
-    const double h2 = c2 * fma(c2, fma(2.0, c2, -3.0), 1.0);
+    const R c3 = R(1.0) - c1 - c2;
+    const R t = P.kT * (c1 * c2) * c3;
+    const R h1 = c1 * fma(c1, fma(R(2.0), c1, -R(3.0)), R(1.0));
+    const R h2 = c2 * fma(c2, fma(R(2.0), c2, -R(3.0)), R(1.0));
     mu1 = fma(-P.kd6[0], l6c1, fma(P.kl[0], h1, -t));
     mu2 = fma(-P.kd6[1], l6c2, fma(P.kl[1], h2, -t));
 }
@@ -135,16 +161,16 @@ struct Nb3 {
     long long dx[3], dy[3], dz[3];
     __device__ __forceinline__ Nb3(const Geo3& g, int x, int y, int z)
     {
-        const long long P = g.pitch, R = (long long)g.ny * g.pitch;
+        const long long P = g.pitch, RZ = (long long)g.ny * g.pitch;
         dx[0] = x == 0 ? g.nx - 1 : -1;
         dx[1] = 0;
         dx[2] = x == g.nx - 1 ? -(long long)(g.nx - 1) : 1;
         dy[0] = y == 0 ? (g.ny - 1) * P : -P;
         dy[1] = 0;
         dy[2] = y == g.ny - 1 ? -(g.ny - 1) * P : P;
-        dz[0] = z == 0 ? (g.nz - 1) * R : -R;
+        dz[0] = z == 0 ? (g.nz - 1) * RZ : -RZ;
         dz[1] = 0;
-        dz[2] = z == g.nz - 1 ? -(g.nz - 1) * R : R;
+        dz[2] = z == g.nz - 1 ? -(g.nz - 1) * RZ : RZ;
     }
     __device__ __forceinline__ long long off(int k) const { return dx[ex(k) + 1] + dy[ey(k) + 1] + dz[ez(k) + 1]; }
     // the neighbour's element offset when link k is fluid, else the node's own
@@ -188,13 +214,19 @@ __global__ void k3_links(const uint8_t* __restrict__ kind, uint32_t* __restrict_
 }
 
 // c_1, c_2 of every node (Eq. 13a); zero on solids.
-__global__ void k3_csum(const double* __restrict__ f, double* __restrict__ cpl, const uint8_t* __restrict__ kind,
+template <typename R>
+__global__ void k3_csum(const R* __restrict__ f, R* __restrict__ cpl, const uint8_t* __restrict__ kind,
                         Geo3 g)
 {
     NODE_OF_THREAD
     const long long PL = g.plane;
-    double a = 0.0, b = 0.0;
+    R a = R(0.0), b = R(0.0);
     if (kind[o] == K_FLUID) {
+        if constexpr (kLo3<R>) {
+            // the rest population as hi + lo
+            a = f[kLoPlane * PL + o];
+            b = f[(kLoPlane + 1) * PL + o];
+        }
 #pragma unroll
         for (int k = 0; k < Q; k++) {
             a += f[k * PL + o];
@@ -207,35 +239,36 @@ __global__ void k3_csum(const double* __restrict__ f, double* __restrict__ cpl, 
 
 // Sum over the 9 opposite pairs of a pair-wise quantity: axis pairs weighted
 // 2, diagonal pairs 1 (the integer weights 36 w_k).
-#define W36_SUM(S) fma(2.0, ((S)[0] + (S)[1]) + (S)[2], (((S)[3] + (S)[4]) + ((S)[5] + (S)[6])) + ((S)[7] + (S)[8]))
+#define W36_SUM(S) fma(R(2.0), ((S)[0] + (S)[1]) + (S)[2], (((S)[3] + (S)[4]) + ((S)[5] + (S)[6])) + ((S)[7] + (S)[8]))
 
 // mu_1, mu_2 of every fluid node: Eq. 8 with the Eq. 20b Laplacian, whose
 // links into wetting solids take the Eq. 42 ghost c + o_i (with the wall
 // value of c taken as the node's own, dx = 1) and into neutral solids c.
-__global__ void k3_mu(const double* __restrict__ cpl, double* __restrict__ mpl, const uint32_t* __restrict__ lnk,
-                      Geo3 g, Prm3 P)
+template <typename R>
+__global__ void k3_mu(const R* __restrict__ cpl, R* __restrict__ mpl, const uint32_t* __restrict__ lnk,
+                      Geo3 g, Prm3<R> P)
 {
     NODE_OF_THREAD
     const long long PL = g.plane;
     const uint32_t L = lnk[o];
-    double mu1 = 0.0, mu2 = 0.0;
+    R mu1 = R(0.0), mu2 = R(0.0);
     if (!(L & LNK_SOLID)) {
         const Nb3 nb(g, x, y, z);
-        const double c1 = cpl[o], c2 = cpl[PL + o];
-        double s1[9], s2[9];
+        const R c1 = cpl[o], c2 = cpl[PL + o];
+        R s1[9], s2[9];
 #pragma unroll
         for (int p = 0; p < 9; p++) {
             const long long ap = nb.at(L, o, 2 * p + 1), am = nb.at(L, o, 2 * p + 2);
             s1[p] = cpl[ap] + cpl[am];
             s2[p] = cpl[PL + ap] + cpl[PL + am];
         }
-        double l1 = fma(-24.0, c1, W36_SUM(s1));
-        double l2 = fma(-24.0, c2, W36_SUM(s2));
+        R l1 = fma(-R(24.0), c1, W36_SUM(s1));
+        R l2 = fma(-R(24.0), c2, W36_SUM(s2));
         const unsigned nwi = (L >> LNK_NW) & 31u;
         if (nwi) {
-            const double c3 = 1.0 - c1 - c2, nw = (double)(int)nwi;
-            const double o1 = P.k4D * fma(P.cos13, c1 * c3, P.cos12 * (c1 * c2));
-            const double o2 = P.k4D * fma(-P.cos12, c1 * c2, P.cos23 * (c2 * c3));
+            const R c3 = R(1.0) - c1 - c2, nw = (R)(int)nwi;
+            const R o1 = P.k4D * fma(P.cos13, c1 * c3, P.cos12 * (c1 * c2));
+            const R o2 = P.k4D * fma(-P.cos12, c1 * c2, P.cos23 * (c2 * c3));
             l1 = fma(nw, o1, l1);
             l2 = fma(nw, o2, l2);
         }
@@ -247,8 +280,8 @@ __global__ void k3_mu(const double* __restrict__ cpl, double* __restrict__ mpl, 
 
 // X . e_k of the direction k = 2p + 1 of opposite pair p (the odd member),
 // and the same weighted by 36 w_k (x 2 on the axis pairs).
-template <int p>
-__device__ __forceinline__ double edot(const double X[3])
+template <int p, typename R>
+__device__ __forceinline__ R edot(const R X[3])
 {
     if constexpr (p < 3) return X[p];
     else if constexpr (p == 3) return X[0] + X[1];
@@ -258,10 +291,10 @@ __device__ __forceinline__ double edot(const double X[3])
     else if constexpr (p == 7) return X[1] + X[2];
     else return X[1] - X[2];
 }
-template <int p>
-__device__ __forceinline__ double wdot(const double X[3])
+template <int p, typename R>
+__device__ __forceinline__ R wdot(const R X[3])
 {
-    if constexpr (p < 3) return 2.0 * X[p];
+    if constexpr (p < 3) return R(2.0) * X[p];
     else return edot<p>(X);
 }
 
@@ -269,26 +302,34 @@ __device__ __forceinline__ double wdot(const double X[3])
 // 12 grad c_i (Eq. 20a with the Eq. 43 ghosts), u and p (Eqs. 13b, 13c),
 // F_s + G, and in the general case grad rho, the F_a factor of Eq. 12 (Eq.
 // 20b on mu_i, Eq. 43 ghosts) and 1/tau_g (Eqs. 15, 18b); the g populations.
+// The g populations of the update node: FP64 keeps them in registers from
+// the moments to the collision; FP32 storage reads them again there (from
+// L1), which frees the registers the latency-bound FP32 update needs (GB300,
+// 192x96x192: update 0.922 -> 0.642 ms; FP64 2.331 -> 2.372 ms the same way).
+template <typename R>
+constexpr bool kGReg3 = !kLo3<R>;
+
+template <typename R>
 struct Node3 {
-    double c1, c2, mu1, mu2, rho;
-    double u[3], usq, p;
-    double T[3];  // 3 (F_s + G)
-    double H[3];  // grad rho + T
-    double aF, itg;
-    double g[Q];
+    R c1, c2, mu1, mu2, rho;
+    R u[3], usq, p;
+    R T[3];  // 3 (F_s + G)
+    R H[3];  // grad rho + T
+    R aF, itg;
+    R g[Q];
 };
 
-template <bool UNI>
-__device__ __forceinline__ void node3(const Geo3& g, const Prm3& P, const double* __restrict__ f,
-                                      const double* __restrict__ cpl, const double* __restrict__ mpl, uint32_t L,
-                                      const Nb3& nb, long long o, Node3& n)
+template <bool UNI, typename R>
+__device__ __forceinline__ void node3(const Geo3& g, const Prm3<R>& P, const R* __restrict__ f,
+                                      const R* __restrict__ cpl, const R* __restrict__ mpl, uint32_t L,
+                                      const Nb3& nb, long long o, Node3<R>& n)
 {
     const long long PL = g.plane;
     n.c1 = cpl[o];
     n.c2 = cpl[PL + o];
     n.mu1 = mpl[o];
     n.mu2 = mpl[PL + o];
-    double d1[9], d2[9], s1[9], s2[9];
+    R d1[9], d2[9], s1[9], s2[9];
 #pragma unroll
     for (int p = 0; p < 9; p++) {
         const long long ap = nb.at(L, o, 2 * p + 1), am = nb.at(L, o, 2 * p + 2);
@@ -299,34 +340,37 @@ __device__ __forceinline__ void node3(const Geo3& g, const Prm3& P, const double
             s2[p] = mpl[PL + ap] + mpl[PL + am];
         }
     }
-    double G1[3], G2[3];
-    G1[0] = fma(2.0, d1[0], (d1[3] + d1[4]) + (d1[5] + d1[6]));
-    G1[1] = fma(2.0, d1[1], (d1[3] - d1[4]) + (d1[7] + d1[8]));
-    G1[2] = fma(2.0, d1[2], (d1[5] - d1[6]) + (d1[7] - d1[8]));
-    G2[0] = fma(2.0, d2[0], (d2[3] + d2[4]) + (d2[5] + d2[6]));
-    G2[1] = fma(2.0, d2[1], (d2[3] - d2[4]) + (d2[7] + d2[8]));
-    G2[2] = fma(2.0, d2[2], (d2[5] - d2[6]) + (d2[7] - d2[8]));
+    R G1[3], G2[3];
+    G1[0] = fma(R(2.0), d1[0], (d1[3] + d1[4]) + (d1[5] + d1[6]));
+    G1[1] = fma(R(2.0), d1[1], (d1[3] - d1[4]) + (d1[7] + d1[8]));
+    G1[2] = fma(R(2.0), d1[2], (d1[5] - d1[6]) + (d1[7] - d1[8]));
+    G2[0] = fma(R(2.0), d2[0], (d2[3] + d2[4]) + (d2[5] + d2[6]));
+    G2[1] = fma(R(2.0), d2[1], (d2[3] - d2[4]) + (d2[7] + d2[8]));
+    G2[2] = fma(R(2.0), d2[2], (d2[5] - d2[6]) + (d2[7] - d2[8]));
     // g moments from the sums and differences of opposite pairs
-    const double* gq = f + 2 * Q * PL;
-    n.g[0] = gq[o];
-    double gs[9], gd[9];
+    const R* gq = f + 2 * Q * PL;
+    if constexpr (kGReg3<R>) n.g[0] = gq[o];
+    R gs[9], gd[9];
 #pragma unroll
     for (int p = 0; p < 9; p++) {
-        n.g[2 * p + 1] = gq[(2 * p + 1) * PL + o];
-        n.g[2 * p + 2] = gq[(2 * p + 2) * PL + o];
-        gs[p] = n.g[2 * p + 1] + n.g[2 * p + 2];
-        gd[p] = n.g[2 * p + 1] - n.g[2 * p + 2];
+        const R gp = gq[(2 * p + 1) * PL + o], gm = gq[(2 * p + 2) * PL + o];
+        if constexpr (kGReg3<R>) {
+            n.g[2 * p + 1] = gp;
+            n.g[2 * p + 2] = gm;
+        }
+        gs[p] = gp + gm;
+        gd[p] = gp - gm;
     }
-    const double sum = (((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7]))) + gs[8];
-    double mom[3];
+    const R sum = (((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7]))) + gs[8];
+    R mom[3];
     mom[0] = gd[0] + ((gd[3] + gd[4]) + (gd[5] + gd[6]));
     mom[1] = gd[1] + ((gd[3] - gd[4]) + (gd[7] + gd[8]));
     mom[2] = gd[2] + ((gd[5] - gd[6]) + (gd[7] - gd[8]));
     // F_s = sum_i mu_i grad c_i with grad c_3 = -grad c_1 - grad c_2 and
     // mu_3 from sum_i mu_i / lambda_i = 0
-    const double m1 = fma(P.qa[0][0], n.mu1, P.qa[0][1] * n.mu2);
-    const double m2 = fma(P.qa[1][0], n.mu1, P.qa[1][1] * n.mu2);
-    double F[3];
+    const R m1 = fma(P.qa[0][0], n.mu1, P.qa[0][1] * n.mu2);
+    const R m2 = fma(P.qa[1][0], n.mu1, P.qa[1][1] * n.mu2);
+    R F[3];
     if constexpr (UNI) {
         n.rho = P.rho0;
         F[0] = fma(m1, G1[0], fma(m2, G2[0], P.Gc[0]));
@@ -336,39 +380,39 @@ __device__ __forceinline__ void node3(const Geo3& g, const Prm3& P, const double
         for (int a = 0; a < 3; a++) n.u[a] = fma(P.hirho, F[a], P.irho * mom[a]);
         n.usq = fma(n.u[0], n.u[0], fma(n.u[1], n.u[1], n.u[2] * n.u[2]));
         // Eq. 13c: p = (1/2) [sum_{k != 0} g_k + rho w_0 (-3/2) u.u] (grad rho = 0)
-        n.p = fma(0.5, sum, P.prho * n.usq);
+        n.p = fma(R(0.5), sum, P.prho * n.usq);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            n.T[a] = 3.0 * F[a];
+            n.T[a] = R(3.0) * F[a];
             n.H[a] = n.T[a];
         }
-        n.aF = 0.0;
+        n.aF = R(0.0);
         n.itg = P.itg0;
     } else {
         n.rho = fma(n.c1, P.rho[0] - P.rho[2], fma(n.c2, P.rho[1] - P.rho[2], P.rho[2]));
-        double gr[3];
+        R gr[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) gr[a] = fma(P.drho12[0], G1[a], P.drho12[1] * G2[a]);
         F[0] = fma(m1, G1[0], fma(m2, G2[0], n.rho * P.gx));
         F[1] = fma(m1, G1[1], fma(m2, G2[1], n.rho * P.gy));
         F[2] = fma(m1, G1[2], m2 * G2[2]);
-        const double ir = tlb::rcp(n.rho);
+        const R ir = tlb::rcp(n.rho);
 #pragma unroll
-        for (int a = 0; a < 3; a++) n.u[a] = fma(0.5, F[a], mom[a]) * ir;
+        for (int a = 0; a < 3; a++) n.u[a] = fma(R(0.5), F[a], mom[a]) * ir;
         n.usq = fma(n.u[0], n.u[0], fma(n.u[1], n.u[1], n.u[2] * n.u[2]));
-        const double ug = fma(n.u[0], gr[0], fma(n.u[1], gr[1], n.u[2] * gr[2]));
+        const R ug = fma(n.u[0], gr[0], fma(n.u[1], gr[1], n.u[2] * gr[2]));
         // Eq. 13c: p = (1/2) [sum_{k != 0} g_k + u.grad rho / 2 + rho w_0 (-3/2) u.u]
-        n.p = fma(0.5, sum, fma(0.25, ug, (-0.25 * n.rho) * n.usq));
+        n.p = fma(R(0.5), sum, fma(R(0.25), ug, (-R(0.25) * n.rho) * n.usq));
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            n.T[a] = 3.0 * F[a];
+            n.T[a] = R(3.0) * F[a];
             n.H[a] = gr[a] + n.T[a];
         }
-        const double l1 = fma(-24.0, n.mu1, W36_SUM(s1));
-        const double l2 = fma(-24.0, n.mu2, W36_SUM(s2));
+        const R l1 = fma(-R(24.0), n.mu1, W36_SUM(s1));
+        const R l2 = fma(-R(24.0), n.mu2, W36_SUM(s2));
         n.aF = fma(P.aM6[0], l1, P.aM6[1] * l2);
-        const double nu = fma(n.c1, P.dnu[0], fma(n.c2, P.dnu[1], P.nu3));
-        n.itg = tlb::rcp(fma(3.0, nu, 0.5));
+        const R nu = fma(n.c1, P.dnu[0], fma(n.c2, P.dnu[1], P.nu3));
+        n.itg = tlb::rcp(fma(R(3.0), nu, R(0.5)));
     }
 }
 
@@ -380,46 +424,63 @@ __device__ __forceinline__ void node3(const Geo3& g, const Prm3& P, const double
 //   Sym = beta K_X + a R_X + P_X,  Anti = a K_X + beta R_X + A_X,
 // K_X = K_w e.H, R_X = w rho/tau_g - K_w u.H, P_X = 3 w p/tau_g - K_w u.T,
 // A_X = K_w e.T + w a_F beta, K_w = w (1 - 1/(2 tau_g)).
+template <typename R>
 struct Coll3 {
-    double omt1, omt2, omtg, t0;
-    double A1[2], A2[2], RX[2], PX[2];
-    double b3[3], Q1[3], Q2[3], Hs[3], Ts[3];
-    double wa36;
+    R omt1, omt2, omtg, t0;
+    R A1[2], A2[2], RX[2], PX[2];
+    R b3[3], Q1[3], Q2[3], Hs[3], Ts[3];
+    R wa36;
 };
 
-template <bool UNI, int p>
-__device__ __forceinline__ void pair3(const Coll3& C, const double* __restrict__ fA, double* __restrict__ fB,
-                                      const Node3& n, const Nb3& nb, uint32_t L, long long o, long long PL)
+template <bool UNI, int p, typename R>
+__device__ __forceinline__ void pair3(const Coll3<R>& C, const R* __restrict__ fA, R* __restrict__ fB,
+                                      const Node3<R>& n, const Nb3& nb, uint32_t L, long long o, long long PL,
+                                      R& d1, R& d2)
 {
     constexpr int kp = 2 * p + 1, km = 2 * p + 2, c = p < 3 ? 0 : 1;
-    const double beta = edot<p>(C.b3);
-    const double KX = wdot<p>(C.Hs);
+    const R beta = edot<p>(C.b3);
+    const R KX = wdot<p>(C.Hs);
     // A_i +- V_i with V_i = 36 w_k e_k.Q'_i (on the axis pairs one fma each)
-    double s1p, s1m, s2p, s2m;
+    R s1p, s1m, s2p, s2m;
     if constexpr (p < 3) {
-        s1p = fma(2.0, C.Q1[p], C.A1[c]);
-        s1m = fma(-2.0, C.Q1[p], C.A1[c]);
-        s2p = fma(2.0, C.Q2[p], C.A2[c]);
-        s2m = fma(-2.0, C.Q2[p], C.A2[c]);
+        s1p = fma(R(2.0), C.Q1[p], C.A1[c]);
+        s1m = fma(-R(2.0), C.Q1[p], C.A1[c]);
+        s2p = fma(R(2.0), C.Q2[p], C.A2[c]);
+        s2m = fma(-R(2.0), C.Q2[p], C.A2[c]);
     } else {
-        const double V1 = edot<p>(C.Q1), V2 = edot<p>(C.Q2);
+        const R V1 = edot<p>(C.Q1), V2 = edot<p>(C.Q2);
         s1p = C.A1[c] + V1;
         s1m = C.A1[c] - V1;
         s2p = C.A2[c] + V2;
         s2m = C.A2[c] - V2;
     }
-    double AX;
+    R AX;
     if constexpr (UNI) AX = KX;
-    else AX = fma(p < 3 ? 2.0 * C.wa36 : C.wa36, beta, wdot<p>(C.Ts));
-    const double a = fma(beta, 0.5 * beta, C.t0);
-    const double sym = fma(beta, KX, fma(a, C.RX[c], C.PX[c]));
-    const double anti = fma(a, KX, fma(beta, C.RX[c], AX));
-    const double o1p = fma(C.omt1, fA[kp * PL + o], s1p);
-    const double o1m = fma(C.omt1, fA[km * PL + o], s1m);
-    const double o2p = fma(C.omt2, fA[(Q + kp) * PL + o], s2p);
-    const double o2m = fma(C.omt2, fA[(Q + km) * PL + o], s2m);
-    const double ogp = fma(C.omtg, n.g[kp], sym + anti);
-    const double ogm = fma(C.omtg, n.g[km], sym - anti);
+    else AX = fma(p < 3 ? R(2.0) * C.wa36 : C.wa36, beta, wdot<p>(C.Ts));
+    const R a = fma(beta, R(0.5) * beta, C.t0);
+    const R sym = fma(beta, KX, fma(a, C.RX[c], C.PX[c]));
+    const R anti = fma(a, KX, fma(beta, C.RX[c], AX));
+    const R f1p = fA[kp * PL + o], f1m = fA[km * PL + o];
+    const R f2p = fA[(Q + kp) * PL + o], f2m = fA[(Q + km) * PL + o];
+    const R o1p = fma(C.omt1, f1p, s1p);
+    const R o1m = fma(C.omt1, f1m, s1m);
+    const R o2p = fma(C.omt2, f2p, s2p);
+    const R o2m = fma(C.omt2, f2m, s2m);
+    if constexpr (kLo3<R>) {
+        // the moving populations' share of the rest pair update
+        d1 += (f1p - o1p) + (f1m - o1m);
+        d2 += (f2p - o2p) + (f2m - o2m);
+    }
+    R gkp, gkm;
+    if constexpr (kGReg3<R>) {
+        gkp = n.g[kp];
+        gkm = n.g[km];
+    } else {  // read again (from L1) instead of holding 19 values in registers
+        gkp = fA[(2 * Q + kp) * PL + o];
+        gkm = fA[(2 * Q + km) * PL + o];
+    }
+    const R ogp = fma(C.omtg, gkp, sym + anti);
+    const R ogm = fma(C.omtg, gkm, sym - anti);
     // push to x + e_k, or back into slot k-bar of this node (Eq. 44)
     const long long dp = (L >> (kp - 1)) & 1u ? kp * PL + o + nb.off(kp) : km * PL + o;
     const long long dm = (L >> (km - 1)) & 1u ? km * PL + o + nb.off(km) : kp * PL + o;
@@ -435,35 +496,39 @@ __device__ __forceinline__ void pair3(const Coll3& C, const double* __restrict__
 // 11a, 11b, 19) and the push to x + e_k.  UNI: equal densities and
 // viscosities (grad rho = 0, F_a = 0, tau_g constant).
 // resident blocks per SM the update is compiled for: the uniform-property
-// update at 3 (168 registers, 16 bytes spilled; GB300, 192x96x192: 2.447 ->
-// 2.348 ms per launch; 2.344 at 4); the general update gains nothing at 2 or 3
+// update at 3 (168 registers, 16 bytes spilled; GB300, 192x96x192: R(2.447) ->
+// R(2.348) ms per launch; R(2.344) at 4); the general update gains nothing at 2 or 3
 #ifndef TLB3_MINB
 #define TLB3_MINB 3
 #endif
 #ifndef TLB3_MINB_GEN
 #define TLB3_MINB_GEN 1
 #endif
-template <bool UNI>
-__global__ void __launch_bounds__(128, UNI ? TLB3_MINB : TLB3_MINB_GEN)
-k3_update(const double* __restrict__ fA, double* __restrict__ fB, double* __restrict__ cu,
-          const double* __restrict__ cpl, const double* __restrict__ mpl, const uint32_t* __restrict__ lnk, Geo3 g,
-          Prm3 P)
+// FP32 storage (bound by memory): resident blocks per SM of both updates
+#ifndef TLB3_MINB32
+#define TLB3_MINB32 3
+#endif
+template <typename R, bool UNI>
+__global__ void __launch_bounds__(128, kLo3<R> ? TLB3_MINB32 : (UNI ? TLB3_MINB : TLB3_MINB_GEN))
+k3_update(const R* __restrict__ fA, R* __restrict__ fB, R* __restrict__ cu,
+          const R* __restrict__ cpl, const R* __restrict__ mpl, const uint32_t* __restrict__ lnk, Geo3 g,
+          Prm3<R> P)
 {
     NODE_OF_THREAD
     const uint32_t L = lnk[o];
     if (L & LNK_SOLID) return;
     const long long PL = g.plane;
     const Nb3 nb(g, x, y, z);
-    Node3 n;
+    Node3<R> n;
     node3<UNI>(g, P, fA, cpl, mpl, L, nb, o, n);
-    constexpr double w0 = 1.0 / 3.0, w36 = 1.0 / 36.0;
-    Coll3 C;
+    constexpr R w0 = R(1.0) / R(3.0), w36 = R(1.0) / R(36.0);
+    Coll3<R> C;
     // order parameters: Q_i = 3 w36 [c_i u / tau_i + (1 - 1/(2 tau_i)) d(c_i u)],
     // d(c_i u) against the previous step's (Eq. 19), which is replaced
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        const double cu1 = n.c1 * n.u[a], cu2 = n.c2 * n.u[a];
-        const double d1 = cu1 - cu[a * PL + o], d2 = cu2 - cu[(3 + a) * PL + o];
+        const R cu1 = n.c1 * n.u[a], cu2 = n.c2 * n.u[a];
+        const R d1 = cu1 - cu[a * PL + o], d2 = cu2 - cu[(3 + a) * PL + o];
         cu[a * PL + o] = cu1;
         cu[(3 + a) * PL + o] = cu2;
         C.Q1[a] = fma(P.kq[0], cu1, P.sq[0] * d1);
@@ -471,8 +536,8 @@ k3_update(const double* __restrict__ fA, double* __restrict__ fB, double* __rest
     }
     C.omt1 = P.omt[0];
     C.omt2 = P.omt[1];
-    const double E1 = fma(P.e0[0], n.mu1, P.itau[0] * n.c1);
-    const double E2 = fma(P.e0[1], n.mu2, P.itau[1] * n.c2);
+    const R E1 = fma(P.e0[0], n.mu1, P.itau[0] * n.c1);
+    const R E2 = fma(P.e0[1], n.mu2, P.itau[1] * n.c2);
 #pragma unroll
     for (int c = 0; c < 2; c++) {
         C.A1[c] = P.aw[0][c] * n.mu1;
@@ -480,9 +545,9 @@ k3_update(const double* __restrict__ fA, double* __restrict__ fB, double* __rest
     }
     // hydrodynamics
 #pragma unroll
-    for (int a = 0; a < 3; a++) C.b3[a] = 3.0 * n.u[a];
-    C.t0 = -1.5 * n.usq;
-    double kG, Kw[2], Rw[2], p3;
+    for (int a = 0; a < 3; a++) C.b3[a] = R(3.0) * n.u[a];
+    C.t0 = -R(1.5) * n.usq;
+    R kG, Kw[2], Rw[2], p3;
     if constexpr (UNI) {
         C.omtg = P.omtg0;
         kG = P.kG0;
@@ -492,22 +557,22 @@ k3_update(const double* __restrict__ fA, double* __restrict__ fB, double* __rest
         Rw[1] = P.Rw0[1];
         p3 = n.p * P.p3tg0;
     } else {
-        C.omtg = 1.0 - n.itg;
-        kG = fma(-0.5, n.itg, 1.0);
-        Kw[0] = (2.0 * w36) * kG;
+        C.omtg = R(1.0) - n.itg;
+        kG = fma(-R(0.5), n.itg, R(1.0));
+        Kw[0] = (R(2.0) * w36) * kG;
         Kw[1] = w36 * kG;
-        const double ri = n.rho * n.itg;
-        Rw[0] = (2.0 * w36) * ri;
+        const R ri = n.rho * n.itg;
+        Rw[0] = (R(2.0) * w36) * ri;
         Rw[1] = w36 * ri;
-        p3 = 3.0 * n.p * n.itg;
+        p3 = R(3.0) * n.p * n.itg;
     }
-    const double uT = fma(n.u[0], n.T[0], fma(n.u[1], n.T[1], n.u[2] * n.T[2]));
-    double uH = uT;
+    const R uT = fma(n.u[0], n.T[0], fma(n.u[1], n.T[1], n.u[2] * n.T[2]));
+    R uH = uT;
     if constexpr (!UNI) uH = fma(n.u[0], n.H[0], fma(n.u[1], n.H[1], n.u[2] * n.H[2]));
 #pragma unroll
     for (int c = 0; c < 2; c++) {
         C.RX[c] = fma(-Kw[c], uH, Rw[c]);
-        C.PX[c] = fma(-Kw[c], uT, (c == 0 ? 2.0 * w36 : w36) * p3);
+        C.PX[c] = fma(-Kw[c], uT, (c == 0 ? R(2.0) * w36 : w36) * p3);
     }
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -516,71 +581,91 @@ k3_update(const double* __restrict__ fA, double* __restrict__ fB, double* __rest
     }
     C.wa36 = w36 * n.aF;
     // rest direction: g^eq_0 = 3p (w_0 - 1) + rho w_0 t0, G_0 = -w_0 K_G (t0 u.H + u.T)
-    const double geq0 = fma(n.rho * w0, C.t0, (3.0 * (w0 - 1.0)) * n.p);
-    const double P0 = fma(geq0, n.itg, -(w0 * kG) * fma(C.t0, uH, uT));
-    fB[o] = fma(C.omt1, fA[o], E1);
-    fB[Q * PL + o] = fma(C.omt2, fA[Q * PL + o], E2);
-    fB[2 * Q * PL + o] = fma(C.omtg, n.g[0], P0);
-    pair3<UNI, 0>(C, fA, fB, n, nb, L, o, PL);
-    pair3<UNI, 1>(C, fA, fB, n, nb, L, o, PL);
-    pair3<UNI, 2>(C, fA, fB, n, nb, L, o, PL);
-    pair3<UNI, 3>(C, fA, fB, n, nb, L, o, PL);
-    pair3<UNI, 4>(C, fA, fB, n, nb, L, o, PL);
-    pair3<UNI, 5>(C, fA, fB, n, nb, L, o, PL);
-    pair3<UNI, 6>(C, fA, fB, n, nb, L, o, PL);
-    pair3<UNI, 7>(C, fA, fB, n, nb, L, o, PL);
-    pair3<UNI, 8>(C, fA, fB, n, nb, L, o, PL);
+    const R geq0 = fma(n.rho * w0, C.t0, (R(3.0) * (w0 - R(1.0))) * n.p);
+    const R P0 = fma(geq0, n.itg, -(w0 * kG) * fma(C.t0, uH, uT));
+    R d1 = R(0), d2 = R(0);  // sum_k (f_k - f'_k) over the moving directions (FP32)
+    if constexpr (!kLo3<R>) {
+        fB[o] = fma(C.omt1, fA[o], E1);
+        fB[Q * PL + o] = fma(C.omt2, fA[Q * PL + o], E2);
+    }
+    fB[2 * Q * PL + o] = fma(C.omtg, kGReg3<R> ? n.g[0] : fA[2 * Q * PL + o], P0);
+    pair3<UNI, 0>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 1>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 2>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 3>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 4>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 5>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 6>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 7>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 8>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    if constexpr (kLo3<R>) {
+        // rest pairs: the old pair plus the moving populations' decrease
+        R h1, l1, h2, l2;
+        rest_add3(fA[o], fA[kLoPlane * PL + o], d1, h1, l1);
+        rest_add3(fA[Q * PL + o], fA[(kLoPlane + 1) * PL + o], d2, h2, l2);
+        fB[o] = h1;
+        fB[Q * PL + o] = h2;
+        fB[kLoPlane * PL + o] = l1;
+        fB[(kLoPlane + 1) * PL + o] = l2;
+    }
 }
 
 // c of every node from dense host-order arrays (c1 then c2, nx*ny*nz each).
-__global__ void k3_load_c(const double* __restrict__ in, double* __restrict__ cpl, const uint8_t* __restrict__ kind,
+template <typename R>
+__global__ void k3_load_c(const double* __restrict__ in, R* __restrict__ cpl, const uint8_t* __restrict__ kind,
                           Geo3 g)
 {
     NODE_OF_THREAD
     const long long n = ((long long)z * g.ny + y) * g.nx + x, N = (long long)g.nx * g.ny * g.nz;
     const bool fl = kind[o] == K_FLUID;
-    cpl[o] = fl ? in[n] : 0.0;
-    cpl[g.plane + o] = fl ? in[N + n] : 0.0;
+    cpl[o] = fl ? R(in[n]) : R(0.0);
+    cpl[g.plane + o] = fl ? R(in[N + n]) : R(0.0);
 }
 
-// Initial state from c, mu (planes) and u, p (dense arrays ux, uy, uz[, p]):
-// f = f^eq(c, mu, u), g = g^eq(p, rho, u), c_i u stored (Eq. 19).
-__global__ void k3_init(double* __restrict__ f, double* __restrict__ cu, const double* __restrict__ cpl,
-                        const double* __restrict__ mpl, const uint8_t* __restrict__ kind,
-                        const double* __restrict__ in, int has_p, Geo3 g, Prm3 P)
+// Initial state from c, mu (planes) and u, p (dense FP64 arrays ux, uy,
+// uz[, p]): f = f^eq(c, mu, u), g = g^eq(p, rho, u), c_i u stored (Eq. 19);
+// with FP32 storage the rest pairs start with lo = 0.
+template <typename R>
+__global__ void k3_init(R* __restrict__ f, R* __restrict__ cu, const R* __restrict__ cpl,
+                        const R* __restrict__ mpl, const uint8_t* __restrict__ kind,
+                        const double* __restrict__ in, int has_p, Geo3 g, Prm3<R> P)
 {
     NODE_OF_THREAD
     const long long PL = g.plane;
     const long long n = ((long long)z * g.ny + y) * g.nx + x, N = (long long)g.nx * g.ny * g.nz;
     if (kind[o] != K_FLUID) {
-        for (int q = 0; q < NPLANES; q++) f[q * PL + o] = 0.0;
-        for (int q = 0; q < 6; q++) cu[q * PL + o] = 0.0;
+        for (int q = 0; q < kPlanes3<R>; q++) f[q * PL + o] = R(0.0);
+        for (int q = 0; q < 6; q++) cu[q * PL + o] = R(0.0);
         return;
     }
-    const double c[2] = {cpl[o], cpl[PL + o]}, mu[2] = {mpl[o], mpl[PL + o]};
-    const double u[3] = {in[n], in[N + n], in[2 * N + n]};
-    const double p = has_p ? in[3 * N + n] : 0.0;
-    const double rho = c[0] * P.rho[0] + c[1] * P.rho[1] + (1.0 - c[0] - c[1]) * P.rho[2];
-    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const R c[2] = {cpl[o], cpl[PL + o]}, mu[2] = {mpl[o], mpl[PL + o]};
+    const R u[3] = {R(in[n]), R(in[N + n]), R(in[2 * N + n])};
+    const R p = has_p ? R(in[3 * N + n]) : R(0.0);
+    const R rho = c[0] * P.rho[0] + c[1] * P.rho[1] + (R(1.0) - c[0] - c[1]) * P.rho[2];
+    const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     for (int k = 0; k < Q; k++) {
-        const double w = wk(k);
-        const double eu = ex(k) * u[0] + ey(k) * u[1] + ez(k) * u[2];
-        const double s = w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+        const R w = R(wk(k));
+        const R eu = R(ex(k)) * u[0] + R(ey(k)) * u[1] + R(ez(k)) * u[2];
+        const R s = w * (R(3.0) * eu + R(4.5) * eu * eu - R(1.5) * usq);
         for (int q = 0; q < 2; q++) {
-            const double em = P.eta[q] * mu[q];
-            f[(Q * q + k) * PL + o] = k == 0 ? c[q] + (w - 1.0) * em : w * (em + 3.0 * c[q] * eu);
+            const R em = P.eta[q] * mu[q];
+            f[(Q * q + k) * PL + o] = k == 0 ? c[q] + (w - R(1.0)) * em : w * (em + R(3.0) * c[q] * eu);
         }
-        f[(2 * Q + k) * PL + o] = k == 0 ? 3.0 * p * (w - 1.0) + rho * s : 3.0 * p * w + rho * s;
+        f[(2 * Q + k) * PL + o] = k == 0 ? R(3.0) * p * (w - R(1.0)) + rho * s : R(3.0) * p * w + rho * s;
+    }
+    if constexpr (kLo3<R>) {
+        f[kLoPlane * PL + o] = R(0.0);
+        f[(kLoPlane + 1) * PL + o] = R(0.0);
     }
     for (int q = 0; q < 2; q++)
         for (int a = 0; a < 3; a++) cu[(3 * q + a) * PL + o] = c[q] * u[a];
 }
 
-// The 11 macroscopic fields c1 c2 c3 rho ux uy uz p mu1 mu2 mu3 as dense
+// The 11 macroscopic fields c1 c2 c3 rho ux uy uz p mu1 mu2 mu3 as dense FP64
 // planes of nx*ny*nz (zero on solids), from the same node3 as the update.
-template <bool UNI>
-__global__ void k3_read(const double* __restrict__ f, const double* __restrict__ cpl, const double* __restrict__ mpl,
-                        const uint32_t* __restrict__ lnk, double* __restrict__ out, Geo3 g, Prm3 P)
+template <typename R, bool UNI>
+__global__ void k3_read(const R* __restrict__ f, const R* __restrict__ cpl, const R* __restrict__ mpl,
+                        const uint32_t* __restrict__ lnk, double* __restrict__ out, Geo3 g, Prm3<R> P)
 {
     NODE_OF_THREAD
     const long long n = ((long long)z * g.ny + y) * g.nx + x, N = (long long)g.nx * g.ny * g.nz;
@@ -588,11 +673,11 @@ __global__ void k3_read(const double* __restrict__ f, const double* __restrict__
     const uint32_t L = lnk[o];
     if (!(L & LNK_SOLID)) {
         const Nb3 nb(g, x, y, z);
-        Node3 m;
+        Node3<R> m;
         node3<UNI>(g, P, f, cpl, mpl, L, nb, o, m);
         v[0] = m.c1;
         v[1] = m.c2;
-        v[2] = 1.0 - m.c1 - m.c2;
+        v[2] = R(1.0) - m.c1 - m.c2;
         v[3] = m.rho;
         v[4] = m.u[0];
         v[5] = m.u[1];
@@ -606,8 +691,11 @@ __global__ void k3_read(const double* __restrict__ f, const double* __restrict__
 }
 
 // FP64 mass totals in a fixed order: per-block partials of c1, c2, c3 and
-// the non-finite count over fluid nodes (from the c planes), then one block.
-__global__ void __launch_bounds__(256) k3_mass_partials(const double* __restrict__ cpl,
+// the non-finite count over fluid nodes, each c_i summed in FP64 from the
+// stored populations (FP32 storage: the rest pairs' lo parts included), then
+// one block.
+template <typename R>
+__global__ void __launch_bounds__(256) k3_mass_partials(const R* __restrict__ f,
                                                         const uint8_t* __restrict__ kind, double* __restrict__ part,
                                                         Geo3 g)
 {
@@ -620,7 +708,16 @@ __global__ void __launch_bounds__(256) k3_mass_partials(const double* __restrict
         const int y = (int)(r % g.ny), z = (int)(r / g.ny);
         const long long o = node_off(g, x, y, z);
         if (kind[o] != K_FLUID) continue;
-        const double c1 = cpl[o], c2 = cpl[g.plane + o];
+        const long long PL = g.plane;
+        double c1 = 0.0, c2 = 0.0;
+        if constexpr (kLo3<R>) {
+            c1 = (double)f[kLoPlane * PL + o];
+            c2 = (double)f[(kLoPlane + 1) * PL + o];
+        }
+        for (int k = 0; k < Q; k++) {
+            c1 += (double)f[k * PL + o];
+            c2 += (double)f[(Q + k) * PL + o];
+        }
         s[0] += c1;
         s[1] += c2;
         s[2] += 1.0 - c1 - c2;
@@ -693,22 +790,27 @@ bool size_ok(int nx, int ny, int nz)
     return nx >= 3 && ny >= 3 && nz >= 3 && (int64_t)nx * ny * nz < ((int64_t)1 << 31);
 }
 
-Layout3 layout3(int nx, int ny, int nz)
+// FP64: 57 distribution planes per buffer; FP32: 59 (the rest pairs' lo
+// parts); c_i u, c and mu planes in the storage type.  Either buffer holds at
+// least 6 FP64 planes (the staging of tlb3_set_fields) and 11 (tlb3_read_fields).
+Layout3 layout3(int nx, int ny, int nz, int precision)
 {
     Layout3 L;
     L.pitch = (int)align3(nx, 32);
     L.plane = (int64_t)L.pitch * ny * nz;
+    const int64_t e = precision == TLB_FP32 ? 4 : 8;
+    const int np = precision == TLB_FP32 ? tlb3::kPlanes3<float> : tlb3::kPlanes3<double>;
     int64_t off = 0;
     auto take = [&](int64_t bytes) {
         const int64_t at = off;
         off = align3(off + bytes, kAlign3);
         return at;
     };
-    L.fA = take(tlb3::NPLANES * L.plane * 8);
-    L.fB = take(tlb3::NPLANES * L.plane * 8);
-    L.cu = take(6 * L.plane * 8);
-    L.cpl = take(2 * L.plane * 8);
-    L.mpl = take(2 * L.plane * 8);
+    L.fA = take(np * L.plane * e);
+    L.fB = take(np * L.plane * e);
+    L.cu = take(6 * L.plane * e);
+    L.cpl = take(2 * L.plane * e);
+    L.mpl = take(2 * L.plane * e);
     L.lnk = take(L.plane * 4);
     L.kind = take(L.plane);
     L.part = take((int64_t)kMassParts3 * 4 * 8);
@@ -726,7 +828,9 @@ struct tlb3_lattice {
     char* ws = nullptr;
     Layout3 lay;
     tlb3::Geo3 geo{};
-    tlb3::Prm3 prm{};
+    int prec = TLB_FP64;
+    tlb3::Prm3<double> prm{};
+    tlb3::Prm3<float> prmf{};
     int cur = 0;
     bool have_params = false, have_fields = false, uni = false;
     std::vector<uint8_t> mask;
@@ -737,12 +841,26 @@ struct tlb3_lattice {
     double prof_ms[3] = {0, 0, 0};
     int64_t prof_n[3] = {0, 0, 0};
 
-    double* buf(int which) { return (double*)(ws + (which == 0 ? lay.fA : lay.fB)); }
-    double* fcur() { return buf(cur); }
-    double* fspare() { return buf(cur ^ 1); }
-    double* cu() { return (double*)(ws + lay.cu); }
-    double* cpl() { return (double*)(ws + lay.cpl); }
-    double* mpl() { return (double*)(ws + lay.mpl); }
+    // the regions in the storage type R
+    template <typename R>
+    R* buf(int which) { return (R*)(ws + (which == 0 ? lay.fA : lay.fB)); }
+    template <typename R>
+    R* fcur() { return buf<R>(cur); }
+    template <typename R>
+    R* fspare() { return buf<R>(cur ^ 1); }
+    template <typename R>
+    R* cu() { return (R*)(ws + lay.cu); }
+    template <typename R>
+    R* cpl() { return (R*)(ws + lay.cpl); }
+    template <typename R>
+    R* mpl() { return (R*)(ws + lay.mpl); }
+    double* stage() { return (double*)(ws + (cur ? lay.fA : lay.fB)); }  // the spare buffer as FP64 staging
+    template <typename R>
+    const tlb3::Prm3<R>& P() const
+    {
+        if constexpr (std::is_same<R, float>::value) return prmf;
+        else return prm;
+    }
     uint8_t* kind() { return (uint8_t*)(ws + lay.kind); }
     uint32_t* lnk() { return (uint32_t*)(ws + lay.lnk); }
     int64_t n() const { return (int64_t)nx * ny * nz; }
@@ -787,12 +905,69 @@ int prof_mark3(tlb3_lattice* L, int j)
 }
 
 // c and mu planes of the current state (the first two launches of a step)
-int order_params3(tlb3_lattice* L)
+template <typename R>
+int order_params3_t(tlb3_lattice* L)
 {
-    tlb3::k3_csum<<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cpl(), L->kind(), L->geo);
+    tlb3::k3_csum<R><<<grid3(L), 128, 0, L->stream>>>(L->fcur<R>(), L->cpl<R>(), L->kind(), L->geo);
     int rc = prof_mark3(L, 1);
     if (rc) return rc;
-    tlb3::k3_mu<<<grid3(L), 128, 0, L->stream>>>(L->cpl(), L->mpl(), L->lnk(), L->geo, L->prm);
+    tlb3::k3_mu<R><<<grid3(L), 128, 0, L->stream>>>(L->cpl<R>(), L->mpl<R>(), L->lnk(), L->geo, L->P<R>());
+    T3_CUDA(cudaGetLastError());
+    return TLB_OK;
+}
+int order_params3(tlb3_lattice* L)
+{
+    return L->prec == TLB_FP32 ? order_params3_t<float>(L) : order_params3_t<double>(L);
+}
+
+// the fused update and push of one step, current buffer -> spare buffer
+template <typename R>
+int update3_t(tlb3_lattice* L)
+{
+    if (L->uni)
+        tlb3::k3_update<R, true><<<grid3(L), 128, 0, L->stream>>>(L->fcur<R>(), L->fspare<R>(), L->cu<R>(), L->cpl<R>(),
+                                                                  L->mpl<R>(), L->lnk(), L->geo, L->P<R>());
+    else
+        tlb3::k3_update<R, false><<<grid3(L), 128, 0, L->stream>>>(L->fcur<R>(), L->fspare<R>(), L->cu<R>(),
+                                                                   L->cpl<R>(), L->mpl<R>(), L->lnk(), L->geo,
+                                                                   L->P<R>());
+    T3_CUDA(cudaGetLastError());
+    return TLB_OK;
+}
+
+// initial state from the FP64 staging (c1, c2 at stage, then ux, uy, uz[, p])
+template <typename R>
+int init3_t(tlb3_lattice* L, const double* stage, bool has_p)
+{
+    const size_t N = (size_t)L->n();
+    tlb3::k3_load_c<R><<<grid3(L), 128, 0, L->stream>>>(stage, L->cpl<R>(), L->kind(), L->geo);
+    tlb3::k3_mu<R><<<grid3(L), 128, 0, L->stream>>>(L->cpl<R>(), L->mpl<R>(), L->lnk(), L->geo, L->P<R>());
+    tlb3::k3_init<R><<<grid3(L), 128, 0, L->stream>>>(L->fcur<R>(), L->cu<R>(), L->cpl<R>(), L->mpl<R>(), L->kind(),
+                                                      stage + 2 * N, has_p ? 1 : 0, L->geo, L->P<R>());
+    T3_CUDA(cudaGetLastError());
+    return TLB_OK;
+}
+
+// the 11 fields as FP64 planes into `out` (device)
+template <typename R>
+int read3_t(tlb3_lattice* L, double* out)
+{
+    if (L->uni)
+        tlb3::k3_read<R, true><<<grid3(L), 128, 0, L->stream>>>(L->fcur<R>(), L->cpl<R>(), L->mpl<R>(), L->lnk(), out,
+                                                                L->geo, L->P<R>());
+    else
+        tlb3::k3_read<R, false><<<grid3(L), 128, 0, L->stream>>>(L->fcur<R>(), L->cpl<R>(), L->mpl<R>(), L->lnk(), out,
+                                                                 L->geo, L->P<R>());
+    T3_CUDA(cudaGetLastError());
+    return TLB_OK;
+}
+
+// FP64 mass totals of the current state into the diag slots
+template <typename R>
+int mass3_t(tlb3_lattice* L, double* part, double* diag)
+{
+    tlb3::k3_mass_partials<R><<<kMassParts3, 256, 0, L->stream>>>(L->fcur<R>(), L->kind(), part, L->geo);
+    tlb3::k3_mass_final<<<1, 256, 0, L->stream>>>(part, kMassParts3, diag);
     T3_CUDA(cudaGetLastError());
     return TLB_OK;
 }
@@ -809,19 +984,21 @@ int links3(tlb3_lattice* L)
 
 extern "C" {
 
-int64_t tlb3_workspace_bytes(int nx, int ny, int nz)
+int64_t tlb3_workspace_bytes(int nx, int ny, int nz, int precision)
 {
     if (!size_ok(nx, ny, nz)) return err3(TLB_EINVAL, "lattice size %dx%dx%d out of range", nx, ny, nz);
+    if (precision != TLB_FP64 && precision != TLB_FP32) return err3(TLB_EINVAL, "precision must be TLB_FP64 or TLB_FP32");
     tlb::clear_error();
-    return layout3(nx, ny, nz).total;
+    return layout3(nx, ny, nz, precision).total;
 }
 
-int tlb3_create(int nx, int ny, int nz, const int32_t edges[6], void* dev_workspace, int64_t ws_bytes,
-                void* cuda_stream, tlb3_lattice** out)
+int tlb3_create(int nx, int ny, int nz, int precision, const int32_t edges[6], void* dev_workspace,
+                int64_t ws_bytes, void* cuda_stream, tlb3_lattice** out)
 {
     if (!out) return err3(TLB_EINVAL, "out is null");
     *out = nullptr;
     if (!size_ok(nx, ny, nz)) return err3(TLB_EINVAL, "lattice size %dx%dx%d out of range", nx, ny, nz);
+    if (precision != TLB_FP64 && precision != TLB_FP32) return err3(TLB_EINVAL, "precision must be TLB_FP64 or TLB_FP32");
     if (!edges) return err3(TLB_EINVAL, "edges is null");
     for (int a = 0; a < 3; a++) {
         const int lo = edges[2 * a], hi = edges[2 * a + 1];
@@ -829,11 +1006,12 @@ int tlb3_create(int nx, int ny, int nz, const int32_t edges[6], void* dev_worksp
             return err3(TLB_EINVAL, "edge kinds must be periodic, wetting or neutral (no lid in 3D)");
         if ((lo == 0) != (hi == 0)) return err3(TLB_EINVAL, "a periodic edge needs a periodic opposite edge");
     }
-    const Layout3 lay = layout3(nx, ny, nz);
+    const Layout3 lay = layout3(nx, ny, nz, precision);
     if (!dev_workspace || ((uintptr_t)dev_workspace) % kAlign3) return err3(TLB_EINVAL, "workspace must be 256-byte aligned");
     if (ws_bytes < lay.total)
         return err3(TLB_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_bytes, (long long)lay.total);
     auto* L = new tlb3_lattice;
+    L->prec = precision;
     L->nx = nx;
     L->ny = ny;
     L->nz = nz;
@@ -911,7 +1089,7 @@ int tlb3_set_params(tlb3_lattice* L, const tlb_params* p)
     const double lam[2] = {l1, l2}, tau[2] = {p->tau1, p->tau2};
     const double rho[3] = {p->rho1, p->rho2, p->rho3}, nu[3] = {p->nu1, p->nu2, p->nu3};
     constexpr double w0 = 1.0 / 3.0, w18 = 1.0 / 18.0, w36 = 1.0 / 36.0;
-    tlb3::Prm3 P{};
+    tlb3::Prm3<double> P{};
     for (int i = 0; i < 3; i++) {
         P.rho[i] = rho[i];
         P.nu[i] = nu[i];
@@ -962,6 +1140,13 @@ int tlb3_set_params(tlb3_lattice* L, const tlb_params* p)
     P.Gc[0] = rho[0] * p->gx;
     P.Gc[1] = rho[0] * p->gy;
     L->prm = P;
+    // the FP32 copy: every member of Prm3 is one scalar of its type
+    static_assert(sizeof(tlb3::Prm3<double>) == 2 * sizeof(tlb3::Prm3<float>), "Prm3 holds scalars only");
+    {
+        const double* src = reinterpret_cast<const double*>(&L->prm);
+        float* dst = reinterpret_cast<float*>(&L->prmf);
+        for (size_t i = 0; i < sizeof(tlb3::Prm3<double>) / sizeof(double); i++) dst[i] = (float)src[i];
+    }
     L->uni = rho[0] == rho[1] && rho[1] == rho[2] && nu[0] == nu[1] && nu[1] == nu[2];
     L->have_params = true;
     return tlb::clear_error();
@@ -975,21 +1160,16 @@ int tlb3_set_fields(tlb3_lattice* L, const double* c1, const double* c2, const d
     if (!L->have_params) return err3(TLB_ESTATE, "set_params first");
     if (!c1 || !c2 || !ux || !uy || !uz) return err3(TLB_EINVAL, "c1, c2, ux, uy, uz must not be null");
     const size_t N = (size_t)L->n(), bytes = N * sizeof(double);
-    double* stage = L->fspare();  // 57 planes of >= N doubles
+    double* stage = L->stage();  // the spare buffer: room for >= 11 FP64 planes of N
     T3_CUDA(cudaMemcpyAsync(stage, c1, bytes, cudaMemcpyHostToDevice, L->stream));
     T3_CUDA(cudaMemcpyAsync(stage + N, c2, bytes, cudaMemcpyHostToDevice, L->stream));
-    tlb3::k3_load_c<<<grid3(L), 128, 0, L->stream>>>(stage, L->cpl(), L->kind(), L->geo);
-    tlb3::k3_mu<<<grid3(L), 128, 0, L->stream>>>(L->cpl(), L->mpl(), L->lnk(), L->geo, L->prm);
-    T3_CUDA(cudaGetLastError());
-    // u, p after the c staging has been consumed (same stream)
     double* in = stage + 2 * N;
     T3_CUDA(cudaMemcpyAsync(in, ux, bytes, cudaMemcpyHostToDevice, L->stream));
     T3_CUDA(cudaMemcpyAsync(in + N, uy, bytes, cudaMemcpyHostToDevice, L->stream));
     T3_CUDA(cudaMemcpyAsync(in + 2 * N, uz, bytes, cudaMemcpyHostToDevice, L->stream));
     if (p) T3_CUDA(cudaMemcpyAsync(in + 3 * N, p, bytes, cudaMemcpyHostToDevice, L->stream));
-    tlb3::k3_init<<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cu(), L->cpl(), L->mpl(), L->kind(), in, p ? 1 : 0,
-                                                   L->geo, L->prm);
-    T3_CUDA(cudaGetLastError());
+    rc = L->prec == TLB_FP32 ? init3_t<float>(L, stage, p != nullptr) : init3_t<double>(L, stage, p != nullptr);
+    if (rc) return rc;
     T3_CUDA(cudaStreamSynchronize(L->stream));
     L->have_fields = true;
     return tlb::clear_error();
@@ -1006,13 +1186,7 @@ int tlb3_step(tlb3_lattice* L, int64_t n)
         if ((rc = prof_mark3(L, 0))) return rc;
         if ((rc = order_params3(L))) return rc;
         if ((rc = prof_mark3(L, 2))) return rc;
-        if (L->uni)
-            tlb3::k3_update<true><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->fspare(), L->cu(), L->cpl(), L->mpl(),
-                                                                   L->lnk(), L->geo, L->prm);
-        else
-            tlb3::k3_update<false><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->fspare(), L->cu(), L->cpl(), L->mpl(),
-                                                                    L->lnk(), L->geo, L->prm);
-        T3_CUDA(cudaGetLastError());
+        if ((rc = L->prec == TLB_FP32 ? update3_t<float>(L) : update3_t<double>(L))) return rc;
         if ((rc = prof_mark3(L, 3))) return rc;
         L->cur ^= 1;
     }
@@ -1066,12 +1240,8 @@ int tlb3_read_fields(tlb3_lattice* L, uint32_t mask, double* host_out)
     if (!host_out || !mask || (mask >> 11)) return err3(TLB_EINVAL, "bad output or field mask (11 fields)");
     if ((rc = order_params3(L))) return rc;
     const size_t N = (size_t)L->n();
-    double* stage = L->fspare();
-    if (L->uni)
-        tlb3::k3_read<true><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cpl(), L->mpl(), L->lnk(), stage, L->geo, L->prm);
-    else
-        tlb3::k3_read<false><<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cpl(), L->mpl(), L->lnk(), stage, L->geo, L->prm);
-    T3_CUDA(cudaGetLastError());
+    double* stage = L->stage();
+    if ((rc = L->prec == TLB_FP32 ? read3_t<float>(L, stage) : read3_t<double>(L, stage))) return rc;
     size_t done = 0;
     for (int q = 0; q < 11; q++) {
         if (!(mask & (1u << q))) continue;
@@ -1090,13 +1260,35 @@ int tlb3_read_state(tlb3_lattice* L, double* host_out)
     if (!host_out) return err3(TLB_EINVAL, "host_out is null");
     const size_t N = (size_t)L->n(), rows = (size_t)L->ny * L->nz;
     const size_t PL = (size_t)L->lay.plane;
-    for (int q = 0; q < 63; q++) {
-        const double* src = q < 57 ? L->fcur() + q * PL : L->cu() + (q - 57) * PL;
-        T3_CUDA(cudaMemcpy2DAsync(host_out + q * N, (size_t)L->nx * sizeof(double), src,
-                                  (size_t)L->lay.pitch * sizeof(double), (size_t)L->nx * sizeof(double), rows,
-                                  cudaMemcpyDeviceToHost, L->stream));
+    if (L->prec == TLB_FP32) {
+        // 57 + 2 lo + 6 FP32 planes to the host, then widened; the rest
+        // populations reported as hi + lo
+        std::vector<float> h((size_t)65 * N);
+        for (int q = 0; q < 65; q++) {
+            const float* src = q < 59 ? L->fcur<float>() + q * PL : L->cu<float>() + (q - 59) * PL;
+            T3_CUDA(cudaMemcpy2DAsync(h.data() + q * N, (size_t)L->nx * sizeof(float), src,
+                                      (size_t)L->lay.pitch * sizeof(float), (size_t)L->nx * sizeof(float), rows,
+                                      cudaMemcpyDeviceToHost, L->stream));
+        }
+        T3_CUDA(cudaStreamSynchronize(L->stream));
+        for (int q = 0; q < 63; q++) {
+            const float* src = h.data() + (size_t)(q < 57 ? q : q + 2) * N;
+            for (size_t i = 0; i < N; i++) host_out[q * N + i] = (double)src[i];
+        }
+        for (int c = 0; c < 2; c++) {
+            const float* lo = h.data() + (size_t)(tlb3::kLoPlane + c) * N;
+            double* rest = host_out + (size_t)(c * tlb3::Q) * N;
+            for (size_t i = 0; i < N; i++) rest[i] += (double)lo[i];
+        }
+    } else {
+        for (int q = 0; q < 63; q++) {
+            const double* src = q < 57 ? L->fcur<double>() + q * PL : L->cu<double>() + (q - 57) * PL;
+            T3_CUDA(cudaMemcpy2DAsync(host_out + q * N, (size_t)L->nx * sizeof(double), src,
+                                      (size_t)L->lay.pitch * sizeof(double), (size_t)L->nx * sizeof(double), rows,
+                                      cudaMemcpyDeviceToHost, L->stream));
+        }
+        T3_CUDA(cudaStreamSynchronize(L->stream));
     }
-    T3_CUDA(cudaStreamSynchronize(L->stream));
     // solid nodes hold no populations (their slots in the two buffers also
     // serve as staging for set_fields and read_fields): report zeros
     for (size_t i = 0; i < N; i++)
@@ -1111,12 +1303,9 @@ int tlb3_diagnostics(tlb3_lattice* L, tlb_diag* out)
     if (rc) return rc;
     if (!L->have_params || !L->have_fields) return err3(TLB_ESTATE, "no state yet");
     if (!out) return err3(TLB_EINVAL, "out is null");
-    tlb3::k3_csum<<<grid3(L), 128, 0, L->stream>>>(L->fcur(), L->cpl(), L->kind(), L->geo);
     double* part = (double*)(L->ws + L->lay.part);
     double* diag = (double*)(L->ws + L->lay.diag);
-    tlb3::k3_mass_partials<<<kMassParts3, 256, 0, L->stream>>>(L->cpl(), L->kind(), part, L->geo);
-    tlb3::k3_mass_final<<<1, 256, 0, L->stream>>>(part, kMassParts3, diag);
-    T3_CUDA(cudaGetLastError());
+    if ((rc = L->prec == TLB_FP32 ? mass3_t<float>(L, part, diag) : mass3_t<double>(L, part, diag))) return rc;
     double h[4];
     T3_CUDA(cudaMemcpyAsync(h, diag, sizeof h, cudaMemcpyDeviceToHost, L->stream));
     T3_CUDA(cudaStreamSynchronize(L->stream));

@@ -8,7 +8,7 @@ import pytest
 
 import workloads as W
 from oracle import OracleLattice3D
-from parity import assert_oracle_parity3
+from parity import BOUNDS, assert_oracle_parity3
 
 pytestmark = pytest.mark.gpu
 
@@ -24,8 +24,8 @@ def T():
     return T
 
 
-def pair(T, w):
-    L = T.lattice3_from_workload(w)
+def pair(T, w, precision="fp64"):
+    L = T.lattice3_from_workload(w, precision=precision)
     O = OracleLattice3D(w.nx, w.ny, w.nz, w.edges, w.mask, w.params)
     O.set_fields(w.c1, w.c2, w.ux, w.uy, w.uz, w.p)
     return L, O
@@ -123,3 +123,61 @@ def test_full_size_benchmark_lattice_fp64(T):
     L.step(2)
     O.step(2)
     assert_oracle_parity3(L, O, w.params, what=w.name)
+
+
+# FP32 storage: the 2D FP32 bounds against the oracle (uz as ux)
+BOUNDS3_FP32 = dict(BOUNDS["fp32"], uz=BOUNDS["fp32"]["ux"])
+
+
+def fp32_errors(fg, fo):
+    out = {}
+    for k, (kind, bound) in BOUNDS3_FP32.items():
+        err = float(np.abs(fg[k] - fo[k]).max())
+        if kind == "rel":
+            err /= max(float(np.abs(fo[k]).max()), 1e-12)
+        out[k] = (err, bound)
+    return out
+
+
+@pytest.mark.parametrize("shape,seed,edges,solids,steps", [
+    ((20, 18, 16), 21, (0, 0, 1, 2, 0, 0), ("sphere",), 200),
+    ((17, 13, 11), 22, (1, 2, 1, 1, 2, 1), ("pillar", "corner"), 120),
+    ((131, 9, 7), 24, (2, 1, 0, 0, 1, 2), ("pillar",), 60),
+])
+def test_fp32_storage_within_bounds_of_the_oracle(T, shape, seed, edges, solids, steps):
+    w = W.random_lattice3(*shape, seed, edges=edges, solids=solids)
+    L, O = pair(T, w, "fp32")
+    L.step(steps)
+    O.step(steps)
+    bad = {k: v for k, v in fp32_errors(L.fields(), O.fields()).items() if not v[0] < v[1]}
+    assert not bad, f"{w.name} fp32 after {steps}: {bad}"
+
+
+def test_fp32_drops_500_steps_within_bounds_and_mass_conserved(T):
+    w = W.drops3d_on_wall(48, 24, 40, R=10.0)
+    L, O = pair(T, w, "fp32")
+    m0 = np.array(L.diagnostics()["mass"])
+    L.step(500)
+    O.step(500)
+    bad = {k: v for k, v in fp32_errors(L.fields(), O.fields()).items() if not v[0] < v[1]}
+    assert not bad, f"{w.name} fp32: {bad}"
+    m1 = np.array(L.diagnostics()["mass"])
+    drift = np.abs(m1[:2] - m0[:2]) / np.abs(m0[:2])
+    assert (drift < 1e-10).all(), drift
+    # the raw state (rest populations as hi + lo) against the oracle's
+    assert np.abs(L.state() - O.state()).max() < BOUNDS3_FP32["c1"][1]
+
+
+def test_fp32_and_fp64_lattices_coexist(T):
+    """An FP32 and an FP64 lattice stepped alternately on one stream keep
+    their own results (each equals a lattice of its precision stepped alone)."""
+    w = W.random_lattice3(16, 12, 10, 25, solids=("sphere",))
+    a32, a64 = T.lattice3_from_workload(w, precision="fp32"), T.lattice3_from_workload(w)
+    b32, b64 = T.lattice3_from_workload(w, precision="fp32"), T.lattice3_from_workload(w)
+    for _ in range(5):
+        a32.step(7)
+        a64.step(7)
+    b32.step(35)
+    b64.step(35)
+    assert np.array_equal(a32.state(), b32.state())
+    assert np.array_equal(a64.state(), b64.state())
