@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "tlbm.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(tlb_[a-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(tlb3?_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -47,6 +47,20 @@ def test_workspace_size_validation(lib):
     assert b64 >= 128 * 64 * (54 + 4) * 8
     assert b32 >= 128 * 64 * (54 + 4) * 4
     assert b64 > b32
+
+
+def test_d3q19_workspace_size_validation(lib):
+    """tlb3_workspace_bytes: FP64 and FP32 storage, and invalid sizes or
+    precisions (host-only)."""
+    import paper_1710_09534_gb300 as T
+    f = lib.tlb3_workspace_bytes
+    w64, w32 = f(64, 32, 48, T.FP64), f(64, 32, 48, T.FP32)
+    assert w64 > 0 and w32 > 0
+    plane = 64 * 32 * 48
+    assert w64 >= (2 * 57 + 6 + 4) * 8 * plane and w32 >= (2 * 59 + 6 + 4) * 4 * plane
+    assert w32 < 0.6 * w64
+    assert f(2, 32, 48, T.FP64) == T.EINVAL and f(64, 32, 48, T.FP16) == T.EINVAL
+    assert f(65536, 65536, 4, T.FP64) == T.EINVAL  # 2^34 nodes: beyond one 32-bit thread index per node
 
 
 def test_inplace_workspace_is_smaller(lib):
