@@ -233,7 +233,10 @@ class Server:
             retired.clear()
 
         while nxt < len(incoming) or waiting or self.active or retired:
-            arrivals_and_admissions()
+            # with lattices on the GPU, admissions happen while a chunk runs
+            # (below), so that their set-up overlaps the device work
+            if not self.active:
+                arrivals_and_admissions()
             stats.peak_bytes = max(stats.peak_bytes, self.used)
             stats.peak_members = max(stats.peak_members, len(self.active))
             if not self.active:
