@@ -75,6 +75,7 @@ class ServeStats:
     peak_members: int = 0
     gpu_busy: float = 0.0
     chunks: int = 0
+    tune_s: float = 0.0   # wall time spent in the tuner (its trial steps leave the state unchanged)
     tuned: list = field(default_factory=list)
 
     def summary(self):
@@ -88,6 +89,7 @@ class ServeStats:
                 "chunks": self.chunks,
                 "gpu_busy_s": round(self.gpu_busy, 3),
                 "gpu_idle_frac": round(max(0.0, 1.0 - self.gpu_busy / max(self.makespan, 1e-9)), 3),
+                "tune_s": round(self.tune_s, 3),
                 "tuned": self.tuned}
 
 
@@ -191,7 +193,9 @@ class Server:
             scratch = int(self.lib.tlb_batch_tune_scratch_bytes(b._h))
             if self.used + scratch > self.budget:
                 return
+            t0 = time.perf_counter()
             cfg = b.tune(trial_steps=self.tune_steps)
+            stats.tune_s += time.perf_counter() - t0
             self.tune_cache[(precision, key)] = cfg
             stats.tuned.append({"precision": precision, "members": len(b.members),
                                 "tiles_log2": key[0], "small_quarters": key[1],
