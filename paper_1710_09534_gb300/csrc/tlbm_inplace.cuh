@@ -249,18 +249,17 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
             cb[0] = b;
             if (it >= 2) {
                 const int sl = (ym + 9) % 3;
-                sh.A1[sl][t] = fma(R(4), ca[1], ca[0] + ca[2]);
-                sh.A2[sl][t] = fma(R(4), cb[1], cb[0] + cb[2]);
-                sh.D1[sl][t] = dir > 0 ? ca[0] - ca[2] : ca[2] - ca[0];
-                sh.D2[sl][t] = dir > 0 ? cb[0] - cb[2] : cb[2] - cb[0];
+                sh.put_ad(sl, t, fma(R(4), ca[1], ca[0] + ca[2]), fma(R(4), cb[1], cb[0] + cb[2]),
+                          dir > 0 ? ca[0] - ca[2] : ca[2] - ca[0], dir > 0 ? cb[0] - cb[2] : cb[2] - cb[0]);
             }
         }
         __syncthreads();
         // 2) mu of row ym (Eq. 8 with Eq. 20b)
         if (it >= 2 && t >= 1 && t < BLOCK - 1) {
             const int sl = (ym + 9) % 3;
-            const R lap1 = fma(R(4), fma(R(-5), ca[1], ca[0] + ca[2]), sh.A1[sl][t - 1] + sh.A1[sl][t + 1]);
-            const R lap2 = fma(R(4), fma(R(-5), cb[1], cb[0] + cb[2]), sh.A2[sl][t - 1] + sh.A2[sl][t + 1]);
+            const auto al = sh.a(sl, t - 1), ar = sh.a(sl, t + 1);
+            const R lap1 = fma(R(4), fma(R(-5), ca[1], ca[0] + ca[2]), al.x + ar.x);
+            const R lap2 = fma(R(4), fma(R(-5), cb[1], cb[0] + cb[2]), al.y + ar.y);
             R mu1, mu2;
             chem_pot(P, ca[1], cb[1], lap1, lap2, mu1, mu2);
             ma[2] = ma[1];
@@ -270,8 +269,7 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
             mb[1] = mb[0];
             mb[0] = mu2;
             if constexpr (!UNI) {
-                sh.M1[t] = fma(R(4), ma[1], ma[0] + ma[2]);
-                sh.M2[t] = fma(R(4), mb[1], mb[0] + mb[2]);
+                sh.put_m(t, fma(R(4), ma[1], ma[0] + ma[2]), fma(R(4), mb[1], mb[0] + mb[2]));
             }
         }
         __syncthreads();
@@ -284,15 +282,18 @@ __device__ __forceinline__ void interior_tile_ip(S* f, CuT<S>* __restrict__ cu, 
             m.c2 = cb[2];
             m.mu1 = ma[1];
             m.mu2 = mb[1];
-            m.g1x = sh.A1[su][t + 1] - sh.A1[su][t - 1];
-            m.g2x = sh.A2[su][t + 1] - sh.A2[su][t - 1];
-            m.g1y = fma(R(4), sh.D1[su][t], sh.D1[su][t - 1] + sh.D1[su][t + 1]);
-            m.g2y = fma(R(4), sh.D2[su][t], sh.D2[su][t - 1] + sh.D2[su][t + 1]);
+            const auto al = sh.a(su, t - 1), ar = sh.a(su, t + 1);
+            const auto dl = sh.d(su, t - 1), dc = sh.d(su, t), dr = sh.d(su, t + 1);
+            m.g1x = ar.x - al.x;
+            m.g2x = ar.y - al.y;
+            m.g1y = fma(R(4), dc.x, dl.x + dr.x);
+            m.g2y = fma(R(4), dc.y, dl.y + dr.y);
             if constexpr (UNI) {
                 m.lm1 = m.lm2 = R(0);
             } else {
-                m.lm1 = fma(R(4), fma(R(-5), ma[1], ma[0] + ma[2]), sh.M1[t - 1] + sh.M1[t + 1]);
-                m.lm2 = fma(R(4), fma(R(-5), mb[1], mb[0] + mb[2]), sh.M2[t - 1] + sh.M2[t + 1]);
+                const auto ml = sh.m(t - 1), mr = sh.m(t + 1);
+                m.lm1 = fma(R(4), fma(R(-5), ma[1], ma[0] + ma[2]), ml.x + mr.x);
+                m.lm2 = fma(R(4), fma(R(-5), mb[1], mb[0] + mb[2]), ml.y + mr.y);
             }
             m.rho = UNI ? P.rho[2] : density(P, m.c1, m.c2);
         }
