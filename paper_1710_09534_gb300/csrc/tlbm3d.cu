@@ -309,6 +309,22 @@ __device__ __forceinline__ R wdot(const R X[3])
 template <typename R>
 constexpr bool kGReg3 = !kLo3<R>;
 
+// Where a node's own planes (populations, rest lo parts, c_i u) are read
+// from: global memory (plane stride PL, element o), or, with STG, the
+// block's shared-memory stage (stride = block size, element = thread) that
+// the update fills by asynchronous copies at its start; ready() waits for
+// this thread's copies.
+template <typename R, bool STG>
+struct PopSrc {
+    const R* b;  // plane 0 of the node
+    long long pl;
+    __device__ __forceinline__ R operator()(int q) const { return b[q * pl]; }
+    __device__ __forceinline__ void ready() const
+    {
+        if constexpr (STG) asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+};
+
 template <typename R>
 struct Node3 {
     R c1, c2, mu1, mu2, rho;
@@ -319,8 +335,8 @@ struct Node3 {
     R g[Q];
 };
 
-template <bool UNI, typename R>
-__device__ __forceinline__ void node3(const Geo3& g, const Prm3<R>& P, const R* __restrict__ f,
+template <bool UNI, typename R, bool STG>
+__device__ __forceinline__ void node3(const Geo3& g, const Prm3<R>& P, const PopSrc<R, STG>& fs,
                                       const R* __restrict__ cpl, const R* __restrict__ mpl, uint32_t L,
                                       const Nb3& nb, long long o, Node3<R>& n)
 {
@@ -348,12 +364,12 @@ __device__ __forceinline__ void node3(const Geo3& g, const Prm3<R>& P, const R* 
     G2[1] = fma(R(2.0), d2[1], (d2[3] - d2[4]) + (d2[7] + d2[8]));
     G2[2] = fma(R(2.0), d2[2], (d2[5] - d2[6]) + (d2[7] - d2[8]));
     // g moments from the sums and differences of opposite pairs
-    const R* gq = f + 2 * Q * PL;
-    if constexpr (kGReg3<R>) n.g[0] = gq[o];
+    fs.ready();
+    if constexpr (kGReg3<R>) n.g[0] = fs(2 * Q);
     R gs[9], gd[9];
 #pragma unroll
     for (int p = 0; p < 9; p++) {
-        const R gp = gq[(2 * p + 1) * PL + o], gm = gq[(2 * p + 2) * PL + o];
+        const R gp = fs(2 * Q + 2 * p + 1), gm = fs(2 * Q + 2 * p + 2);
         if constexpr (kGReg3<R>) {
             n.g[2 * p + 1] = gp;
             n.g[2 * p + 2] = gm;
@@ -432,8 +448,8 @@ struct Coll3 {
     R wa36;
 };
 
-template <bool UNI, int p, typename R>
-__device__ __forceinline__ void pair3(const Coll3<R>& C, const R* __restrict__ fA, R* __restrict__ fB,
+template <bool UNI, int p, typename R, bool STG>
+__device__ __forceinline__ void pair3(const Coll3<R>& C, const PopSrc<R, STG>& fs, R* __restrict__ fB,
                                       const Node3<R>& n, const Nb3& nb, uint32_t L, long long o, long long PL,
                                       R& d1, R& d2)
 {
@@ -460,8 +476,8 @@ __device__ __forceinline__ void pair3(const Coll3<R>& C, const R* __restrict__ f
     const R a = fma(beta, R(0.5) * beta, C.t0);
     const R sym = fma(beta, KX, fma(a, C.RX[c], C.PX[c]));
     const R anti = fma(a, KX, fma(beta, C.RX[c], AX));
-    const R f1p = fA[kp * PL + o], f1m = fA[km * PL + o];
-    const R f2p = fA[(Q + kp) * PL + o], f2m = fA[(Q + km) * PL + o];
+    const R f1p = fs(kp), f1m = fs(km);
+    const R f2p = fs(Q + kp), f2m = fs(Q + km);
     const R o1p = fma(C.omt1, f1p, s1p);
     const R o1m = fma(C.omt1, f1m, s1m);
     const R o2p = fma(C.omt2, f2p, s2p);
@@ -476,8 +492,8 @@ __device__ __forceinline__ void pair3(const Coll3<R>& C, const R* __restrict__ f
         gkp = n.g[kp];
         gkm = n.g[km];
     } else {  // read again (from L1) instead of holding 19 values in registers
-        gkp = fA[(2 * Q + kp) * PL + o];
-        gkm = fA[(2 * Q + km) * PL + o];
+        gkp = fs(2 * Q + kp);
+        gkm = fs(2 * Q + km);
     }
     const R ogp = fma(C.omtg, gkp, sym + anti);
     const R ogm = fma(C.omtg, gkm, sym - anti);
@@ -504,23 +520,45 @@ __device__ __forceinline__ void pair3(const Coll3<R>& C, const R* __restrict__ f
 #ifndef TLB3_MINB_GEN
 #define TLB3_MINB_GEN 1
 #endif
-// FP32 storage (bound by memory): resident blocks per SM of both updates
+// FP32 storage (bound by memory): resident blocks per SM of the uniform and
+// the general update; with the stage below, GB300, 192x96x192, uniform:
+// 0.432 / 0.377 / 0.370 ms per launch at 2 / 3 / 4 blocks (128 registers,
+// 8 bytes spilled; the general update would spill 76 bytes at 4)
 #ifndef TLB3_MINB32
-#define TLB3_MINB32 3
+#define TLB3_MINB32 4
 #endif
-template <typename R, bool UNI>
-__global__ void __launch_bounds__(128, kLo3<R> ? TLB3_MINB32 : (UNI ? TLB3_MINB : TLB3_MINB_GEN))
-k3_update(const R* __restrict__ fA, R* __restrict__ fB, R* __restrict__ cu,
-          const R* __restrict__ cpl, const R* __restrict__ mpl, const uint32_t* __restrict__ lnk, Geo3 g,
-          Prm3<R> P)
+#ifndef TLB3_MINB32_GEN
+#define TLB3_MINB32_GEN 3
+#endif
+// FP32 storage: the update node's 59 population planes and 6 c_i u values
+// are copied asynchronously into a shared-memory stage at the start of the
+// update (no registers held while they are in flight; 33 KB per block) and
+// read from there: GB300, 192x96x192, update 0.643 -> 0.377 ms per launch at
+// 3 blocks per SM (whole step 4.40 -> 6.59 G node updates/s).  Before, the
+// populations were loaded where each direction pair is collided, a memory
+// latency the 12 resident warps per SM could not cover.
+#ifndef TLB3_STAGE32
+#define TLB3_STAGE32 1
+#endif
+template <typename R>
+constexpr bool kStage3 = kLo3<R> && TLB3_STAGE32 != 0;
+constexpr int kStageRows3 = kPlanes3<float> + 6;
+
+__device__ __forceinline__ void cp_async4(unsigned dst, const void* src)
 {
-    NODE_OF_THREAD
-    const uint32_t L = lnk[o];
-    if (L & LNK_SOLID) return;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
+template <typename R, bool UNI, bool STG>
+__device__ __forceinline__ void update3_node(const PopSrc<R, STG>& fs, const PopSrc<R, STG>& cs, R* __restrict__ fB,
+                                             R* __restrict__ cu, const R* __restrict__ cpl,
+                                             const R* __restrict__ mpl, uint32_t L, const Geo3& g, int x, int y,
+                                             int z, long long o, const Prm3<R>& P)
+{
     const long long PL = g.plane;
     const Nb3 nb(g, x, y, z);
     Node3<R> n;
-    node3<UNI>(g, P, fA, cpl, mpl, L, nb, o, n);
+    node3<UNI>(g, P, fs, cpl, mpl, L, nb, o, n);
     constexpr R w0 = R(1.0) / R(3.0), w36 = R(1.0) / R(36.0);
     Coll3<R> C;
     // order parameters: Q_i = 3 w36 [c_i u / tau_i + (1 - 1/(2 tau_i)) d(c_i u)],
@@ -528,7 +566,7 @@ k3_update(const R* __restrict__ fA, R* __restrict__ fB, R* __restrict__ cu,
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         const R cu1 = n.c1 * n.u[a], cu2 = n.c2 * n.u[a];
-        const R d1 = cu1 - cu[a * PL + o], d2 = cu2 - cu[(3 + a) * PL + o];
+        const R d1 = cu1 - cs(a), d2 = cu2 - cs(3 + a);
         cu[a * PL + o] = cu1;
         cu[(3 + a) * PL + o] = cu2;
         C.Q1[a] = fma(P.kq[0], cu1, P.sq[0] * d1);
@@ -585,28 +623,61 @@ k3_update(const R* __restrict__ fA, R* __restrict__ fB, R* __restrict__ cu,
     const R P0 = fma(geq0, n.itg, -(w0 * kG) * fma(C.t0, uH, uT));
     R d1 = R(0), d2 = R(0);  // sum_k (f_k - f'_k) over the moving directions (FP32)
     if constexpr (!kLo3<R>) {
-        fB[o] = fma(C.omt1, fA[o], E1);
-        fB[Q * PL + o] = fma(C.omt2, fA[Q * PL + o], E2);
+        fB[o] = fma(C.omt1, fs(0), E1);
+        fB[Q * PL + o] = fma(C.omt2, fs(Q), E2);
     }
-    fB[2 * Q * PL + o] = fma(C.omtg, kGReg3<R> ? n.g[0] : fA[2 * Q * PL + o], P0);
-    pair3<UNI, 0>(C, fA, fB, n, nb, L, o, PL, d1, d2);
-    pair3<UNI, 1>(C, fA, fB, n, nb, L, o, PL, d1, d2);
-    pair3<UNI, 2>(C, fA, fB, n, nb, L, o, PL, d1, d2);
-    pair3<UNI, 3>(C, fA, fB, n, nb, L, o, PL, d1, d2);
-    pair3<UNI, 4>(C, fA, fB, n, nb, L, o, PL, d1, d2);
-    pair3<UNI, 5>(C, fA, fB, n, nb, L, o, PL, d1, d2);
-    pair3<UNI, 6>(C, fA, fB, n, nb, L, o, PL, d1, d2);
-    pair3<UNI, 7>(C, fA, fB, n, nb, L, o, PL, d1, d2);
-    pair3<UNI, 8>(C, fA, fB, n, nb, L, o, PL, d1, d2);
+    fB[2 * Q * PL + o] = fma(C.omtg, kGReg3<R> ? n.g[0] : fs(2 * Q), P0);
+    pair3<UNI, 0>(C, fs, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 1>(C, fs, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 2>(C, fs, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 3>(C, fs, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 4>(C, fs, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 5>(C, fs, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 6>(C, fs, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 7>(C, fs, fB, n, nb, L, o, PL, d1, d2);
+    pair3<UNI, 8>(C, fs, fB, n, nb, L, o, PL, d1, d2);
     if constexpr (kLo3<R>) {
         // rest pairs: the old pair plus the moving populations' decrease
         R h1, l1, h2, l2;
-        rest_add3(fA[o], fA[kLoPlane * PL + o], d1, h1, l1);
-        rest_add3(fA[Q * PL + o], fA[(kLoPlane + 1) * PL + o], d2, h2, l2);
+        rest_add3(fs(0), fs(kLoPlane), d1, h1, l1);
+        rest_add3(fs(Q), fs(kLoPlane + 1), d2, h2, l2);
         fB[o] = h1;
         fB[Q * PL + o] = h2;
         fB[kLoPlane * PL + o] = l1;
         fB[(kLoPlane + 1) * PL + o] = l2;
+    }
+}
+
+template <typename R, bool UNI>
+__global__ void __launch_bounds__(128, kLo3<R> ? (UNI ? TLB3_MINB32 : TLB3_MINB32_GEN) : (UNI ? TLB3_MINB : TLB3_MINB_GEN))
+k3_update(const R* __restrict__ fA, R* __restrict__ fB, R* __restrict__ cu,
+          const R* __restrict__ cpl, const R* __restrict__ mpl, const uint32_t* __restrict__ lnk, Geo3 g,
+          Prm3<R> P)
+{
+    NODE_OF_THREAD
+    const long long PL = g.plane;
+    if constexpr (kStage3<R>) {
+        // launched with 128 threads: row q of the stage holds plane q of the
+        // block's nodes (the 6 c_i u planes after the populations)
+        __shared__ float stg[kStageRows3][128];
+        const int t = threadIdx.x;
+        const unsigned sb = (unsigned)__cvta_generic_to_shared(&stg[0][t]);
+#pragma unroll
+        for (int q = 0; q < kPlanes3<R>; q++) cp_async4(sb + 4u * 128u * q, fA + q * PL + o);
+#pragma unroll
+        for (int a = 0; a < 6; a++) cp_async4(sb + 4u * 128u * (kPlanes3<R> + a), cu + a * PL + o);
+        const PopSrc<R, true> fs{&stg[0][t], 128}, cs{&stg[kPlanes3<R>][t], 128};
+        const uint32_t L = lnk[o];
+        if (L & LNK_SOLID) {
+            fs.ready();  // no copy into the stage may outlive the block
+            return;
+        }
+        update3_node<R, UNI>(fs, cs, fB, cu, cpl, mpl, L, g, x, y, z, o, P);
+    } else {
+        const uint32_t L = lnk[o];
+        if (L & LNK_SOLID) return;
+        update3_node<R, UNI>(PopSrc<R, false>{fA + o, PL}, PopSrc<R, false>{cu + o, PL}, fB, cu, cpl, mpl, L, g, x,
+                             y, z, o, P);
     }
 }
 
@@ -674,7 +745,7 @@ __global__ void k3_read(const R* __restrict__ f, const R* __restrict__ cpl, cons
     if (!(L & LNK_SOLID)) {
         const Nb3 nb(g, x, y, z);
         Node3<R> m;
-        node3<UNI>(g, P, f, cpl, mpl, L, nb, o, m);
+        node3<UNI>(g, P, PopSrc<R, false>{f + o, g.plane}, cpl, mpl, L, nb, o, m);
         v[0] = m.c1;
         v[1] = m.c2;
         v[2] = R(1.0) - m.c1 - m.c2;
