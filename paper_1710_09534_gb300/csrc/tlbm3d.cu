@@ -540,13 +540,25 @@ __device__ __forceinline__ void pair3(const Coll3<R>& C, const PopSrc<R, STG>& f
 #ifndef TLB3_STAGE32
 #define TLB3_STAGE32 1
 #endif
+// FP64: the same stage (57 + 6 rows of 8 bytes: 64.5 KB of dynamic shared
+// memory per block) gains nothing, the update being bound by the FP64 unit:
+// GB300, 192x96x192, uniform update 2.331 -> 2.339 ms per launch, general
+// step 973.6 -> 976.7 M node updates/s; off
+#ifndef TLB3_STAGE64
+#define TLB3_STAGE64 0
+#endif
 template <typename R>
-constexpr bool kStage3 = kLo3<R> && TLB3_STAGE32 != 0;
-constexpr int kStageRows3 = kPlanes3<float> + 6;
+constexpr bool kStage3 = kLo3<R> ? TLB3_STAGE32 != 0 : TLB3_STAGE64 != 0;
+template <typename R>
+constexpr int kStageRows3 = kPlanes3<R> + 6;
+// dynamic shared memory of one update block (the FP32 stage is static)
+template <typename R>
+constexpr size_t kStageDyn3 = (kStage3<R> && !kLo3<R>) ? sizeof(R) * 128 * kStageRows3<R> : 0;
 
-__device__ __forceinline__ void cp_async4(unsigned dst, const void* src)
+template <int N>
+__device__ __forceinline__ void cp_async(unsigned dst, const void* src)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(N) : "memory");
 }
 
 template <typename R, bool UNI, bool STG>
@@ -659,13 +671,21 @@ k3_update(const R* __restrict__ fA, R* __restrict__ fB, R* __restrict__ cu,
     if constexpr (kStage3<R>) {
         // launched with 128 threads: row q of the stage holds plane q of the
         // block's nodes (the 6 c_i u planes after the populations)
-        __shared__ float stg[kStageRows3][128];
+        R(*stg)[128];
+        if constexpr (kLo3<R>) {
+            __shared__ float s32[kStageRows3<float>][128];
+            stg = s32;
+        } else {
+            extern __shared__ __align__(16) unsigned char s64[];
+            stg = reinterpret_cast<R(*)[128]>(s64);
+        }
         const int t = threadIdx.x;
+        constexpr unsigned E = sizeof(R);
         const unsigned sb = (unsigned)__cvta_generic_to_shared(&stg[0][t]);
 #pragma unroll
-        for (int q = 0; q < kPlanes3<R>; q++) cp_async4(sb + 4u * 128u * q, fA + q * PL + o);
+        for (int q = 0; q < kPlanes3<R>; q++) cp_async<E>(sb + E * 128u * q, fA + q * PL + o);
 #pragma unroll
-        for (int a = 0; a < 6; a++) cp_async4(sb + 4u * 128u * (kPlanes3<R> + a), cu + a * PL + o);
+        for (int a = 0; a < 6; a++) cp_async<E>(sb + E * 128u * (kPlanes3<R> + a), cu + a * PL + o);
         const PopSrc<R, true> fs{&stg[0][t], 128}, cs{&stg[kPlanes3<R>][t], 128};
         const uint32_t L = lnk[o];
         if (L & LNK_SOLID) {
@@ -907,6 +927,7 @@ struct tlb3_lattice {
     std::vector<uint8_t> mask;
     // per-kernel timing (tlb3_profile): 4 events per step around the three launches
     bool prof = false;
+    bool stage_attr = false;  // the update's dynamic shared memory limit raised
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
     double prof_ms[3] = {0, 0, 0};
@@ -995,13 +1016,22 @@ int order_params3(tlb3_lattice* L)
 template <typename R>
 int update3_t(tlb3_lattice* L)
 {
+    constexpr size_t dyn = tlb3::kStageDyn3<R>;
+    if (dyn > 0 && !L->stage_attr) {
+        // above the default 48 KB of dynamic shared memory (per device: the
+        // lattice lives on one)
+        T3_CUDA(cudaFuncSetAttribute(tlb3::k3_update<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        T3_CUDA(cudaFuncSetAttribute(tlb3::k3_update<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        L->stage_attr = true;
+    }
     if (L->uni)
-        tlb3::k3_update<R, true><<<grid3(L), 128, 0, L->stream>>>(L->fcur<R>(), L->fspare<R>(), L->cu<R>(), L->cpl<R>(),
-                                                                  L->mpl<R>(), L->lnk(), L->geo, L->P<R>());
+        tlb3::k3_update<R, true><<<grid3(L), 128, dyn, L->stream>>>(L->fcur<R>(), L->fspare<R>(), L->cu<R>(),
+                                                                    L->cpl<R>(), L->mpl<R>(), L->lnk(), L->geo,
+                                                                    L->P<R>());
     else
-        tlb3::k3_update<R, false><<<grid3(L), 128, 0, L->stream>>>(L->fcur<R>(), L->fspare<R>(), L->cu<R>(),
-                                                                   L->cpl<R>(), L->mpl<R>(), L->lnk(), L->geo,
-                                                                   L->P<R>());
+        tlb3::k3_update<R, false><<<grid3(L), 128, dyn, L->stream>>>(L->fcur<R>(), L->fspare<R>(), L->cu<R>(),
+                                                                     L->cpl<R>(), L->mpl<R>(), L->lnk(), L->geo,
+                                                                     L->P<R>());
     T3_CUDA(cudaGetLastError());
     return TLB_OK;
 }
