@@ -304,8 +304,9 @@ __device__ __forceinline__ R wdot(const R X[3])
 // 20b on mu_i, Eq. 43 ghosts) and 1/tau_g (Eqs. 15, 18b); the g populations.
 // The g populations of the update node: FP64 keeps them in registers from
 // the moments to the collision; FP32 storage reads them again there (from
-// L1), which frees the registers the latency-bound FP32 update needs (GB300,
-// 192x96x192: update 0.922 -> 0.642 ms; FP64 2.331 -> 2.372 ms the same way).
+// its shared-memory stage), which frees registers for more resident warps
+// (GB300, 192x96x192, before the stage, reading again through L1: update
+// 0.922 -> 0.642 ms; FP64 2.331 -> 2.372 ms the same way).
 template <typename R>
 constexpr bool kGReg3 = !kLo3<R>;
 
@@ -491,7 +492,7 @@ __device__ __forceinline__ void pair3(const Coll3<R>& C, const PopSrc<R, STG>& f
     if constexpr (kGReg3<R>) {
         gkp = n.g[kp];
         gkm = n.g[km];
-    } else {  // read again (from L1) instead of holding 19 values in registers
+    } else {  // read again instead of holding 19 values in registers
         gkp = fs(2 * Q + kp);
         gkm = fs(2 * Q + km);
     }
