@@ -523,8 +523,8 @@ __device__ __forceinline__ void pair3(const Coll3<R>& C, const PopSrc<R, STG>& f
 #endif
 // FP32 storage (bound by memory): resident blocks per SM of the uniform and
 // the general update; with the stage below, GB300, 192x96x192, uniform:
-// 0.432 / 0.377 / 0.370 ms per launch at 2 / 3 / 4 blocks (128 registers,
-// 8 bytes spilled; the general update would spill 76 bytes at 4)
+// 0.432 / 0.377 / 0.370 / 0.384 ms per launch at 2 / 3 / 4 / 5 blocks (4: 128
+// registers, 8 bytes spilled; the general update would spill 76 bytes at 4)
 #ifndef TLB3_MINB32
 #define TLB3_MINB32 4
 #endif
