@@ -373,7 +373,9 @@ int tlb3_read_state(tlb3_lattice *lat, double *host_out);
 int tlb3_diagnostics(tlb3_lattice *lat, tlb_diag *out);
 /* Per-kernel timing with CUDA events on the lattice's stream, as tlb_profile:
  * ms[0..2] and launches[0..2] for the order-parameter, chemical-potential and
- * update launches of the steps run since tlb3_profile(lat, 1). */
+ * update launches of the steps run since tlb3_profile(lat, 1).  With FP32
+ * storage and equal densities and viscosities the update forms the chemical
+ * potentials itself (no second launch): ms[1] is then the empty interval. */
 int tlb3_profile(tlb3_lattice *lat, int enable);
 int tlb3_profile_read(tlb3_lattice *lat, double ms[3], int64_t launches[3]);
 void tlb3_destroy(tlb3_lattice *lat);

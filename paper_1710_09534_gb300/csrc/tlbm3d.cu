@@ -241,9 +241,28 @@ __global__ void k3_csum(const R* __restrict__ f, R* __restrict__ cpl, const uint
 // 2, diagonal pairs 1 (the integer weights 36 w_k).
 #define W36_SUM(S) fma(R(2.0), ((S)[0] + (S)[1]) + (S)[2], (((S)[3] + (S)[4]) + ((S)[5] + (S)[6])) + ((S)[7] + (S)[8]))
 
-// mu_1, mu_2 of every fluid node: Eq. 8 with the Eq. 20b Laplacian, whose
+// mu_1, mu_2 of a fluid node from the pair sums s_p = c(x + e_k) + c(x - e_k)
+// of its link-selected neighbours: Eq. 8 with the Eq. 20b Laplacian, whose
 // links into wetting solids take the Eq. 42 ghost c + o_i (with the wall
 // value of c taken as the node's own, dx = 1) and into neutral solids c.
+template <typename R>
+__device__ __forceinline__ void mu_from_sums(const Prm3<R>& P, uint32_t L, R c1, R c2, const R s1[9],
+                                             const R s2[9], R& mu1, R& mu2)
+{
+    R l1 = fma(-R(24.0), c1, W36_SUM(s1));
+    R l2 = fma(-R(24.0), c2, W36_SUM(s2));
+    const unsigned nwi = (L >> LNK_NW) & 31u;
+    if (nwi) {
+        const R c3 = R(1.0) - c1 - c2, nw = (R)(int)nwi;
+        const R o1 = P.k4D * fma(P.cos13, c1 * c3, P.cos12 * (c1 * c2));
+        const R o2 = P.k4D * fma(-P.cos12, c1 * c2, P.cos23 * (c2 * c3));
+        l1 = fma(nw, o1, l1);
+        l2 = fma(nw, o2, l2);
+    }
+    chem_pot(P, c1, c2, l1, l2, mu1, mu2);
+}
+
+// mu_1, mu_2 of every fluid node (zero on solids).
 template <typename R>
 __global__ void k3_mu(const R* __restrict__ cpl, R* __restrict__ mpl, const uint32_t* __restrict__ lnk,
                       Geo3 g, Prm3<R> P)
@@ -262,17 +281,7 @@ __global__ void k3_mu(const R* __restrict__ cpl, R* __restrict__ mpl, const uint
             s1[p] = cpl[ap] + cpl[am];
             s2[p] = cpl[PL + ap] + cpl[PL + am];
         }
-        R l1 = fma(-R(24.0), c1, W36_SUM(s1));
-        R l2 = fma(-R(24.0), c2, W36_SUM(s2));
-        const unsigned nwi = (L >> LNK_NW) & 31u;
-        if (nwi) {
-            const R c3 = R(1.0) - c1 - c2, nw = (R)(int)nwi;
-            const R o1 = P.k4D * fma(P.cos13, c1 * c3, P.cos12 * (c1 * c2));
-            const R o2 = P.k4D * fma(-P.cos12, c1 * c2, P.cos23 * (c2 * c3));
-            l1 = fma(nw, o1, l1);
-            l2 = fma(nw, o2, l2);
-        }
-        chem_pot(P, c1, c2, l1, l2, mu1, mu2);
+        mu_from_sums(P, L, c1, c2, s1, s2, mu1, mu2);
     }
     mpl[o] = mu1;
     mpl[PL + o] = mu2;
@@ -336,27 +345,35 @@ struct Node3 {
     R g[Q];
 };
 
-template <bool UNI, typename R, bool STG>
+template <bool UNI, typename R, bool STG, bool FUSE_MU = false>
 __device__ __forceinline__ void node3(const Geo3& g, const Prm3<R>& P, const PopSrc<R, STG>& fs,
                                       const R* __restrict__ cpl, const R* __restrict__ mpl, uint32_t L,
                                       const Nb3& nb, long long o, Node3<R>& n)
 {
     const long long PL = g.plane;
+    constexpr bool FUSE = FUSE_MU && UNI;
     n.c1 = cpl[o];
     n.c2 = cpl[PL + o];
-    n.mu1 = mpl[o];
-    n.mu2 = mpl[PL + o];
+    if constexpr (!FUSE) {
+        n.mu1 = mpl[o];
+        n.mu2 = mpl[PL + o];
+    }
     R d1[9], d2[9], s1[9], s2[9];
 #pragma unroll
     for (int p = 0; p < 9; p++) {
         const long long ap = nb.at(L, o, 2 * p + 1), am = nb.at(L, o, 2 * p + 2);
-        d1[p] = cpl[ap] - cpl[am];
-        d2[p] = cpl[PL + ap] - cpl[PL + am];
-        if constexpr (!UNI) {
+        const R a1 = cpl[ap], b1 = cpl[am], a2 = cpl[PL + ap], b2 = cpl[PL + am];
+        d1[p] = a1 - b1;
+        d2[p] = a2 - b2;
+        if constexpr (FUSE) {  // the c sums of the node's own mu
+            s1[p] = a1 + b1;
+            s2[p] = a2 + b2;
+        } else if constexpr (!UNI) {
             s1[p] = mpl[ap] + mpl[am];
             s2[p] = mpl[PL + ap] + mpl[PL + am];
         }
     }
+    if constexpr (FUSE) mu_from_sums(P, L, n.c1, n.c2, s1, s2, n.mu1, n.mu2);
     R G1[3], G2[3];
     G1[0] = fma(R(2.0), d1[0], (d1[3] + d1[4]) + (d1[5] + d1[6]));
     G1[1] = fma(R(2.0), d1[1], (d1[3] - d1[4]) + (d1[7] + d1[8]));
@@ -550,6 +567,14 @@ __device__ __forceinline__ void pair3(const Coll3<R>& C, const PopSrc<R, STG>& f
 #endif
 template <typename R>
 constexpr bool kStage3 = kLo3<R> ? TLB3_STAGE32 != 0 : TLB3_STAGE64 != 0;
+// FP32 storage, uniform update: the node's mu computed in the update from
+// the c stencil it loads anyway, so a step has no k3_mu launch and reads no
+// mu plane (the general update needs the neighbours' mu: k3_mu stays)
+#ifndef TLB3_FUSE_MU32
+#define TLB3_FUSE_MU32 1
+#endif
+template <typename R>
+constexpr bool kFuseMu3 = kLo3<R> && TLB3_FUSE_MU32 != 0;
 template <typename R>
 constexpr int kStageRows3 = kPlanes3<R> + 6;
 // dynamic shared memory of one update block (the FP32 stage is static)
@@ -571,7 +596,7 @@ __device__ __forceinline__ void update3_node(const PopSrc<R, STG>& fs, const Pop
     const long long PL = g.plane;
     const Nb3 nb(g, x, y, z);
     Node3<R> n;
-    node3<UNI>(g, P, fs, cpl, mpl, L, nb, o, n);
+    node3<UNI, R, STG, kFuseMu3<R>>(g, P, fs, cpl, mpl, L, nb, o, n);
     constexpr R w0 = R(1.0) / R(3.0), w36 = R(1.0) / R(36.0);
     Coll3<R> C;
     // order parameters: Q_i = 3 w36 [c_i u / tau_i + (1 - 1/(2 tau_i)) d(c_i u)],
@@ -997,20 +1022,22 @@ int prof_mark3(tlb3_lattice* L, int j)
     return TLB_OK;
 }
 
-// c and mu planes of the current state (the first two launches of a step)
+// c and mu planes of the current state (the first two launches of a step;
+// in_step: mu only where the update does not form it itself)
 template <typename R>
-int order_params3_t(tlb3_lattice* L)
+int order_params3_t(tlb3_lattice* L, bool in_step)
 {
     tlb3::k3_csum<R><<<grid3(L), 128, 0, L->stream>>>(L->fcur<R>(), L->cpl<R>(), L->kind(), L->geo);
     int rc = prof_mark3(L, 1);
     if (rc) return rc;
-    tlb3::k3_mu<R><<<grid3(L), 128, 0, L->stream>>>(L->cpl<R>(), L->mpl<R>(), L->lnk(), L->geo, L->P<R>());
+    if (!(in_step && L->uni && tlb3::kFuseMu3<R>))
+        tlb3::k3_mu<R><<<grid3(L), 128, 0, L->stream>>>(L->cpl<R>(), L->mpl<R>(), L->lnk(), L->geo, L->P<R>());
     T3_CUDA(cudaGetLastError());
     return TLB_OK;
 }
-int order_params3(tlb3_lattice* L)
+int order_params3(tlb3_lattice* L, bool in_step = false)
 {
-    return L->prec == TLB_FP32 ? order_params3_t<float>(L) : order_params3_t<double>(L);
+    return L->prec == TLB_FP32 ? order_params3_t<float>(L, in_step) : order_params3_t<double>(L, in_step);
 }
 
 // the fused update and push of one step, current buffer -> spare buffer
@@ -1286,7 +1313,7 @@ int tlb3_step(tlb3_lattice* L, int64_t n)
     for (int64_t s = 0; s < n; s++) {
         if (L->prof && L->ev_used == kProfSteps3 && (rc = prof_fold3(L))) return rc;
         if ((rc = prof_mark3(L, 0))) return rc;
-        if ((rc = order_params3(L))) return rc;
+        if ((rc = order_params3(L, true))) return rc;
         if ((rc = prof_mark3(L, 2))) return rc;
         if ((rc = L->prec == TLB_FP32 ? update3_t<float>(L) : update3_t<double>(L))) return rc;
         if ((rc = prof_mark3(L, 3))) return rc;
